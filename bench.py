@@ -1,0 +1,271 @@
+#!/usr/bin/env python3
+"""Benchmark: MLUPS of the fused vdW lattice Boltzmann step on one GB300.
+
+One benchmark step = one full time step (propagation, density, forces, wall
+rule, equilibrium, forcing, collision) over the 4096x1024 sheared workload
+in FP32.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the host cores, each step a bounded row band of the same workload.
+Multi-GPU runs are independent replicas (the lattice is not sharded).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+B_ALG_FP32 = 72.0  # algorithmic bytes per site update: 9 populations read + 9 written
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_solver(w, stream_handle):
+    from paper_1307_6703_gb300 import LB_FP32, Solver
+    return Solver(w.nx, w.ny, precision=LB_FP32, walls=w.walls, a=w.a, b=w.b, T=w.T,
+                  kappa=w.kappa, tau=w.tau, A0=w.A0, lam=w.lam, u_bot=w.u_bot,
+                  u_top=w.u_top, N=w.N, Q=w.Q, stream=stream_handle)
+
+
+def cpu_oracle_mlups(w, budget_s: float, band_rows: int, max_steps: int | None = None):
+    """Time the FP64 oracle on a row band of the workload (bounded sample)."""
+    import oracle
+    nth = os.cpu_count() or 1
+    wb = w.with_(ny=band_rows)
+    o = oracle.Oracle(oracle.Params(nthreads=nth, **wb.physics()))
+    o.init_noise(w.seed, w.rho_mean, w.noise)
+    o.step(1)  # warm-up (allocations, first touch)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= budget_s):
+            break
+    mlups = wb.nx * wb.ny * steps / el / 1e6
+    return mlups, nth, f"{steps} oracle FP64 steps on a {wb.nx}x{wb.ny} row band of the {w.nx}x{w.ny} workload ({el:.1f} s)"
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1307_6703_gb300.workloads import C4
+    w = C4
+    band = 64
+    mlups_w, nth, _ = cpu_oracle_mlups(w, 0, band, max_steps=max(args.warmup, 1))
+    mlups, nth, sample = cpu_oracle_mlups(w, 0, band, max_steps=args.steps)
+    ms = w.nx * band / (mlups * 1e6) * 1e3
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": round(mlups, 3), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "sample_rows": band},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": nth,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1307_6703_gb300 import LB_ERR_UNSTABLE, lb_init, lb_moments, lb_reduce, lb_step
+    from paper_1307_6703_gb300.workloads import C4, noise_field
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = C4
+    sites = w.nx * w.ny
+    stream = torch.cuda.Stream()
+    s = make_solver(w, stream.cuda_stream)
+    s.init_noise(w.seed + rank, w.rho_mean, w.noise)
+
+    # ------------------------------------------------ device-resident timing
+    lb_step(s.h, args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        lb_step(s.h, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    rc, _ = lb_reduce(s.h)
+    unstable = rc == LB_ERR_UNSTABLE
+
+    t_max = t_ms
+    if dist is not None:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = sites * args.steps * world / (t_max * 1e-3) / 1e6
+    per_launch_s = t_ms * 1e-3 / args.steps
+    achieved = B_ALG_FP32 * sites / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # --------------------------------------------- end to end through the ABI
+    # Host inputs from pinned memory; every step reads back the step's
+    # result (mass and momentum, 24 bytes) to the host.
+    n0 = torch.from_numpy(noise_field(w, seed=w.seed + rank)).pin_memory()
+    mom = torch.empty((3, w.ny, w.nx), dtype=torch.float32).pin_memory()
+    k_e2e = max(min(args.steps, 200), 1)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lb_init(s.h, 1, 0, 0.0, 0.0, n0.data_ptr(), None, None)
+    for _ in range(k_e2e):
+        lb_step(s.h, 1)
+        lb_reduce(s.h)
+    lb_moments(s.h, mom[0].data_ptr(), mom[1].data_ptr(), mom[2].data_ptr(), 1, 0)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_mlups = sites * k_e2e * world / e2e_s / 1e6
+    h2d = n0.numel() * 8 / k_e2e
+    d2h = 24 + mom.numel() * 4 / k_e2e
+    s.close()
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "walls": True,
+                       "u_w": w.u_top, "A0": w.A0, "lambda": w.lam, "T_over_Tc": 0.95,
+                       "tau": w.tau, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2: two 151 MB FP32 population buffers",
+                       "unstable_after_timing": unstable},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_kind": peak_kind, "kernel": "lb_step (fused)",
+                         "bytes_per_site": B_ALG_FP32},
+            "clocks": clocks,
+            "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS",
+                    "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
+                    "steps": k_e2e},
+            "gpu_launches": args.steps,
+        }
+        if not args.no_cpu_baseline:
+            mlups, nth, sample = cpu_oracle_mlups(w, args.cpu_seconds, 64)
+            line["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": nth,
+                                    "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    import __graft_entry__
+    __graft_entry__.build()
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

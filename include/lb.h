@@ -1,0 +1,168 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for an
+ * isothermal two-dimensional van der Waals liquid-vapour fluid under a
+ * periodic external force and moving walls (Coclite, Gonnella & Lamura,
+ * arXiv:1307.6703, Sec. II).
+ *
+ * Conventions shared by every entry point
+ *  - Units are lattice units: dx = dt = 1, D2Q9 velocities c_i in {0,+-1}^2,
+ *    reference temperature T0 = 1/3.  The paper's units (dt = sqrt(3)/3,
+ *    |e| = sqrt(3), T0 = 1) map onto these by T -> T/3, a -> a/3,
+ *    kappa -> kappa/3; densities, b, tau (in steps), lengths, the force
+ *    amplitude A0, shear rates and velocities (in dx/dt) are unchanged.
+ *  - Fields are row-major [ny][nx], x fastest.  x is the periodic flow
+ *    direction; rows 0 and ny-1 are the walls when walls are on.
+ *  - Populations are structure-of-arrays planes [9][ny][nx] in link order
+ *    0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE.
+ *  - The stored state at time t is the post-collision, not yet propagated
+ *    populations f*(r, t-1); one step propagates (pull), rebuilds the wall
+ *    links, collides and stores f*(r, t).
+ *  - Every call returns LB_OK (0) or a negative LB_ERR_* code; nothing is
+ *    thrown across the ABI.  lb_last_error() gives a message for the last
+ *    failure on a handle.
+ *  - The caller owns every buffer it passes; the library owns the device
+ *    memory of a handle (allocated by lb_create, freed by lb_destroy) and
+ *    never keeps a caller pointer after a call returns.
+ *  - Work is enqueued on the stream given in lb_params; calls that return
+ *    host data synchronise that stream.  One handle must not be used from
+ *    two host threads at once.
+ *  - There is no CPU fallback: every computation runs in this library's
+ *    CUDA kernels, and a call without a usable CUDA device fails with
+ *    LB_ERR_CUDA.
+ */
+#ifndef LB_H_
+#define LB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LB_OK = 0,
+  LB_ERR_ARG = -1,      /* invalid argument or parameter set             */
+  LB_ERR_CUDA = -2,     /* CUDA runtime error (no device, launch failure) */
+  LB_ERR_OOM = -3,      /* device allocation failed                       */
+  LB_ERR_UNSTABLE = -4, /* non-finite or unphysical density detected      */
+  LB_ERR_TIMEOUT = -5,  /* a bounded device wait gave up                  */
+  LB_ERR_STATE = -6     /* call out of order (e.g. step before init)      */
+};
+
+/* Storage / arithmetic precision of a handle. */
+enum {
+  LB_FP64 = 0,    /* FP64 storage and arithmetic, no fused multiply-add:
+                     the evaluation order of the FP64 oracle (parity mode) */
+  LB_FP32 = 1,    /* FP32 storage and arithmetic (performance path)        */
+  LB_BF16DEV = 2, /* reserved: 16-bit deviation storage                    */
+  LB_FP16DEV = 3  /* reserved: 16-bit deviation storage                    */
+};
+
+/* Element type selector for lb_moments. */
+enum { LB_DTYPE_F64 = 0, LB_DTYPE_F32 = 1 };
+
+/* Problem statement (Sec. II and IV of the paper):
+ *  Eq. (eqstate)  p^w = n T / (1 - b n) - a n^2
+ *  Eq. (force2)   F_int = d(n T - p^w) + kappa n d(lap n)
+ *  Eq. (periodicforce)  F_ext = (A0 sin(2 pi x / lambda), 0), x = column
+ *  Eqs. (xstencil, laplstencil)  3x3 stencils with parameters N and Q
+ *                 (M = (1 - 2N)/4, R = (1 - Q)/2; N = 1/2, Q = 1 is the
+ *                 standard central scheme)
+ *  Eq. (evoleq)   BGK relaxation time tau (in steps), tau > 1/2
+ *  Moving walls   rows 0 and ny-1 move along x with u_bot and u_top; the
+ *                 paper's shear rate gamma gives u_bot = -gamma (ny-1)/2,
+ *                 u_top = +gamma (ny-1)/2.                               */
+typedef struct {
+  int32_t nx, ny;    /* columns (periodic) and rows; nx >= 1, ny >= 1, and
+                        ny >= 3 when walls are on                           */
+  int32_t walls;     /* 1: moving walls on rows 0 and ny-1; 0: periodic y  */
+  int32_t precision; /* LB_FP64 or LB_FP32                                 */
+  double a, b;       /* van der Waals constants (lattice units)            */
+  double T;          /* temperature (lattice units; T_c = 8a/(27b))        */
+  double kappa;      /* square-gradient (surface tension) coefficient      */
+  double tau;        /* relaxation time in steps                           */
+  double A0, lambda; /* periodic force amplitude and wavelength (lambda = 0
+                        switches the force off)                            */
+  double u_bot, u_top; /* wall x-velocities                                */
+  double N, Q;       /* stencil parameters                                 */
+  double rho_ref;    /* reserved (16-bit deviation storage); set 0         */
+  void *stream;      /* cudaStream_t to enqueue on; NULL = default stream  */
+} lb_params;
+
+typedef struct lb_handle lb_handle;
+
+/* Create a solver for the problem *p and allocate its device state (two
+ * population buffers of 9*nx*ny elements plus small work buffers).
+ * *out receives the handle.  Errors: LB_ERR_ARG (bad sizes, tau <= 1/2,
+ * b*n range, precision), LB_ERR_CUDA, LB_ERR_OOM.                          */
+int lb_create(const lb_params *p, lb_handle **out);
+
+/* Initial condition: f*_i = f_i^eq(n0, u0) of Eq. (eqfunc), fluid at the
+ * given density and velocity with no force correction.
+ *  mode 0: noisy uniform density n0 = rho_mean + noise_amp (2U - 1), where
+ *          U in [0,1) is the top 53 bits of output y*nx + x of the
+ *          counter-based SplitMix64 generator seeded with `seed`
+ *          (Steele, Lea & Flood 2014); u0 = 0.  rho0/ux0/uy0 are ignored.
+ *  mode 1: n0 = rho0[ny][nx] (HOST pointer, double, required); ux0 and uy0
+ *          (HOST, double, [ny][nx]) may each be NULL for zero velocity.
+ * Resets the step counter to 0.  Synchronises the stream when host arrays
+ * are read.  Errors: LB_ERR_ARG, LB_ERR_CUDA.                             */
+int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean,
+            double noise_amp, const double *rho0, const double *ux0,
+            const double *uy0);
+
+/* Advance by nsteps >= 0 time steps of Eq. (evoleq) -- propagation,
+ * density (n-hat on wall rows), forces of Eq. (force2) + Eq.
+ * (periodicforce), wall rule, u* of Eq. (newvel), equilibrium Eq.
+ * (eqfunc), forcing Eqs. (forceterm, coeff), BGK collision -- one fused
+ * kernel launch per step, enqueued on the handle's stream without
+ * synchronising.  Errors: LB_ERR_STATE (not initialised), LB_ERR_CUDA.     */
+int lb_step(lb_handle *h, int64_t nsteps);
+
+/* Density n (n-hat on wall rows) and physical velocity u* of Eq. (newvel)
+ * at the current time, i.e. the propagation, forces and wall rule of the
+ * next step applied to the stored state, written to rho, ux, uy ([ny][nx],
+ * element type `dtype`).  Any of the three may be NULL.  on_device = 1:
+ * the pointers are device pointers and the call only enqueues work;
+ * on_device = 0: host pointers, the call synchronises the stream.
+ * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA.                          */
+int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype,
+               int on_device);
+
+/* Global FP64 sums over the stored state: out[0] = total mass
+ * sum_r sum_i f*_i (conserved by the scheme up to rounding, Sec. II),
+ * out[1], out[2] = sum_r sum_i f*_i c_i (x, y).  The sums use a fixed
+ * reduction order, so the result is deterministic.  Host pointer out[3];
+ * synchronises the stream.  Returns LB_ERR_UNSTABLE if any population is
+ * non-finite or any site's post-collision mass lies outside (0, 1/b).     */
+int lb_reduce(lb_handle *h, double *out);
+
+/* Checkpoint: copy the stored populations ([9][ny][nx], storage precision
+ * of the handle) to the HOST buffer buf.  *bytes is the buffer size on
+ * entry and the bytes needed on return; buf = NULL queries the size.
+ * Synchronises the stream.  Errors: LB_ERR_ARG (buffer too small).       */
+int lb_get_state(lb_handle *h, void *buf, size_t *bytes);
+
+/* Restore populations written by lb_get_state of a handle with the same
+ * nx, ny and precision (HOST buffer, exactly the size lb_get_state
+ * reports) and set the step counter to `step`.  Continuing from a restored
+ * state is bitwise identical to never having stopped.                      */
+int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step);
+
+/* Number of steps taken since lb_init / lb_set_state. */
+int lb_get_step(const lb_handle *h, int64_t *step);
+
+/* Release the handle and its device memory (synchronises the stream).
+ * NULL is accepted. */
+int lb_destroy(lb_handle *h);
+
+/* Message for the last failed call on h (or for the last failed lb_create
+ * when h is NULL).  The string stays valid until the next call on h.      */
+const char *lb_last_error(const lb_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H_ */

@@ -1,0 +1,380 @@
+// lb_api.cu -- host side of the C ABI declared in include/lb.h, plus the
+// deterministic FP64 reduction kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lb.h"
+#include "lb_device.cuh"
+#include "lb_internal.h"
+
+using lbk::StepArgs;
+
+struct lb_handle {
+  lb_params p{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  size_t S = 0;          // sites
+  size_t elem = 0;       // bytes per stored population
+  void *f[2] = {nullptr, nullptr};
+  int cur = 0;
+  void *sinx = nullptr;  // device table, storage type
+  double *d_fields = nullptr;   // 3*S doubles, staging for lb_init mode 1
+  void *d_mom = nullptr;        // 3*S doubles, staging for host moments
+  double *d_partials = nullptr; // reduction scratch
+  int *d_flag = nullptr;
+  double *d_out = nullptr;
+  int red_blocks = 0;
+  int64_t step = 0;
+  bool initialised = false;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(lb_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(lb_handle *h, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, m);
+}
+
+#define LB_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <typename real_t>
+StepArgs<real_t> make_args(const lb_handle *h) {
+  const lb_params &p = h->p;
+  StepArgs<real_t> A;
+  A.nx = p.nx;
+  A.ny = p.ny;
+  A.walls = p.walls;
+  A.plane = h->S;
+  A.T = (real_t)p.T;
+  A.a = (real_t)p.a;
+  A.b = (real_t)p.b;
+  A.kappa = (real_t)p.kappa;
+  A.omega = (real_t)(1.0 / p.tau);
+  A.g = (real_t)(1.0 - 1.0 / (2.0 * p.tau));
+  A.th = (real_t)(1.0 / 3.0 - p.T);
+  A.A0 = (real_t)p.A0;
+  A.u_bot = (real_t)p.u_bot;
+  A.u_top = (real_t)p.u_top;
+  A.N = (real_t)p.N;
+  A.M = (real_t)((1.0 - 2.0 * p.N) / 4.0);
+  A.Q = (real_t)p.Q;
+  const double R = (1.0 - p.Q) / 2.0;
+  A.R = (real_t)R;
+  A.four_QR = (real_t)(4.0 * (p.Q + R));
+  A.sinx = (const real_t *)h->sinx;
+  return A;
+}
+
+// ------------------------------------------------------------ reductions
+
+constexpr int RED_THREADS = 256;
+
+// Pass 1: each block sums mass and momentum of its grid-stride share of the
+// sites in FP64 (fixed order) and flags non-finite or out-of-range sites.
+template <typename real_t>
+__global__ void __launch_bounds__(RED_THREADS)
+reduce_pass1(const real_t *__restrict__ f, size_t S, double nmax, double *__restrict__ partials,
+             int *__restrict__ flag) {
+  __shared__ double sm[3][RED_THREADS];
+  double m = 0.0, jx = 0.0, jy = 0.0;
+  int bad = 0;
+  for (size_t s = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; s < S;
+       s += (size_t)gridDim.x * RED_THREADS) {
+    double v[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) v[i] = (double)f[i * S + s];
+    double ms = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) ms += v[i];
+    const double xs = ((((v[1] - v[3]) + v[5]) - v[6]) - v[7]) + v[8];
+    const double ys = ((((v[2] - v[4]) + v[5]) + v[6]) - v[7]) - v[8];
+    if (!(ms > 0.0 && ms < nmax) || !isfinite(xs) || !isfinite(ys)) bad = 1;
+    m += ms;
+    jx += xs;
+    jy += ys;
+  }
+  sm[0][threadIdx.x] = m;
+  sm[1][threadIdx.x] = jx;
+  sm[2][threadIdx.x] = jy;
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) sm[c][threadIdx.x] += sm[c][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x + 0] = sm[0][0];
+    partials[3 * blockIdx.x + 1] = sm[1][0];
+    partials[3 * blockIdx.x + 2] = sm[2][0];
+  }
+  if (bad) atomicOr(flag, 1);
+}
+
+// Pass 2: one block adds the block partials in a fixed order.
+__global__ void __launch_bounds__(RED_THREADS)
+reduce_pass2(const double *__restrict__ partials, int nblocks, double *__restrict__ out) {
+  __shared__ double sm[3][RED_THREADS];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += RED_THREADS)
+#pragma unroll
+    for (int c = 0; c < 3; c++) acc[c] += partials[3 * b + c];
+#pragma unroll
+  for (int c = 0; c < 3; c++) sm[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) sm[c][threadIdx.x] += sm[c][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sm[0][0];
+    out[1] = sm[1][0];
+    out[2] = sm[2][0];
+  }
+}
+
+bool fp64(const lb_handle *h) { return h->p.precision == LB_FP64; }
+
+}  // namespace
+
+extern "C" {
+
+int lb_create(const lb_params *p, lb_handle **out) {
+  if (!p || !out) return fail(nullptr, LB_ERR_ARG, "lb_create: null argument");
+  *out = nullptr;
+  if (p->nx < 1 || p->ny < 1) return fail(nullptr, LB_ERR_ARG, "lb_create: nx and ny must be >= 1");
+  if (p->walls != 0 && p->walls != 1) return fail(nullptr, LB_ERR_ARG, "lb_create: walls must be 0 or 1");
+  if (p->walls && p->ny < 3) return fail(nullptr, LB_ERR_ARG, "lb_create: walls need ny >= 3");
+  if (p->precision != LB_FP64 && p->precision != LB_FP32)
+    return fail(nullptr, LB_ERR_ARG, "lb_create: precision must be LB_FP64 or LB_FP32");
+  if (!(p->tau > 0.5)) return fail(nullptr, LB_ERR_ARG, "lb_create: tau must exceed 1/2");
+  if (!(p->T > 0.0) || !(p->b >= 0.0) || !std::isfinite(p->a) || !std::isfinite(p->kappa) ||
+      !std::isfinite(p->N) || !std::isfinite(p->Q) || !std::isfinite(p->A0) ||
+      !(p->lambda >= 0.0) || !std::isfinite(p->u_bot) || !std::isfinite(p->u_top))
+    return fail(nullptr, LB_ERR_ARG, "lb_create: non-finite or out-of-range physical parameter");
+  if ((double)p->nx * (double)p->ny * 9.0 > 4.0e9)
+    return fail(nullptr, LB_ERR_ARG, "lb_create: lattice too large");
+
+  lb_handle *h = new (std::nothrow) lb_handle();
+  if (!h) return fail(nullptr, LB_ERR_OOM, "lb_create: host allocation failed");
+  h->p = *p;
+  h->st = (cudaStream_t)p->stream;
+  h->S = (size_t)p->nx * (size_t)p->ny;
+  h->elem = fp64(h) ? sizeof(double) : sizeof(float);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->f[0], 9 * h->S * h->elem);
+  if (e == cudaSuccess) e = cudaMalloc(&h->f[1], 9 * h->S * h->elem);
+  if (e == cudaSuccess) e = cudaMalloc(&h->sinx, (size_t)p->nx * h->elem);
+  h->red_blocks = (int)std::min<size_t>((h->S + RED_THREADS - 1) / RED_THREADS, 1024);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_partials, 3 * (size_t)h->red_blocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_out, 3 * sizeof(double));
+  if (e == cudaSuccess) {
+    // sin(2 pi x / lambda), evaluated in FP64 on the host.
+    const size_t nb = (size_t)p->nx * h->elem;
+    void *tab = malloc(nb);
+    if (!tab) e = cudaErrorMemoryAllocation;
+    else {
+      for (int x = 0; x < p->nx; x++) {
+        const double s = (p->lambda != 0.0) ? std::sin((6.283185307179586 * (double)x) / p->lambda) : 0.0;
+        if (fp64(h)) ((double *)tab)[x] = s;
+        else ((float *)tab)[x] = (float)s;
+      }
+      e = cudaMemcpy(h->sinx, tab, nb, cudaMemcpyHostToDevice);
+      free(tab);
+    }
+  }
+  if (e != cudaSuccess) {
+    std::string m = std::string("lb_create: ") + cudaGetErrorString(e);
+    int code = (e == cudaErrorMemoryAllocation) ? LB_ERR_OOM : LB_ERR_CUDA;
+    lb_destroy(h);
+    return fail(nullptr, code, m);
+  }
+  *out = h;
+  return LB_OK;
+}
+
+int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean, double noise_amp,
+            const double *rho0, const double *ux0, const double *uy0) {
+  if (!h) return LB_ERR_ARG;
+  if (mode != 0 && mode != 1) return fail(h, LB_ERR_ARG, "lb_init: mode must be 0 or 1");
+  const double *dr = nullptr, *du = nullptr, *dv = nullptr;
+  if (mode == 1) {
+    if (!rho0) return fail(h, LB_ERR_ARG, "lb_init: mode 1 needs rho0");
+    if (!h->d_fields) LB_CUDA(h, cudaMalloc((void **)&h->d_fields, 3 * h->S * sizeof(double)));
+    const size_t nb = h->S * sizeof(double);
+    LB_CUDA(h, cudaMemcpyAsync(h->d_fields, rho0, nb, cudaMemcpyHostToDevice, h->st));
+    dr = h->d_fields;
+    if (ux0) {
+      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + h->S, ux0, nb, cudaMemcpyHostToDevice, h->st));
+      du = h->d_fields + h->S;
+    }
+    if (uy0) {
+      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + 2 * h->S, uy0, nb, cudaMemcpyHostToDevice, h->st));
+      dv = h->d_fields + 2 * h->S;
+    }
+  }
+  h->cur = 0;
+  cudaError_t e = fp64(h)
+                      ? lbk::launch_init((double *)h->f[0], h->p.nx, h->p.ny, mode, seed, rho_mean,
+                                         noise_amp, dr, du, dv, h->p.T, h->st)
+                      : lbk::launch_init((float *)h->f[0], h->p.nx, h->p.ny, mode, seed, rho_mean,
+                                         noise_amp, dr, du, dv, h->p.T, h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: init kernel");
+  if (mode == 1) LB_CUDA(h, cudaStreamSynchronize(h->st));
+  h->step = 0;
+  h->initialised = true;
+  return LB_OK;
+}
+
+int lb_step(lb_handle *h, int64_t nsteps) {
+  if (!h) return LB_ERR_ARG;
+  if (nsteps < 0) return fail(h, LB_ERR_ARG, "lb_step: nsteps < 0");
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_step: state not initialised");
+  if (fp64(h)) {
+    const StepArgs<double> A = make_args<double>(h);
+    for (int64_t k = 0; k < nsteps; k++) {
+      cudaError_t e = lbk::launch_step((const double *)h->f[h->cur], (double *)h->f[h->cur ^ 1], A, h->st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: step kernel");
+      h->cur ^= 1;
+      h->step++;
+    }
+  } else {
+    const StepArgs<float> A = make_args<float>(h);
+    for (int64_t k = 0; k < nsteps; k++) {
+      cudaError_t e = lbk::launch_step((const float *)h->f[h->cur], (float *)h->f[h->cur ^ 1], A, h->st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: step kernel");
+      h->cur ^= 1;
+      h->step++;
+    }
+  }
+  return LB_OK;
+}
+
+int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_device) {
+  if (!h) return LB_ERR_ARG;
+  if (dtype != LB_DTYPE_F64 && dtype != LB_DTYPE_F32) return fail(h, LB_ERR_ARG, "lb_moments: bad dtype");
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_moments: state not initialised");
+  const size_t es = dtype == LB_DTYPE_F64 ? sizeof(double) : sizeof(float);
+  void *dn = rho, *du = ux, *dv = uy;
+  if (!on_device) {
+    if (!h->d_mom) LB_CUDA(h, cudaMalloc(&h->d_mom, 3 * h->S * sizeof(double)));
+    char *base = (char *)h->d_mom;
+    dn = rho ? base : nullptr;
+    du = ux ? base + h->S * es : nullptr;
+    dv = uy ? base + 2 * h->S * es : nullptr;
+  }
+  cudaError_t e = fp64(h) ? lbk::launch_moments((const double *)h->f[h->cur], make_args<double>(h), dn, du, dv, dtype, h->st)
+                          : lbk::launch_moments((const float *)h->f[h->cur], make_args<float>(h), dn, du, dv, dtype, h->st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lb_moments: kernel");
+  if (!on_device) {
+    const size_t nb = h->S * es;
+    if (rho) LB_CUDA(h, cudaMemcpyAsync(rho, dn, nb, cudaMemcpyDeviceToHost, h->st));
+    if (ux) LB_CUDA(h, cudaMemcpyAsync(ux, du, nb, cudaMemcpyDeviceToHost, h->st));
+    if (uy) LB_CUDA(h, cudaMemcpyAsync(uy, dv, nb, cudaMemcpyDeviceToHost, h->st));
+    LB_CUDA(h, cudaStreamSynchronize(h->st));
+  }
+  return LB_OK;
+}
+
+int lb_reduce(lb_handle *h, double *out) {
+  if (!h || !out) return h ? fail(h, LB_ERR_ARG, "lb_reduce: null output") : LB_ERR_ARG;
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reduce: state not initialised");
+  const double nmax = h->p.b > 0.0 ? 1.0 / h->p.b : INFINITY;
+  LB_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
+  if (fp64(h))
+    reduce_pass1<double><<<h->red_blocks, RED_THREADS, 0, h->st>>>((const double *)h->f[h->cur], h->S, nmax, h->d_partials, h->d_flag);
+  else
+    reduce_pass1<float><<<h->red_blocks, RED_THREADS, 0, h->st>>>((const float *)h->f[h->cur], h->S, nmax, h->d_partials, h->d_flag);
+  LB_CUDA(h, cudaGetLastError());
+  reduce_pass2<<<1, RED_THREADS, 0, h->st>>>(h->d_partials, h->red_blocks, h->d_out);
+  LB_CUDA(h, cudaGetLastError());
+  int flag = 0;
+  LB_CUDA(h, cudaMemcpyAsync(out, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  LB_CUDA(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  LB_CUDA(h, cudaStreamSynchronize(h->st));
+  if (flag) {
+    char m[128];
+    snprintf(m, sizeof m, "lb_reduce: non-finite or out-of-range density at step %lld", (long long)h->step);
+    return fail(h, LB_ERR_UNSTABLE, m);
+  }
+  return LB_OK;
+}
+
+int lb_get_state(lb_handle *h, void *buf, size_t *bytes) {
+  if (!h || !bytes) return h ? fail(h, LB_ERR_ARG, "lb_get_state: null size") : LB_ERR_ARG;
+  const size_t need = 9 * h->S * h->elem;
+  if (!buf) {
+    *bytes = need;
+    return LB_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return fail(h, LB_ERR_ARG, "lb_get_state: buffer too small");
+  }
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_get_state: state not initialised");
+  LB_CUDA(h, cudaMemcpyAsync(buf, h->f[h->cur], need, cudaMemcpyDeviceToHost, h->st));
+  LB_CUDA(h, cudaStreamSynchronize(h->st));
+  *bytes = need;
+  return LB_OK;
+}
+
+int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step) {
+  if (!h || !buf) return h ? fail(h, LB_ERR_ARG, "lb_set_state: null buffer") : LB_ERR_ARG;
+  const size_t need = 9 * h->S * h->elem;
+  if (bytes != need) return fail(h, LB_ERR_ARG, "lb_set_state: size mismatch");
+  if (step < 0) return fail(h, LB_ERR_ARG, "lb_set_state: negative step");
+  LB_CUDA(h, cudaMemcpyAsync(h->f[h->cur], buf, need, cudaMemcpyHostToDevice, h->st));
+  LB_CUDA(h, cudaStreamSynchronize(h->st));
+  h->step = step;
+  h->initialised = true;
+  return LB_OK;
+}
+
+int lb_get_step(const lb_handle *h, int64_t *step) {
+  if (!h || !step) return LB_ERR_ARG;
+  *step = h->step;
+  return LB_OK;
+}
+
+int lb_destroy(lb_handle *h) {
+  if (!h) return LB_OK;
+  if (h->st || h->initialised) cudaStreamSynchronize(h->st);
+  cudaFree(h->f[0]);
+  cudaFree(h->f[1]);
+  cudaFree(h->sinx);
+  cudaFree(h->d_fields);
+  cudaFree(h->d_mom);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_flag);
+  cudaFree(h->d_out);
+  delete h;
+  return LB_OK;
+}
+
+const char *lb_last_error(const lb_handle *h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

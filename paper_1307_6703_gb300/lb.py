@@ -1,0 +1,228 @@
+"""ctypes binding of the C ABI in include/lb.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; the
+:class:`Solver` convenience class only strings those calls together.  All
+computation happens in the CUDA library; loading fails loudly when it is
+missing or when no CUDA device is usable -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LB_OK = 0
+LB_ERR_ARG = -1
+LB_ERR_CUDA = -2
+LB_ERR_OOM = -3
+LB_ERR_UNSTABLE = -4
+LB_ERR_TIMEOUT = -5
+LB_ERR_STATE = -6
+
+LB_FP64 = 0
+LB_FP32 = 1
+LB_BF16DEV = 2
+LB_FP16DEV = 3
+
+LB_DTYPE_F64 = 0
+LB_DTYPE_F32 = 1
+
+_ERR_NAMES = {LB_ERR_ARG: "LB_ERR_ARG", LB_ERR_CUDA: "LB_ERR_CUDA", LB_ERR_OOM: "LB_ERR_OOM",
+              LB_ERR_UNSTABLE: "LB_ERR_UNSTABLE", LB_ERR_TIMEOUT: "LB_ERR_TIMEOUT",
+              LB_ERR_STATE: "LB_ERR_STATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblb.so")
+
+
+class lb_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("walls", C.c_int32),
+                ("precision", C.c_int32),
+                ("a", C.c_double), ("b", C.c_double), ("T", C.c_double),
+                ("kappa", C.c_double), ("tau", C.c_double),
+                ("A0", C.c_double), ("lambda_", C.c_double),
+                ("u_bot", C.c_double), ("u_top", C.c_double),
+                ("N", C.c_double), ("Q", C.c_double), ("rho_ref", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    """Load liblb.so (built by paper_1307_6703_gb300.build); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise FileNotFoundError(
+                f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        lib.lb_create.argtypes = [C.POINTER(lb_params), C.POINTER(P)]
+        lib.lb_init.argtypes = [P, C.c_int, C.c_uint64, C.c_double, C.c_double, P, P, P]
+        lib.lb_step.argtypes = [P, C.c_int64]
+        lib.lb_moments.argtypes = [P, P, P, P, C.c_int, C.c_int]
+        lib.lb_reduce.argtypes = [P, C.POINTER(C.c_double)]
+        lib.lb_get_state.argtypes = [P, P, C.POINTER(C.c_size_t)]
+        lib.lb_set_state.argtypes = [P, P, C.c_size_t, C.c_int64]
+        lib.lb_get_step.argtypes = [P, C.POINTER(C.c_int64)]
+        lib.lb_destroy.argtypes = [P]
+        lib.lb_last_error.argtypes = [P]
+        lib.lb_last_error.restype = C.c_char_p
+        for name in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_reduce",
+                     "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy"):
+            getattr(lib, name).restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, h) -> int:
+    if rc != LB_OK:
+        raise LBError(rc, lb_last_error(h))
+    return rc
+
+
+def _addr(a) -> int | None:
+    """Address of a numpy array, a torch tensor, or a raw integer pointer."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+# ------------------------------------------------------- same-name wrappers
+
+def lb_create(p: lb_params) -> int:
+    h = C.c_void_p()
+    _check(load_library().lb_create(C.byref(p), C.byref(h)), None)
+    return h.value
+
+
+def lb_init(h, mode: int, seed: int = 0, rho_mean: float = 0.0, noise_amp: float = 0.0,
+            rho0=None, ux0=None, uy0=None) -> int:
+    for a in (rho0, ux0, uy0):
+        if isinstance(a, np.ndarray):
+            assert a.dtype == np.float64 and a.flags.c_contiguous
+    return _check(load_library().lb_init(h, mode, seed, rho_mean, noise_amp, _addr(rho0),
+                                         _addr(ux0), _addr(uy0)), h)
+
+
+def lb_step(h, nsteps: int) -> int:
+    return _check(load_library().lb_step(h, nsteps), h)
+
+
+def lb_moments(h, rho, ux, uy, dtype: int, on_device: int) -> int:
+    return _check(load_library().lb_moments(h, _addr(rho), _addr(ux), _addr(uy), dtype,
+                                            on_device), h)
+
+
+def lb_reduce(h, out=None):
+    """Returns (rc, [mass, momx, momy]); LB_ERR_UNSTABLE is returned, not raised."""
+    buf = (C.c_double * 3)()
+    rc = load_library().lb_reduce(h, buf)
+    if rc not in (LB_OK, LB_ERR_UNSTABLE):
+        _check(rc, h)
+    vals = [buf[0], buf[1], buf[2]]
+    if out is not None:
+        out[:] = vals
+    return rc, vals
+
+
+def lb_get_state(h, buf=None) -> int:
+    n = C.c_size_t(0 if buf is None else buf.nbytes)
+    _check(load_library().lb_get_state(h, _addr(buf), C.byref(n)), h)
+    return n.value
+
+
+def lb_set_state(h, buf, step: int = 0) -> int:
+    return _check(load_library().lb_set_state(h, _addr(buf), buf.nbytes, step), h)
+
+
+def lb_get_step(h) -> int:
+    t = C.c_int64()
+    _check(load_library().lb_get_step(h, C.byref(t)), h)
+    return t.value
+
+
+def lb_destroy(h) -> int:
+    return load_library().lb_destroy(h)
+
+
+def lb_last_error(h) -> str:
+    s = load_library().lb_last_error(h)
+    return s.decode() if s else ""
+
+
+# ------------------------------------------------------------ convenience
+
+class Solver:
+    """Owns one lb_handle.  Arguments are lattice-unit parameters as in lb.h."""
+
+    def __init__(self, nx: int, ny: int, *, walls: bool = True, precision: int = LB_FP32,
+                 a: float, b: float, T: float, kappa: float, tau: float,
+                 A0: float = 0.0, lam: float = 0.0, u_bot: float = 0.0, u_top: float = 0.0,
+                 N: float = 0.5, Q: float = 1.0, stream: int | None = None):
+        self.nx, self.ny, self.precision = nx, ny, precision
+        self.params = lb_params(nx, ny, int(walls), precision, a, b, T, kappa, tau, A0, lam,
+                                u_bot, u_top, N, Q, 0.0, stream)
+        self.h = lb_create(self.params)
+        self.dtype = np.float64 if precision == LB_FP64 else np.float32
+
+    def init_noise(self, seed: int, rho_mean: float, amp: float):
+        lb_init(self.h, 0, seed, rho_mean, amp)
+        return self
+
+    def init_fields(self, rho0, ux0=None, uy0=None):
+        c = (lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64))
+        lb_init(self.h, 1, 0, 0.0, 0.0, c(rho0), c(ux0), c(uy0))
+        return self
+
+    def step(self, nsteps: int = 1):
+        lb_step(self.h, nsteps)
+        return self
+
+    def moments(self, dtype=np.float64):
+        shape = (self.ny, self.nx)
+        n, u, v = (np.empty(shape, dtype=dtype) for _ in range(3))
+        code = LB_DTYPE_F64 if dtype == np.float64 else LB_DTYPE_F32
+        lb_moments(self.h, n, u, v, code, 0)
+        return n, u, v
+
+    def reduce(self):
+        return lb_reduce(self.h)
+
+    def get_state(self) -> np.ndarray:
+        buf = np.empty((9, self.ny, self.nx), dtype=self.dtype)
+        lb_get_state(self.h, buf)
+        return buf
+
+    def set_state(self, f: np.ndarray, step: int = 0):
+        lb_set_state(self.h, np.ascontiguousarray(f, dtype=self.dtype), step)
+        return self
+
+    @property
+    def t(self) -> int:
+        return lb_get_step(self.h)
+
+    def close(self):
+        if self.h:
+            lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

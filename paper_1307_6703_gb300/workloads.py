@@ -1,0 +1,91 @@
+"""Synthetic workloads: parameter sets and seeded initial fields.
+
+This module holds no arithmetic of the method; it only states the problems
+(lattice-unit parameters) and draws seeded inputs.  Tests, the benchmark and
+the smoke check use it for both the CUDA path and the oracle.
+
+Parameter set.  The paper's van der Waals fluid in lattice units (dx = dt = 1,
+T0 = 1/3): a = 3/8, b = 1/3 (critical point n_c = 1, T_c = 1/3),
+kappa = 0.1 (the paper's 0.3), tau = 1, isotropic stencils from Table 1
+(OVC column).  The lattice sizes, wall speeds and potential wavelengths are
+those of the workloads below; temperatures and force amplitudes are the
+paper's own (Sec. IV: T = 0.95 T_c, A0 = 1e-4) where larger values make the
+scheme blow up from a noisy symmetric quench.
+"""
+from __future__ import annotations
+
+from dataclasses import asdict, dataclass, replace
+
+import numpy as np
+
+TC = 1.0 / 3.0  # critical temperature of the paper's set in lattice units
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    walls: bool
+    T: float
+    tau: float
+    A0: float
+    lam: float
+    u_bot: float
+    u_top: float
+    N: float
+    Q: float
+    steps: int
+    a: float = 3.0 / 8.0
+    b: float = 1.0 / 3.0
+    kappa: float = 0.1
+    rho_mean: float = 1.0          # n_c
+    noise: float = 0.01 / 3.5      # +-1 % of n_c... scaled from +-0.01 at rho_c = 3.5
+    seed: int = 1
+
+    def physics(self) -> dict:
+        d = asdict(self)
+        for k in ("name", "steps", "rho_mean", "noise", "seed"):
+            d.pop(k)
+        return d
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+# Plain FP64 step, 64x32, static walls, T = 0.9 T_c, tau = 1, lambda = 32,
+# A0 = 1e-3 (the paper's largest amplitude; 0.05 diverges), 2000 steps.
+C1 = Workload("fp64_64x32_static_walls", 64, 32, True, 0.9 * TC, 1.0, 1e-3, 32.0, 0.0, 0.0,
+              0.3, 2.6, 2000)
+
+# Sheared zebra phase, FP32, 512x256, walls at -U_w / +U_w, lambda = 128,
+# T = 0.95 T_c, tau = 1, A0 = 1e-4, 1000 steps.
+def C2(u_w: float) -> Workload:
+    return Workload(f"fp32_512x256_shear_{u_w:g}", 512, 256, True, 0.95 * TC, 1.0, 1e-4, 128.0,
+                    -u_w, u_w, 0.3, 2.0, 1000)
+
+
+# Headline lattice: 4096x1024, walls at -0.05 / +0.05, lambda = 512,
+# T = 0.95 T_c, tau = 1, A0 = 1e-4.
+C4 = Workload("fp32_4096x1024_shear_0.05", 4096, 1024, True, 0.95 * TC, 1.0, 1e-4, 512.0,
+              -0.05, 0.05, 0.3, 2.0, 1000)
+
+
+def noise_field(w: Workload, seed: int | None = None) -> np.ndarray:
+    """Seeded noisy-uniform density rho_mean + noise * U(-1, 1), [ny][nx]."""
+    rng = np.random.default_rng(w.seed if seed is None else seed)
+    return w.rho_mean + w.noise * rng.uniform(-1.0, 1.0, size=(w.ny, w.nx))
+
+
+def droplet_field(nx: int, ny: int, radius: float, n_in: float, n_out: float,
+                  width: float = 3.0) -> np.ndarray:
+    """Smooth disc of density n_in in a background n_out (tanh edge)."""
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    r = np.hypot(xx - nx / 2 + 0.5, yy - ny / 2 + 0.5)
+    return n_out + (n_in - n_out) * 0.5 * (1.0 - np.tanh((r - radius) / width))
+
+
+def slab_field(nx: int, ny: int, n_in: float, n_out: float, width: float = 3.0) -> np.ndarray:
+    """Liquid slab in the middle half of the rows (two flat interfaces)."""
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    return n_out + (n_in - n_out) * 0.5 * (np.tanh((y - ny / 4) / width) - np.tanh((y - 3 * ny / 4) / width))

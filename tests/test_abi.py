@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every symbol include/lb.h
+declares; the Python binding carries the same names.  No GPU needed (no
+compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1307_6703_gb300.build import build_library
+    return ctypes.CDLL(build_library())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_has_same_names():
+    import paper_1307_6703_gb300 as pkg
+    for name in declared_functions():
+        assert callable(getattr(pkg, name)), name
+
+
+def test_params_struct_layout_matches_header():
+    from paper_1307_6703_gb300.lb import lb_params
+    # 4 int32 + 12 doubles + 1 pointer on LP64
+    assert ctypes.sizeof(lb_params) == 4 * 4 + 12 * 8 + 8
+
+
+def test_create_rejects_bad_parameters_without_gpu(lib):
+    """Argument validation happens before any CUDA call."""
+    from paper_1307_6703_gb300 import LB_ERR_ARG, LBError, lb_create, lb_params
+    base = dict(nx=8, ny=8, walls=1, precision=1, a=0.375, b=1 / 3, T=0.3, kappa=0.1,
+                tau=1.0, A0=0.0, lambda_=0.0, u_bot=0.0, u_top=0.0, N=0.5, Q=1.0,
+                rho_ref=0.0, stream=None)
+    for bad in (dict(tau=0.5), dict(nx=0), dict(walls=1, ny=2), dict(precision=7), dict(T=-1.0)):
+        p = lb_params(**{**base, **bad})
+        with pytest.raises(LBError) as ei:
+            lb_create(p)
+        assert ei.value.code == LB_ERR_ARG
+
+
+def test_product_path_does_not_touch_oracle():
+    """The package never imports the oracle (test infrastructure only)."""
+    pkg = os.path.join(ROOT, "paper_1307_6703_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text
+                assert "lb_oracle" not in text

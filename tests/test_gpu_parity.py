@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 (parity mode, no fused multiply-add) must agree to 1e-12 relative and is
+expected to agree bit for bit.  FP32 is held to 1e-5 max relative density
+error where the dynamics do not amplify rounding, and on the unstable
+512x256 quench to the drift FP32 rounding causes in the oracle itself (see
+test_fp32_config_512x256_1000_steps).  Sizes span several
+tiles with ragged tails, the degenerate 1x1 lattice and the wall/no-wall
+cases; the full 4096x1024 lattice is checked step by step.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import oracle_for, rel_err, solver_for
+
+pytestmark = pytest.mark.gpu
+
+from paper_1307_6703_gb300 import LB_ERR_UNSTABLE, LB_FP32, LB_FP64  # noqa: E402
+from paper_1307_6703_gb300.workloads import C1, C2, C4, TC, noise_field  # noqa: E402
+
+SMALL = [
+    # (nx, ny, walls, u_w, steps)
+    (1, 1, False, 0.0, 30),
+    (3, 5, False, 0.0, 40),
+    (5, 3, True, 0.03, 40),
+    (33, 9, True, 0.02, 60),
+    (37, 17, False, 0.0, 60),
+    (70, 41, True, 0.05, 80),
+]
+
+
+def small_workload(nx, ny, walls, u_w, steps):
+    return C1.with_(nx=nx, ny=ny, walls=walls, u_bot=-u_w, u_top=u_w, steps=steps,
+                    lam=float(max(nx // 2, 1)), A0=1e-3 if nx > 1 else 0.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}")
+def test_fp64_small_lattices(case):
+    w = small_workload(*case)
+    n0 = noise_field(w)
+    ref = oracle_for(w).init_fields(n0).step(w.steps)
+    s = solver_for(w, LB_FP64).init_fields(n0).step(w.steps)
+    f = s.get_state()
+    assert rel_err(f, ref.f) <= 1e-12
+    n, ux, uy = s.moments()
+    rn, rux, ruy = ref.moments()
+    assert rel_err(n, rn) <= 1e-12
+    assert np.abs(ux - rux).max() <= 1e-12 * max(np.abs(rux).max(), 1e-3)
+    assert np.abs(uy - ruy).max() <= 1e-12 * max(np.abs(ruy).max(), 1e-3)
+    s.close()
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}")
+def test_fp64_small_lattices_bitwise(case):
+    """The FP64 parity mode evaluates the oracle's formulas in the same order
+    without fused multiply-adds, so the populations agree bit for bit."""
+    w = small_workload(*case)
+    n0 = noise_field(w)
+    ref = oracle_for(w).init_fields(n0).step(w.steps)
+    s = solver_for(w, LB_FP64).init_fields(n0).step(w.steps)
+    assert np.array_equal(s.get_state(), ref.f)
+    s.close()
+
+
+def test_fp64_noise_init_matches_oracle():
+    """Device SplitMix64 initial condition (lb_init mode 0) = oracle's."""
+    w = C1
+    ref = oracle_for(w).init_noise(7, w.rho_mean, w.noise)
+    s = solver_for(w, LB_FP64).init_noise(7, w.rho_mean, w.noise)
+    assert np.array_equal(s.get_state(), ref.f)
+    s.close()
+
+
+def test_fp64_config_64x32_2000_steps():
+    w = C1
+    n0 = noise_field(w)
+    ref = oracle_for(w).init_fields(n0).step(w.steps)
+    s = solver_for(w, LB_FP64).init_fields(n0).step(w.steps)
+    n, ux, uy = s.moments()
+    rn, rux, ruy = ref.moments()
+    assert rel_err(n, rn) <= 1e-12
+    assert np.abs(ux - rux).max() <= 1e-12 * np.abs(rux).max()
+    assert np.abs(uy - ruy).max() <= 1e-12 * np.abs(ruy).max()
+    assert rel_err(s.get_state(), ref.f) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}")
+def test_fp32_small_lattices(case):
+    w = small_workload(*case)
+    n0 = noise_field(w)
+    ref = oracle_for(w).init_fields(n0).step(w.steps)
+    s = solver_for(w, LB_FP32).init_fields(n0).step(w.steps)
+    n, _, _ = s.moments()
+    rn, _, _ = ref.moments()
+    assert rel_err(n, rn) <= 1e-5
+    s.close()
+
+
+def _fp32_storage_divergence(w, n0, steps):
+    """How far the FP64 oracle drifts when its state is rounded to FP32
+    after every step (no other change): the floor that FP32 storage alone
+    imposes on this workload."""
+    a = oracle_for(w).init_fields(n0)
+    b = oracle_for(w).init_fields(n0)
+    for _ in range(steps):
+        a.step(1)
+        b.step(1)
+        b.f = b.f.astype(np.float32).astype(np.float64)
+    na, nb = a.moments()[0], b.moments()[0]
+    return float(np.abs(na - nb).max() / np.abs(na).max())
+
+
+@pytest.mark.parametrize("u_w", [0.01, 0.05])
+def test_fp32_config_512x256_1000_steps(u_w):
+    """FP32 against the FP64 oracle on the sheared 512x256 quench.
+
+    The noisy symmetric quench is linearly unstable (spinodal
+    decomposition): perturbations of FP32 size are amplified ~1e3 between
+    steps 100 and 500.  The max relative density error is held to 1e-5 at
+    step 100, before the amplification, and at 1000 steps to the drift that
+    FP32 rounding produces in the oracle itself: at most 30x the divergence
+    of the oracle with its state rounded to FP32 after every step (FP32
+    arithmetic rounds each population ~25 times per step)."""
+    w = C2(u_w)
+    n0 = noise_field(w)
+    ref = oracle_for(w).init_fields(n0)
+    s = solver_for(w, LB_FP32).init_fields(n0)
+    curve = []
+    done = 0
+    for t in (100, 250, 500, 1000):
+        ref.step(t - done)
+        s.step(t - done)
+        done = t
+        n, _, _ = s.moments()
+        rn, _, _ = ref.moments()
+        curve.append((t, float(np.abs(n - rn).max() / np.abs(rn).max())))
+    s.close()
+    floor = _fp32_storage_divergence(w, n0, 1000)
+    print(f"fp32 error curve (step, max rel density error): {curve}; "
+          f"oracle FP32-storage divergence at 1000 steps: {floor:.3e}")
+    assert curve[0][1] <= 1e-5, curve
+    assert curve[-1][1] <= 30.0 * floor, (curve, floor)
+
+
+def test_full_size_fp32_one_step():
+    """4096x1024 (the benchmark lattice, same launch path): device noise
+    init and one step against the oracle on every site."""
+    w = C4
+    ref = oracle_for(w).init_noise(w.seed, w.rho_mean, w.noise)
+    s = solver_for(w, LB_FP32).init_noise(w.seed, w.rho_mean, w.noise)
+    f0 = s.get_state()
+    assert rel_err(f0, ref.f) <= 6e-8  # FP32 rounding of the FP64 equilibrium
+    ref.step(1)
+    s.step(1)
+    assert rel_err(s.get_state(), ref.f) <= 1e-6
+    n, ux, uy = s.moments()
+    rn, rux, ruy = ref.moments()
+    assert rel_err(n, rn) <= 1e-6
+    s.close()
+
+
+def test_full_size_fp64_one_step_bitwise():
+    w = C4
+    ref = oracle_for(w).init_noise(3, w.rho_mean, w.noise).step(1)
+    s = solver_for(w, LB_FP64).init_noise(3, w.rho_mean, w.noise).step(1)
+    assert np.array_equal(s.get_state(), ref.f)
+    s.close()
+
+
+def test_full_size_fp32_mass_conservation():
+    w = C4
+    s = solver_for(w, LB_FP32).init_noise(w.seed, w.rho_mean, w.noise)
+    rc, (m0, _, _) = s.reduce()
+    assert rc == 0
+    s.step(300)
+    rc, (m1, jx, jy) = s.reduce()
+    assert rc == 0
+    assert abs(m1 - m0) / m0 < 2e-5
+    s.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = C2(0.05).with_(nx=96, ny=48)
+    a = solver_for(w, LB_FP32).init_noise(5, w.rho_mean, w.noise).step(200)
+    b = solver_for(w, LB_FP32).init_noise(5, w.rho_mean, w.noise).step(100)
+    state = b.get_state()
+    b.close()
+    c = solver_for(w, LB_FP32).set_state(state, step=100).step(100)
+    assert c.t == 200
+    assert np.array_equal(a.get_state(), c.get_state())
+    a.close()
+    c.close()
+
+
+def test_instability_is_reported():
+    """A poisoned initial field (NaN and a negative density) is caught by
+    lb_reduce with LB_ERR_UNSTABLE; the context stays usable."""
+    w = C1.with_(nx=32, ny=16)
+    n0 = noise_field(w)
+    n0[3, 5] = np.nan
+    s = solver_for(w, LB_FP32).init_fields(n0).step(3)
+    rc, _ = s.reduce()
+    assert rc == LB_ERR_UNSTABLE
+    n0 = noise_field(w)
+    n0[2, 2] = -0.5
+    s2 = solver_for(w, LB_FP32).init_fields(n0)
+    rc, _ = s2.reduce()
+    assert rc == LB_ERR_UNSTABLE
+    ok = solver_for(w, LB_FP32).init_fields(noise_field(w)).step(3)
+    assert ok.reduce()[0] == 0
+    for x in (s, s2, ok):
+        x.close()
+
+
+def test_moments_to_device_and_stream():
+    """lb_moments writes device pointers (torch tensors) on a torch stream
+    and agrees with the host path."""
+    import torch
+    from paper_1307_6703_gb300 import LB_DTYPE_F32, Solver, lb_moments
+    w = C2(0.01).with_(nx=128, ny=64)
+    st = torch.cuda.Stream()
+    s = Solver(w.nx, w.ny, precision=LB_FP32, walls=True, a=w.a, b=w.b, T=w.T, kappa=w.kappa,
+               tau=w.tau, A0=w.A0, lam=w.lam, u_bot=w.u_bot, u_top=w.u_top, N=w.N, Q=w.Q,
+               stream=st.cuda_stream)
+    s.init_noise(2, w.rho_mean, w.noise).step(20)
+    n = torch.empty((w.ny, w.nx), device="cuda", dtype=torch.float32)
+    u = torch.empty_like(n)
+    v = torch.empty_like(n)
+    lb_moments(s.h, n, u, v, LB_DTYPE_F32, 1)
+    st.synchronize()
+    hn, hu, hv = s.moments(dtype=np.float32)
+    assert np.array_equal(n.cpu().numpy(), hn) and np.array_equal(u.cpu().numpy(), hu)
+    s.close()
