@@ -157,6 +157,34 @@ int lb_get_step(const lb_handle *h, int64_t *step);
  * NULL is accepted. */
 int lb_destroy(lb_handle *h);
 
+/* Allocation-free variant of lb_reduce (the paper has no counterpart; this
+ * is a service for callers that cannot allocate device memory -- code
+ * embedded in a host application that owns the device memory budget, or a
+ * real-time loop where cudaMalloc may block).  It computes the same FP64
+ * sums as lb_reduce (total mass, x and y momentum of the populations, and
+ * the non-finite / out-of-range flag) over a caller-owned population buffer,
+ * and allocates nothing: its scratch is one partial per lattice row in a
+ * fixed device array of LB_NOALLOC_MAX_ROWS entries (32 bytes each, 512 KB
+ * in all, held by every GPU that loads the library until process exit).
+ *  f          DEVICE pointer, populations [9][ny][nx] (compact, x fastest)
+ *             of type double (LB_FP64) or float (LB_FP32)
+ *  b          van der Waals b; densities must lie in (0, 1/b) (b = 0: > 0)
+ *  out        DEVICE pointer to 3 doubles: mass, momentum x, momentum y
+ *  flag       DEVICE pointer to one int set to 1 if any site is non-finite
+ *             or outside (0, 1/b), else 0; may be NULL
+ *  stream     cudaStream_t to enqueue on (NULL = default stream)
+ * Enqueues two kernels and returns without synchronising.  The first call on
+ * a device looks up the scratch array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the one
+ * scratch array, so calls that overlap on the GPU race and must be
+ * serialised by the caller.  The row partials are summed in a fixed order,
+ * so results are deterministic; they equal lb_reduce's up to the order of
+ * FP64 additions.  Errors: LB_ERR_ARG (null pointer, bad precision,
+ * nx < 1, ny < 1 or ny > LB_NOALLOC_MAX_ROWS), LB_ERR_CUDA.                */
+#define LB_NOALLOC_MAX_ROWS 16384
+int lb_reduce_noalloc(const void *f, int precision, int32_t nx, int32_t ny, double b,
+                      double *out, int *flag, void *stream);
+
 /* Message for the last failed call on h (or for the last failed lb_create
  * when h is NULL).  The string stays valid until the next call on h.      */
 const char *lb_last_error(const lb_handle *h);

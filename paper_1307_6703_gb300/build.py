@@ -23,6 +23,7 @@ UNITS = {
     "lb_api.cu": [],
     "lb_f32.cu": [],
     "lb_f64.cu": ["--fmad=false"],
+    "lb_noalloc.cu": [],
 }
 
 

@@ -76,8 +76,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_destroy.argtypes = [P]
         lib.lb_last_error.argtypes = [P]
         lib.lb_last_error.restype = C.c_char_p
+        lib.lb_reduce_noalloc.argtypes = [P, C.c_int, C.c_int32, C.c_int32, C.c_double, P, P, P]
         for name in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_reduce",
-                     "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy"):
+                     "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy",
+                     "lb_reduce_noalloc"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -158,6 +160,17 @@ def lb_get_step(h) -> int:
 
 def lb_destroy(h) -> int:
     return load_library().lb_destroy(h)
+
+
+def lb_reduce_noalloc(f, precision: int, nx: int, ny: int, b: float, out, flag=None,
+                      stream=None) -> int:
+    """Allocation-free reduction over a caller-owned DEVICE population buffer;
+    `out` (3 doubles) and `flag` (1 int) are DEVICE buffers.  Asynchronous."""
+    rc = load_library().lb_reduce_noalloc(_addr(f), precision, nx, ny, b, _addr(out),
+                                          _addr(flag), stream)
+    if rc != LB_OK:
+        raise LBError(rc, "lb_reduce_noalloc failed")
+    return rc
 
 
 def lb_last_error(h) -> str:
