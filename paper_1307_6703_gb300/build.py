@@ -24,6 +24,7 @@ UNITS = {
     "lb_f32.cu": [],
     "lb_f64.cu": ["--fmad=false"],
     "lb_noalloc.cu": [],
+    "lb_sweep.cu": [],
 }
 
 

@@ -18,6 +18,18 @@ struct lb_handle {
   int device = 0;
   size_t S = 0;          // sites
   size_t elem = 0;       // bytes per stored population
+  // Layout of a state buffer: plane q, site (x, y) at element
+  // q * plane + off + y * pitch + x.  Compact (pitch = nx, off = 0) for the
+  // tile kernel; padded with 4 ghost columns / rows for the sweep kernel.
+  int pitch = 0;
+  long long plane = 0, off = 0;
+  bool sweep = false;            // FP32 strip-sweep kernel in use
+  CUtensorMap tmap[2];           // TMA descriptors of the two state buffers
+  size_t sweep_smem = 0;
+  int sweep_seg = 64, sweep_nstrips = 0, sweep_nseg = 0, sweep_base = 0, sweep_extra = 0;
+  double *d_cta = nullptr;       // per-CTA partials written by the sweep kernel
+  bool cta_valid = false;        // d_cta describes the current state
+  int *d_err = nullptr;          // bounded-wait failure flag
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
   void *sinx = nullptr;  // device table, storage type
@@ -60,7 +72,9 @@ StepArgs<real_t> make_args(const lb_handle *h) {
   A.nx = p.nx;
   A.ny = p.ny;
   A.walls = p.walls;
-  A.plane = h->S;
+  A.plane = (size_t)h->plane;
+  A.pitch = h->pitch;
+  A.off = h->off;
   A.T = (real_t)p.T;
   A.a = (real_t)p.a;
   A.b = (real_t)p.b;
@@ -89,16 +103,17 @@ constexpr int RED_THREADS = 256;
 // sites in FP64 (fixed order) and flags non-finite or out-of-range sites.
 template <typename real_t>
 __global__ void __launch_bounds__(RED_THREADS)
-reduce_pass1(const real_t *__restrict__ f, size_t S, double nmax, double *__restrict__ partials,
-             int *__restrict__ flag) {
+reduce_pass1(const real_t *__restrict__ f, int nx, size_t S, int pitch, long long plane,
+             long long off, double nmax, double *__restrict__ partials, int *__restrict__ flag) {
   __shared__ double sm[3][RED_THREADS];
   double m = 0.0, jx = 0.0, jy = 0.0;
   int bad = 0;
   for (size_t s = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; s < S;
        s += (size_t)gridDim.x * RED_THREADS) {
+    const long long e = off + (long long)(s / (size_t)nx) * pitch + (long long)(s % (size_t)nx);
     double v[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) v[i] = (double)f[i * S + s];
+    for (int i = 0; i < 9; i++) v[i] = (double)f[i * plane + e];
     double ms = 0.0;
 #pragma unroll
     for (int i = 0; i < 9; i++) ms += v[i];
@@ -153,7 +168,107 @@ reduce_pass2(const double *__restrict__ partials, int nblocks, double *__restric
   }
 }
 
+// Pass 2 over the sweep kernel's per-CTA records (mass, J_x, J_y, flag).
+__global__ void __launch_bounds__(RED_THREADS)
+reduce_cta(const double *__restrict__ cta, int nblocks, double *__restrict__ out, int *__restrict__ flag) {
+  __shared__ double sm[3][RED_THREADS];
+  double acc[3] = {0.0, 0.0, 0.0};
+  int bad = 0;
+  for (int b = threadIdx.x; b < nblocks; b += RED_THREADS) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) acc[c] += cta[4 * b + c];
+    if (!(cta[4 * b + 3] == 0.0)) bad = 1;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) sm[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) sm[c][threadIdx.x] += sm[c][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(flag, 1);
+  if (threadIdx.x == 0) {
+    out[0] = sm[0][0];
+    out[1] = sm[1][0];
+    out[2] = sm[2][0];
+  }
+}
+
 bool fp64(const lb_handle *h) { return h->p.precision == LB_FP64; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t make_row_map(lb_handle *h, void *base, CUtensorMap *map) {
+  static encode_tiled_fn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = (encode_tiled_fn)fn;
+  }
+  // 3D view (column, padded row, plane); one box = one row of all planes,
+  // 128 columns wide.
+  const cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)(h->p.ny + 8), 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)h->pitch * 4, (cuuint64_t)h->plane * 4};
+  const cuuint32_t box[3] = {128, 1, 9};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
+  const lb_params &p = h->p;
+  lbk::SweepArgs A;
+  A.nx = p.nx;
+  A.ny = p.ny;
+  A.walls = p.walls;
+  A.pitch = h->pitch;
+  A.plane = h->plane;
+  A.off = h->off;
+  A.seg_h = h->sweep_seg;
+  A.nseg = h->sweep_nseg;
+  A.nstrips = h->sweep_nstrips;
+  A.base_w = h->sweep_base;
+  A.extra = h->sweep_extra;
+  const double T0 = 1.0 / 3.0;
+  A.T = (float)p.T;
+  A.a = (float)p.a;
+  A.b = (float)p.b;
+  A.kappa = (float)p.kappa;
+  A.omega = (float)(1.0 / p.tau);
+  A.one_minus_omega = (float)(1.0 - 1.0 / p.tau);
+  A.g = (float)(1.0 - 1.0 / (2.0 * p.tau));
+  A.th = (float)(T0 - p.T);
+  A.A0 = (float)p.A0;
+  A.u_bot = (float)p.u_bot;
+  A.u_top = (float)p.u_top;
+  A.N = (float)p.N;
+  A.M = (float)((1.0 - 2.0 * p.N) / 4.0);
+  A.Q = (float)p.Q;
+  A.R = (float)((1.0 - p.Q) / 2.0);
+  A.four_QR = (float)(4.0 * (p.Q + (1.0 - p.Q) / 2.0));
+  const double k = (p.T - T0) / (2.0 * T0 * T0);
+  A.A_rest = (float)(1.0 + k * (0.0 - 2.0 * T0));
+  A.A_ax = (float)(1.0 + k * (1.0 - 2.0 * T0));
+  A.A_diag = (float)(1.0 + k * (2.0 - 2.0 * T0));
+  A.nmax = p.b > 0.0 ? (float)(1.0 / p.b) : 3.0e38f;
+  A.sinx = (const float *)h->sinx;
+  A.fout = fout;
+  A.partials = h->d_cta;
+  A.err = h->d_err;
+  return A;
+}
 
 }  // namespace
 
@@ -181,9 +296,37 @@ int lb_create(const lb_params *p, lb_handle **out) {
   h->st = (cudaStream_t)p->stream;
   h->S = (size_t)p->nx * (size_t)p->ny;
   h->elem = fp64(h) ? sizeof(double) : sizeof(float);
+  // The FP32 strip-sweep kernel needs x in multiples of 4 (16-byte TMA
+  // boxes) and at least 8 sites per direction (one ghost band of 4 each).
+  h->sweep = !fp64(h) && p->nx % 4 == 0 && p->nx >= 8 && p->ny >= 8;
+  if (h->sweep) {
+    h->pitch = ((p->nx + 8 + 31) / 32) * 32;
+    h->plane = (long long)h->pitch * (p->ny + 8);
+    h->off = 4LL * h->pitch + 4;
+    h->sweep_nstrips = (p->nx + 119) / 120;
+    h->sweep_base = 4 * (p->nx / (4 * h->sweep_nstrips));
+    h->sweep_extra = (p->nx - h->sweep_base * h->sweep_nstrips) / 4;
+    h->sweep_seg = p->ny < 64 ? p->ny : 64;
+    h->sweep_nseg = (p->ny + h->sweep_seg - 1) / h->sweep_seg;
+  } else {
+    h->pitch = p->nx;
+    h->plane = (long long)h->S;
+    h->off = 0;
+  }
+  const size_t buf_bytes = 9 * (size_t)h->plane * h->elem;
   cudaError_t e = cudaGetDevice(&h->device);
-  if (e == cudaSuccess) e = cudaMalloc(&h->f[0], 9 * h->S * h->elem);
-  if (e == cudaSuccess) e = cudaMalloc(&h->f[1], 9 * h->S * h->elem);
+  if (e == cudaSuccess) e = cudaMalloc(&h->f[0], buf_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->f[1], buf_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, buf_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->f[1], 0, buf_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+  if (e == cudaSuccess && h->sweep) {
+    e = cudaMalloc((void **)&h->d_cta, 4 * sizeof(double) * (size_t)h->sweep_nstrips * h->sweep_nseg);
+    if (e == cudaSuccess) e = lbk::sweep_prepare(&h->sweep_smem);
+    if (e == cudaSuccess) e = make_row_map(h, h->f[0], &h->tmap[0]);
+    if (e == cudaSuccess) e = make_row_map(h, h->f[1], &h->tmap[1]);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&h->sinx, (size_t)p->nx * h->elem);
   h->red_blocks = (int)std::min<size_t>((h->S + RED_THREADS - 1) / RED_THREADS, 1024);
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_partials, 3 * (size_t)h->red_blocks * sizeof(double));
@@ -236,11 +379,19 @@ int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean, double noise
   }
   h->cur = 0;
   cudaError_t e = fp64(h)
-                      ? lbk::launch_init((double *)h->f[0], h->p.nx, h->p.ny, mode, seed, rho_mean,
-                                         noise_amp, dr, du, dv, h->p.T, h->st)
-                      : lbk::launch_init((float *)h->f[0], h->p.nx, h->p.ny, mode, seed, rho_mean,
-                                         noise_amp, dr, du, dv, h->p.T, h->st);
+                      ? lbk::launch_init((double *)h->f[0], h->p.nx, h->p.ny, h->pitch, h->plane,
+                                         h->off, mode, seed, rho_mean, noise_amp, dr, du, dv,
+                                         h->p.T, h->st)
+                      : lbk::launch_init((float *)h->f[0], h->p.nx, h->p.ny, h->pitch, h->plane,
+                                         h->off, mode, seed, rho_mean, noise_amp, dr, du, dv,
+                                         h->p.T, h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: init kernel");
+  if (h->sweep) {
+    e = lbk::launch_ghost_fill((float *)h->f[0], h->p.nx, h->p.ny, h->pitch, h->plane, h->off,
+                               h->p.walls, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: ghost fill");
+  }
+  h->cta_valid = false;
   if (mode == 1) LB_CUDA(h, cudaStreamSynchronize(h->st));
   h->step = 0;
   h->initialised = true;
@@ -258,6 +409,15 @@ int lb_step(lb_handle *h, int64_t nsteps) {
       if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: step kernel");
       h->cur ^= 1;
       h->step++;
+    }
+  } else if (h->sweep) {
+    for (int64_t k = 0; k < nsteps; k++) {
+      const lbk::SweepArgs A = sweep_args(h, (float *)h->f[h->cur ^ 1]);
+      cudaError_t e = lbk::launch_sweep(h->tmap[h->cur], A, h->sweep_smem, h->st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: sweep kernel");
+      h->cur ^= 1;
+      h->step++;
+      h->cta_valid = true;
     }
   } else {
     const StepArgs<float> A = make_args<float>(h);
@@ -302,17 +462,29 @@ int lb_reduce(lb_handle *h, double *out) {
   if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reduce: state not initialised");
   const double nmax = h->p.b > 0.0 ? 1.0 / h->p.b : INFINITY;
   LB_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
-  if (fp64(h))
-    reduce_pass1<double><<<h->red_blocks, RED_THREADS, 0, h->st>>>((const double *)h->f[h->cur], h->S, nmax, h->d_partials, h->d_flag);
-  else
-    reduce_pass1<float><<<h->red_blocks, RED_THREADS, 0, h->st>>>((const float *)h->f[h->cur], h->S, nmax, h->d_partials, h->d_flag);
+  if (h->sweep && h->cta_valid) {
+    // The last sweep step left one record per CTA (site sums in FP32,
+    // totals in FP64): only the final pass remains.
+    reduce_cta<<<1, RED_THREADS, 0, h->st>>>(h->d_cta, h->sweep_nstrips * h->sweep_nseg, h->d_out, h->d_flag);
+  } else {
+    if (fp64(h))
+      reduce_pass1<double><<<h->red_blocks, RED_THREADS, 0, h->st>>>(
+          (const double *)h->f[h->cur], h->p.nx, h->S, h->pitch, h->plane, h->off, nmax,
+          h->d_partials, h->d_flag);
+    else
+      reduce_pass1<float><<<h->red_blocks, RED_THREADS, 0, h->st>>>(
+          (const float *)h->f[h->cur], h->p.nx, h->S, h->pitch, h->plane, h->off, nmax,
+          h->d_partials, h->d_flag);
+    LB_CUDA(h, cudaGetLastError());
+    reduce_pass2<<<1, RED_THREADS, 0, h->st>>>(h->d_partials, h->red_blocks, h->d_out);
+  }
   LB_CUDA(h, cudaGetLastError());
-  reduce_pass2<<<1, RED_THREADS, 0, h->st>>>(h->d_partials, h->red_blocks, h->d_out);
-  LB_CUDA(h, cudaGetLastError());
-  int flag = 0;
+  int flag = 0, werr = 0;
   LB_CUDA(h, cudaMemcpyAsync(out, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   LB_CUDA(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  LB_CUDA(h, cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   LB_CUDA(h, cudaStreamSynchronize(h->st));
+  if (werr) return fail(h, LB_ERR_TIMEOUT, "lb_reduce: a bounded device wait gave up during a step");
   if (flag) {
     char m[128];
     snprintf(m, sizeof m, "lb_reduce: non-finite or out-of-range density at step %lld", (long long)h->step);
@@ -333,7 +505,17 @@ int lb_get_state(lb_handle *h, void *buf, size_t *bytes) {
     return fail(h, LB_ERR_ARG, "lb_get_state: buffer too small");
   }
   if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_get_state: state not initialised");
-  LB_CUDA(h, cudaMemcpyAsync(buf, h->f[h->cur], need, cudaMemcpyDeviceToHost, h->st));
+  if (h->pitch == h->p.nx && h->off == 0 && (size_t)h->plane == h->S) {
+    LB_CUDA(h, cudaMemcpyAsync(buf, h->f[h->cur], need, cudaMemcpyDeviceToHost, h->st));
+  } else {
+    const size_t row = (size_t)h->p.nx * h->elem;
+    for (int q = 0; q < 9; q++) {
+      const char *src = (const char *)h->f[h->cur] + ((size_t)q * h->plane + h->off) * h->elem;
+      char *dst = (char *)buf + (size_t)q * h->S * h->elem;
+      LB_CUDA(h, cudaMemcpy2DAsync(dst, row, src, (size_t)h->pitch * h->elem, row, h->p.ny,
+                                   cudaMemcpyDeviceToHost, h->st));
+    }
+  }
   LB_CUDA(h, cudaStreamSynchronize(h->st));
   *bytes = need;
   return LB_OK;
@@ -344,8 +526,21 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step) {
   const size_t need = 9 * h->S * h->elem;
   if (bytes != need) return fail(h, LB_ERR_ARG, "lb_set_state: size mismatch");
   if (step < 0) return fail(h, LB_ERR_ARG, "lb_set_state: negative step");
-  LB_CUDA(h, cudaMemcpyAsync(h->f[h->cur], buf, need, cudaMemcpyHostToDevice, h->st));
+  if (h->pitch == h->p.nx && h->off == 0 && (size_t)h->plane == h->S) {
+    LB_CUDA(h, cudaMemcpyAsync(h->f[h->cur], buf, need, cudaMemcpyHostToDevice, h->st));
+  } else {
+    const size_t row = (size_t)h->p.nx * h->elem;
+    for (int q = 0; q < 9; q++) {
+      char *dst = (char *)h->f[h->cur] + ((size_t)q * h->plane + h->off) * h->elem;
+      const char *src = (const char *)buf + (size_t)q * h->S * h->elem;
+      LB_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->elem, src, row, row, h->p.ny,
+                                   cudaMemcpyHostToDevice, h->st));
+    }
+    LB_CUDA(h, lbk::launch_ghost_fill((float *)h->f[h->cur], h->p.nx, h->p.ny, h->pitch, h->plane,
+                                      h->off, h->p.walls, h->st));
+  }
   LB_CUDA(h, cudaStreamSynchronize(h->st));
+  h->cta_valid = false;
   h->step = step;
   h->initialised = true;
   return LB_OK;
@@ -368,6 +563,8 @@ int lb_destroy(lb_handle *h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_flag);
   cudaFree(h->d_out);
+  cudaFree(h->d_cta);
+  cudaFree(h->d_err);
   delete h;
   return LB_OK;
 }

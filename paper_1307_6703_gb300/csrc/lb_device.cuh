@@ -36,7 +36,9 @@ struct Consts {
 template <typename real_t>
 struct StepArgs {
   int nx, ny, walls;
-  size_t plane;         // nx * ny
+  size_t plane;         // element stride between population planes
+  int pitch;            // element stride between rows
+  long long off;        // element offset of site (0, 0) within a plane
   real_t T, a, b, kappa, omega /* 1/tau */, g /* 1 - 1/(2 tau) */, th /* T0 - T */;
   real_t A0, u_bot, u_top;
   real_t N, M, Q, R, four_QR /* 4 (Q + R) */;
@@ -151,12 +153,12 @@ __device__ __forceinline__ void pull9(const real_t *__restrict__ fin, const Step
   const int ym = (y == 0) ? (wl ? -1 : A.ny - 1) : y - 1;
   const int yp = (y == A.ny - 1) ? (wl ? -1 : 0) : y + 1;
   const size_t P = A.plane;
-  const size_t r0 = (size_t)y * A.nx;
+  const size_t r0 = (size_t)(A.off + (long long)y * A.pitch);
   f[0] = fin[0 * P + r0 + x];
   f[1] = fin[1 * P + r0 + xm];
   f[3] = fin[3 * P + r0 + xp];
   if (ym >= 0) {
-    const size_t rm = (size_t)ym * A.nx;
+    const size_t rm = (size_t)(A.off + (long long)ym * A.pitch);
     f[2] = fin[2 * P + rm + x];
     f[5] = fin[5 * P + rm + xm];
     f[6] = fin[6 * P + rm + xp];
@@ -164,7 +166,7 @@ __device__ __forceinline__ void pull9(const real_t *__restrict__ fin, const Step
     f[2] = f[5] = f[6] = real_t(0);
   }
   if (yp >= 0) {
-    const size_t rp = (size_t)yp * A.nx;
+    const size_t rp = (size_t)(A.off + (long long)yp * A.pitch);
     f[4] = fin[4 * P + rp + x];
     f[7] = fin[7 * P + rp + xp];
     f[8] = fin[8 * P + rp + xm];
@@ -327,7 +329,7 @@ tile_step_kernel(const real_t *__restrict__ fin, real_t *__restrict__ fout,
     real_t fe[9], Fi[9];
     feq9(n, ux, uy, A.T, fe);
     forcing9(A.g, A.th, ux, uy, Fx, Fy, dnx, dny, divJ, Fi);
-    const size_t s = (size_t)gy * nx + gx;
+    const size_t s = (size_t)(A.off + (long long)gy * A.pitch + gx);
 #pragma unroll
     for (int i = 0; i < 9; i++) fout[i * A.plane + s] = (f[i] - A.omega * (f[i] - fe[i])) + Fi[i];
     }
@@ -346,10 +348,10 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
 
 // f*_i = f_i^eq(n0, u0) evaluated in FP64, stored as real_t.
 template <typename real_t>
-__global__ void init_kernel(real_t *__restrict__ f, int nx, int ny, int mode, uint64_t seed,
-                            double rho_mean, double amp, const double *__restrict__ rho0,
-                            const double *__restrict__ ux0, const double *__restrict__ uy0,
-                            double T) {
+__global__ void init_kernel(real_t *__restrict__ f, int nx, int ny, int pitch, long long plane,
+                            long long off, int mode, uint64_t seed, double rho_mean, double amp,
+                            const double *__restrict__ rho0, const double *__restrict__ ux0,
+                            const double *__restrict__ uy0, double T) {
   const size_t S = (size_t)nx * ny;
   for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < S;
        s += (size_t)gridDim.x * blockDim.x) {
@@ -364,8 +366,10 @@ __global__ void init_kernel(real_t *__restrict__ f, int nx, int ny, int mode, ui
     }
     double fe[9];
     feq9<double>(n0, u, v, T, fe);
+    const long long y = (long long)(s / (size_t)nx), x = (long long)(s % (size_t)nx);
+    const long long e = off + y * pitch + x;
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i * S + s] = (real_t)fe[i];
+    for (int i = 0; i < 9; i++) f[i * plane + e] = (real_t)fe[i];
   }
 }
 

@@ -25,12 +25,12 @@ cudaError_t launch_moments(const float *fin, const StepArgs<float> &A, void *n, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_init(float *f, int nx, int ny, int mode, uint64_t seed, double rho_mean,
+cudaError_t launch_init(float *f, int nx, int ny, int pitch, long long plane, long long off, int mode, uint64_t seed, double rho_mean,
                         double amp, const double *rho0, const double *ux0, const double *uy0,
                         double T, cudaStream_t st) {
   const size_t S = (size_t)nx * ny;
   const unsigned blocks = (unsigned)((S + 255) / 256 < 4096 ? (S + 255) / 256 : 4096);
-  init_kernel<float><<<blocks, 256, 0, st>>>(f, nx, ny, mode, seed, rho_mean, amp, rho0, ux0, uy0, T);
+  init_kernel<float><<<blocks, 256, 0, st>>>(f, nx, ny, pitch, plane, off, mode, seed, rho_mean, amp, rho0, ux0, uy0, T);
   return cudaGetLastError();
 }
 

@@ -94,7 +94,22 @@ def test_fp64_config_64x32_2000_steps():
     s.close()
 
 
-@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}")
+# Lattices that take the FP32 strip-sweep kernel (nx % 4 == 0, nx, ny >= 8):
+# one and several strips and segments, ragged strip widths and segment tails.
+# At T = 0.9 T_c the quench amplifies FP32 rounding (max relative density
+# error ~2e-6 at step 40, ~1.3e-5 at step 80 for both FP32 kernels), so these
+# run 40 steps.
+SWEEP = [
+    (8, 8, True, 0.02, 40),
+    (8, 8, False, 0.0, 40),
+    (124, 9, False, 0.0, 40),
+    (248, 67, True, 0.04, 40),
+    (300, 130, True, 0.05, 40),
+    (300, 130, False, 0.0, 40),
+]
+
+
+@pytest.mark.parametrize("case", SMALL + SWEEP, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}")
 def test_fp32_small_lattices(case):
     w = small_workload(*case)
     n0 = noise_field(w)

@@ -40,8 +40,12 @@ def test_noalloc_reduce_matches_lb_reduce_twice(prec_name):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert int(flag.item()) == 0, call
-        assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0]), (call, got, ref)
-        scale = max(abs(ref[0]) * 1e-12, 1e-9)
+        # FP64 states: both sums are FP64 throughout.  FP32 states: lb_reduce
+        # reads the per-CTA records of the FP32 step kernel, whose site sums
+        # are formed in FP32 (relative accuracy ~1e-7 per site).
+        rtol = 1e-12 if prec == LB_FP64 else 2e-6
+        assert abs(got[0] - ref[0]) <= rtol * abs(ref[0]), (call, got, ref)
+        scale = max(abs(ref[0]) * rtol, 1e-9)
         assert abs(got[1] - ref[1]) <= scale and abs(got[2] - ref[2]) <= scale, (call, got, ref)
 
 
