@@ -199,34 +199,6 @@ reduce_cta(const double *__restrict__ cta, int nblocks, double *__restrict__ out
 
 bool fp64(const lb_handle *h) { return h->p.precision == LB_FP64; }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point.
-typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-cudaError_t make_row_map(lb_handle *h, void *base, CUtensorMap *map) {
-  static encode_tiled_fn encode = nullptr;
-  if (!encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                     cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    encode = (encode_tiled_fn)fn;
-  }
-  // 3D view (column, padded row, plane); one box = one row of all planes,
-  // 128 columns wide.
-  const cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)(h->p.ny + 8), 9};
-  const cuuint64_t strides[2] = {(cuuint64_t)h->pitch * 4, (cuuint64_t)h->plane * 4};
-  const cuuint32_t box[3] = {128, 1, 9};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   const lb_params &p = h->p;
   lbk::SweepArgs A;
@@ -324,8 +296,8 @@ int lb_create(const lb_params *p, lb_handle **out) {
   if (e == cudaSuccess && h->sweep) {
     e = cudaMalloc((void **)&h->d_cta, 4 * sizeof(double) * (size_t)h->sweep_nstrips * h->sweep_nseg);
     if (e == cudaSuccess) e = lbk::sweep_prepare(&h->sweep_smem);
-    if (e == cudaSuccess) e = make_row_map(h, h->f[0], &h->tmap[0]);
-    if (e == cudaSuccess) e = make_row_map(h, h->f[1], &h->tmap[1]);
+    if (e == cudaSuccess) e = lbk::sweep_make_map(h->f[0], h->pitch, p->ny, h->plane, &h->tmap[0]);
+    if (e == cudaSuccess) e = lbk::sweep_make_map(h->f[1], h->pitch, p->ny, h->plane, &h->tmap[1]);
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->sinx, (size_t)p->nx * h->elem);
   h->red_blocks = (int)std::min<size_t>((h->S + RED_THREADS - 1) / RED_THREADS, 1024);

@@ -29,6 +29,9 @@ struct SweepArgs {
 };
 
 cudaError_t sweep_prepare(size_t *smem_bytes);
+// TMA descriptor of one padded FP32 state buffer, with the box the sweep
+// kernel's ring expects (built next to the kernel so the two cannot differ).
+cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUtensorMap *map);
 cudaError_t launch_sweep(const CUtensorMap &tin, const SweepArgs &A, size_t smem, cudaStream_t st);
 cudaError_t launch_ghost_fill(float *f, int nx, int ny, int pitch, long long plane, long long off,
                               int walls, cudaStream_t st);

@@ -3,21 +3,23 @@
 // shared memory by TMA.
 //
 // Work decomposition.  The lattice is cut into column strips of W <= 120
-// interior columns and row segments of up to SEG rows.  One CTA (128
-// threads, one thread per column of a 128-column window x0-4 .. x0+123)
-// sweeps its segment upwards, one row per iteration.  Every row of the
-// previous state is read from HBM once by the TMA engine: a 3D tensor copy
-// brings the 128-column row of all nine population planes into a ring of
-// RING rows in shared memory (mbarrier-tracked), RING-7 rows ahead of use.
+// interior columns and row segments of up to SEG rows.  One CTA (256
+// threads: two warp groups, one per row of a row pair, each with one thread
+// per column of a 128-column window x0-4 .. x0+123) sweeps its segment
+// upwards, two rows per iteration.  Every row of the previous state is read
+// from HBM once by the TMA engine: a 3D tensor copy brings a pair of
+// 128-column rows of all nine population planes into a ring of six pairs in
+// shared memory (mbarrier-tracked), two pairs ahead of use.
 //
-// Per iteration r four stages run, separated by CTA barriers:
-//   A  row r    : propagated populations (pull), density n (n-hat on walls),
-//                 raw momentum sum_i f_i c_i                 -> ring n[5]
-//   B  row r-1  : P = p^i - p^w (Eq. eqstate) and L = lap n   -> ring P,L[3]
-//   C  row r-2  : F = dP + kappa n dL + F_ext (Eq. force2), n u* (Eq. newvel),
-//                 wall rule on wall rows                       -> ring J[3]
-//   D  row r-3  : grad n, div(n u*), equilibrium (Eq. eqfunc), forcing
-//                 (Eqs. forceterm, coeff), BGK collision; store f* to HBM.
+// Iteration k (a = ya - 3 + 2k) runs four stages, separated by CTA barriers,
+// each on two rows:
+//   A  rows a, a+1     : propagated populations (pull), density n (n-hat on
+//                        walls), raw momentum sum_i f_i c_i      -> n ring
+//   B  rows a-1, a     : P = p^i - p^w (Eq. eqstate), L = lap n  -> P/L ring
+//   C  rows a-2, a-1   : F = dP + kappa n dL + F_ext (Eq. force2), n u*
+//                        (Eq. newvel), wall rule on wall rows   -> J/F ring
+//   D  rows a-3, a-2   : grad n, div(n u*), equilibrium (Eq. eqfunc), forcing
+//                        (Eqs. forceterm, coeff), BGK collision; store f*.
 // Column halos (3, 2, 1 sites for n, P/L, F/J) are computed by the edge
 // threads of the window; row halos come from the sweep itself, so apart from
 // the 7-row warm-up of each segment nothing is recomputed.
@@ -47,20 +49,26 @@ namespace lbk {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kCols = 128;
-constexpr int kRing = 10;
-constexpr unsigned kRowBytes = 9u * kCols * sizeof(float);
+constexpr int kCols = 128;                 // TMA box width (columns x0-4 .. x0+123)
+constexpr int kPairs = 6;                  // population ring, in pairs of rows
+constexpr int kThreads = 256;              // warps 0-3: first row of a pair, 4-7: second
+constexpr int kPairFloats = 9 * 2 * kCols;  // one pair of rows of all nine planes
+constexpr unsigned kPairBytes = kPairFloats * sizeof(float);
 constexpr uint32_t kWaitLimit = 1u << 22;
 
+// Rings of row pairs.  A row y belongs to pair (y - y0) / 2 of a ring with
+// origin y0: populations y0 = ya - 4, density ya - 3, P/L ya - 4, n u* and
+// force ya - 5, chosen so that iteration k writes pair k of every ring.
 struct __align__(128) SweepSmem {
-  float pops[kRing][9][kCols];
-  float n[5][kCols];
-  float P[3][kCols];
-  float L[3][kCols];
-  float Jx[3][kCols];
-  float Jy[3][kCols];
-  unsigned long long full[kRing];
+  float pops[kPairs][9][2][kCols];
+  float n[3][2][kCols];
+  float P[2][2][kCols];
+  float L[2][2][kCols];
+  float Jx[2][2][kCols];
+  float Jy[2][2][kCols];
+  float Fx[2][2][kCols];
+  float Fy[2][2][kCols];
+  unsigned long long full[kPairs];
   double red[4][kThreads / 32];
 };
 
@@ -89,10 +97,10 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *er
   atomicOr(err, 1);
 }
 
-// One row (all nine planes, 128 columns) of the padded state into a ring slot.
-__device__ __forceinline__ void tma_row(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad,
-                                        int ypad) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kRowBytes)
+// Two rows (all nine planes, 128 columns) of the padded state into a ring slot.
+__device__ __forceinline__ void tma_pair(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad,
+                                         int ypad) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kPairBytes)
                : "memory");
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -101,22 +109,27 @@ __device__ __forceinline__ void tma_row(const CUtensorMap *map, uint32_t dst, ui
       : "memory");
 }
 
-__device__ __forceinline__ int mirror_row(int y, int ny, int walls) {
-  if (!walls) return y;
-  if (y < 0) return -y;
-  if (y > ny - 1) return 2 * (ny - 1) - y;
-  return y;
+__device__ __forceinline__ int dec(int s, int n) { return s == 0 ? n - 1 : s - 1; }
+__device__ __forceinline__ int inc(int s, int n) { return s == n - 1 ? 0 : s + 1; }
+
+// Row j (0, 1, 2 = r-1, r, r+1) of the three rows centred on this thread's
+// row, in a ring of pairs whose pairs `lo` and `hi` hold them.
+__device__ __forceinline__ const float *row_in(const float *ring, int pair_floats, int row_floats,
+                                               int lo, int hi, int g, int j) {
+  const int q = g + j;
+  return ring + (q >> 1 ? hi : lo) * pair_floats + (q & 1) * row_floats;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
 sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
   extern __shared__ unsigned char smem_raw[];
   SweepSmem &S = *reinterpret_cast<SweepSmem *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
 
-  const int t = threadIdx.x;
+  const int t = threadIdx.x & (kCols - 1);
+  const int g = threadIdx.x >> 7;  // row within the pair
   const int strip = blockIdx.x, seg = blockIdx.y;
   const int x0 = strip * A.base_w + 4 * min(strip, A.extra);
   const int W = A.base_w + (strip < A.extra ? 4 : 0);
@@ -125,148 +138,172 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
   const int nx = A.nx, ny = A.ny;
   const bool walls = A.walls != 0;
   const int x = x0 - 4 + t;  // interior column of this thread (may be a halo column)
-  const int xw = x < 0 ? x + nx : (x >= nx ? x - nx : x);
   const bool actA = t >= 1 && t <= W + 6;
   const bool actB = t >= 2 && t <= W + 5;
   const bool actC = t >= 3 && t <= W + 4;
   const bool actD = t >= 4 && t <= W + 3;
-  const int nload = (yb - ya) + 8;  // rows ya-4 .. yb+3
-  const float sinx = actC ? A.sinx[xw] : 0.f;  // x in [x0-1, x0+W] for stage C
+  const int kmax = (yb - ya + 5) >> 1;  // last iteration
+  const int npairs = kmax + 2;          // rows ya-4 .. ya+2*kmax+3
+  float sinx = 0.f;
+  if (actC) sinx = A.sinx[x < 0 ? x + nx : (x >= nx ? x - nx : x)];
 
-  if (t == 0) {
-    for (int s = 0; s < kRing; ++s) mbar_init(smem_u32(&S.full[s]));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int L = 0; L < min(kRing, nload); ++L)
-      tma_row(&tin, smem_u32(&S.pops[L][0][0]), smem_u32(&S.full[L]), x0, ya + L);
+    for (int P = 0; P < min(kPairs, npairs); ++P)
+      tma_pair(&tin, smem_u32(&S.pops[P][0][0][0]), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
   __syncthreads();
   mbar_wait(smem_u32(&S.full[0]), 0, A.err);
-  mbar_wait(smem_u32(&S.full[1]), 0, A.err);
 
-  // ring slots (all row arguments are >= ya - 4)
-  auto pslot = [&](int y) { return (y - ya + 4) % kRing; };
-  auto nslot = [&](int y) { return (y - ya + 10) % 5; };
-  auto tslot = [&](int y) { return (y - ya + 12) % 3; };
-
-  float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f, sx2 = 0.f, sy2 = 0.f;
-  float Fx_cur = 0.f, Fy_cur = 0.f, Fx_prev = 0.f, Fy_prev = 0.f;
+  const float *pops = &S.pops[0][0][0][0];
+  constexpr int PF = kPairFloats, PR = 2 * kCols;  // pair / plane strides in pops
+  float sx_prev = 0.f, sy_prev = 0.f;
   float acc_m = 0.f, acc_x = 0.f, acc_y = 0.f;
   int bad = 0;
+  // ring slots of pair k (and neighbours) for the rings of 6, 3 and 2 pairs
+  int s6 = 0, s3 = 0;
 
-  for (int r = ya - 3; r <= yb + 2; ++r) {
-    const int i = r - (ya - 3);
+  for (int k = 0; k <= kmax; ++k) {
+    const int s6m1 = dec(s6, kPairs), s6m2 = dec(s6m1, kPairs), s6p1 = inc(s6, kPairs);
+    const int s3m1 = dec(s3, 3), s3m2 = dec(s3m1, 3);
+    const int s2 = k & 1, s2m1 = s2 ^ 1;
     {
-      const int Lw = i + 2;  // newest row needed by this iteration
-      mbar_wait(smem_u32(&S.full[Lw % kRing]), (Lw / kRing) & 1, A.err);
+      const int P = k + 1;  // newest pair needed by this iteration
+      mbar_wait(smem_u32(&S.full[s6p1]), (P / kPairs) & 1, A.err);
     }
-    const int rA = r, rB = r - 1, rC = r - 2, rD = r - 3;
+    const int a = ya - 3 + 2 * k;
+    const int rA = a + g, rB = a - 1 + g, rC = a - 2 + g, rD = a - 3 + g;
 
     // ------------------------------------------------ A: density, raw momentum
-    sx2 = sx1; sy2 = sy1; sx1 = sx0; sy1 = sy0;
+    float sx_new = 0.f, sy_new = 0.f;
     if (actA && (!walls || (rA >= 0 && rA <= ny - 1))) {
-      const float(*pm)[kCols] = S.pops[pslot(rA - 1)];
-      const float(*p0)[kCols] = S.pops[pslot(rA)];
-      const float(*pp)[kCols] = S.pops[pslot(rA + 1)];
-      const float f0 = p0[0][t], f1 = p0[1][t - 1], f3 = p0[3][t + 1];
-      const float f2 = pm[2][t], f5 = pm[5][t - 1], f6 = pm[6][t + 1];
-      const float f4 = pp[4][t], f7 = pp[7][t + 1], f8 = pp[8][t - 1];
+      const float *pm = row_in(pops, PF, kCols, s6, s6p1, g, 0);
+      const float *p0 = row_in(pops, PF, kCols, s6, s6p1, g, 1);
+      const float *pp = row_in(pops, PF, kCols, s6, s6p1, g, 2);
+      const float f0 = p0[0 * PR + t], f1 = p0[1 * PR + t - 1], f3 = p0[3 * PR + t + 1];
+      const float f2 = pm[2 * PR + t], f5 = pm[5 * PR + t - 1], f6 = pm[6 * PR + t + 1];
+      const float f4 = pp[4 * PR + t], f7 = pp[7 * PR + t + 1], f8 = pp[8 * PR + t - 1];
       float n;
       if (walls && rA == 0) {
-        n = p0[0][t] + p0[4][t] + p0[7][t] + p0[8][t] + f1 + f3 + f4 + f7 + f8;
+        n = p0[0 * PR + t] + p0[4 * PR + t] + p0[7 * PR + t] + p0[8 * PR + t] + f1 + f3 + f4 + f7 + f8;
       } else if (walls && rA == ny - 1) {
-        n = p0[0][t] + p0[2][t] + p0[6][t] + p0[5][t] + f1 + f3 + f2 + f6 + f5;
+        n = p0[0 * PR + t] + p0[2 * PR + t] + p0[6 * PR + t] + p0[5 * PR + t] + f1 + f3 + f2 + f6 + f5;
       } else {
         n = (((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7))) + f8;
-        sx0 = ((f1 - f3) + (f5 - f6)) + (f8 - f7);
-        sy0 = ((f2 - f4) + (f5 + f6)) - (f7 + f8);
+        sx_new = ((f1 - f3) + (f5 - f6)) + (f8 - f7);
+        sy_new = ((f2 - f4) + (f5 + f6)) - (f7 + f8);
       }
-      S.n[nslot(rA)][t] = n;
+      S.n[s3][g][t] = n;
     }
     __syncthreads();
-    // The slot of row L = i - 4 is free now (last used by iteration i - 1).
-    if (t == 0 && i >= 4 && i - 4 + kRing < nload) {
-      const int L = i - 4 + kRing;
-      tma_row(&tin, smem_u32(&S.pops[L % kRing][0][0]), smem_u32(&S.full[L % kRing]), x0, ya + L);
+    // The slot of pair k-3 is free (last used by iteration k-1): refill it.
+    if (threadIdx.x == 0 && k >= 3 && k + 3 < npairs) {
+      const int P = k + 3;  // slot (k+3) % 6 == (k-3) % 6
+      tma_pair(&tin, smem_u32(pops + dec(s6m2, kPairs) * PF), smem_u32(&S.full[dec(s6m2, kPairs)]), x0,
+               ya + 2 * P);
     }
 
-    // ------------------------------------------------ B: P and lap n
+    // ------------------------------------------------ B: P = p^i - p^w, L = lap n
     if (actB && rB >= ya - 2 && (!walls || (rB >= 0 && rB <= ny - 1))) {
-      const float *nm = S.n[nslot(mirror_row(rB - 1, ny, A.walls))];
-      const float *n0 = S.n[nslot(rB)];
-      const float *np = S.n[nslot(mirror_row(rB + 1, ny, A.walls))];
+      const float *nr = &S.n[0][0][0];
+      const float *nm = row_in(nr, 2 * kCols, kCols, s3m1, s3, g, 0);
+      const float *n0 = row_in(nr, 2 * kCols, kCols, s3m1, s3, g, 1);
+      const float *np = row_in(nr, 2 * kCols, kCols, s3m1, s3, g, 2);
+      if (walls && rB == 0) nm = np;
+      if (walls && rB == ny - 1) np = nm;
       const float c = n0[t];
       const float lap = A.Q * ((n0[t + 1] + n0[t - 1]) + (np[t] + nm[t])) +
                         A.R * ((np[t + 1] + np[t - 1]) + (nm[t + 1] + nm[t - 1])) - A.four_QR * c;
       const float nT = c * A.T;
       const float pw = nT * __frcp_rn(1.0f - A.b * c) - A.a * c * c;
-      S.P[tslot(rB)][t] = nT - pw;
-      S.L[tslot(rB)][t] = lap;
+      S.P[s2][g][t] = nT - pw;
+      S.L[s2][g][t] = lap;
     }
     __syncthreads();
 
     // ------------------------------------------------ C: force and n u*
-    Fx_prev = Fx_cur;
-    Fy_prev = Fy_cur;
     if (actC && rC >= ya - 1 && (!walls || (rC >= 0 && rC <= ny - 1))) {
-      const int sm = tslot(mirror_row(rC - 1, ny, A.walls));
-      const int s0 = tslot(rC);
-      const int sp = tslot(mirror_row(rC + 1, ny, A.walls));
-      const float *Pm = S.P[sm], *P0 = S.P[s0], *Pp = S.P[sp];
-      const float *Lm = S.L[sm], *L0 = S.L[s0], *Lp = S.L[sp];
+      const float *Pr = &S.P[0][0][0], *Lr = &S.L[0][0][0];
+      const float *Pm = row_in(Pr, 2 * kCols, kCols, s2m1, s2, g, 0);
+      const float *P0 = row_in(Pr, 2 * kCols, kCols, s2m1, s2, g, 1);
+      const float *Pp = row_in(Pr, 2 * kCols, kCols, s2m1, s2, g, 2);
+      const float *Lm = row_in(Lr, 2 * kCols, kCols, s2m1, s2, g, 0);
+      const float *L0 = row_in(Lr, 2 * kCols, kCols, s2m1, s2, g, 1);
+      const float *Lp = row_in(Lr, 2 * kCols, kCols, s2m1, s2, g, 2);
+      if (walls && rC == 0) { Pm = Pp; Lm = Lp; }
+      if (walls && rC == ny - 1) { Pp = Pm; Lp = Lm; }
       const float dPx = A.N * (P0[t + 1] - P0[t - 1]) + A.M * ((Pp[t + 1] - Pp[t - 1]) + (Pm[t + 1] - Pm[t - 1]));
       const float dPy = A.N * (Pp[t] - Pm[t]) + A.M * ((Pp[t + 1] - Pm[t + 1]) + (Pp[t - 1] - Pm[t - 1]));
       const float dLx = A.N * (L0[t + 1] - L0[t - 1]) + A.M * ((Lp[t + 1] - Lp[t - 1]) + (Lm[t + 1] - Lm[t - 1]));
       const float dLy = A.N * (Lp[t] - Lm[t]) + A.M * ((Lp[t + 1] - Lm[t + 1]) + (Lp[t - 1] - Lm[t - 1]));
-      const float n = S.n[nslot(rC)][t];
+      // density of row rC: pair k-1 (+g) of the density ring
+      const float n = S.n[s3m1][g][t];  // row rC: pair k-1, row g of the density ring
       const float kn = A.kappa * n;
-      Fx_cur = (dPx + kn * dLx) + A.A0 * sinx;
-      Fy_cur = dPy + kn * dLy;
-      float sx = sx2, sy = sy2;
+      const float Fx = (dPx + kn * dLx) + A.A0 * sinx;
+      const float Fy = dPy + kn * dLy;
+      float sx = sx_prev, sy = sy_prev;
       if (walls && (rC == 0 || rC == ny - 1)) {
-        const float(*pm)[kCols] = S.pops[pslot(rC - 1)];
-        const float(*p0)[kCols] = S.pops[pslot(rC)];
-        const float(*pp)[kCols] = S.pops[pslot(rC + 1)];
+        const float *pm = row_in(pops, PF, kCols, s6m1, s6, g, 0);
+        const float *p0 = row_in(pops, PF, kCols, s6m1, s6, g, 1);
+        const float *pp = row_in(pops, PF, kCols, s6m1, s6, g, 2);
         float f[9];
-        f[0] = p0[0][t]; f[1] = p0[1][t - 1]; f[3] = p0[3][t + 1];
-        f[2] = pm[2][t]; f[5] = pm[5][t - 1]; f[6] = pm[6][t + 1];
-        f[4] = pp[4][t]; f[7] = pp[7][t + 1]; f[8] = pp[8][t - 1];
+        f[0] = p0[0 * PR + t]; f[1] = p0[1 * PR + t - 1]; f[3] = p0[3 * PR + t + 1];
+        f[2] = pm[2 * PR + t]; f[5] = pm[5 * PR + t - 1]; f[6] = pm[6 * PR + t + 1];
+        f[4] = pp[4 * PR + t]; f[7] = pp[7 * PR + t + 1]; f[8] = pp[8 * PR + t - 1];
         const bool top = rC != 0;
-        wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx_cur, Fy_cur, n, f);
+        wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
         sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
         sy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
       }
-      S.Jx[s0][t] = sx + 0.5f * Fx_cur;
-      S.Jy[s0][t] = sy + 0.5f * Fy_cur;
+      S.Jx[s2][g][t] = sx + 0.5f * Fx;
+      S.Jy[s2][g][t] = sy + 0.5f * Fy;
+      S.Fx[s2][g][t] = Fx;
+      S.Fy[s2][g][t] = Fy;
     }
+    sx_prev = sx_new;
+    sy_prev = sy_new;
     __syncthreads();
 
     // ------------------------------------------------ D: collide and store
-    if (actD && rD >= ya) {
+    if (actD && rD >= ya && rD < yb) {
       const bool bot_wall = walls && rD == 0, top_wall = walls && rD == ny - 1;
-      const int mrm = mirror_row(rD - 1, ny, A.walls), mrp = mirror_row(rD + 1, ny, A.walls);
-      const float *nm = S.n[nslot(mrm)], *n0 = S.n[nslot(rD)], *np = S.n[nslot(mrp)];
+      const float *nr = &S.n[0][0][0];
+      const float *nm = row_in(nr, 2 * kCols, kCols, s3m2, s3m1, g, 0);
+      const float *n0 = row_in(nr, 2 * kCols, kCols, s3m2, s3m1, g, 1);
+      const float *np = row_in(nr, 2 * kCols, kCols, s3m2, s3m1, g, 2);
+      const float *Xr = &S.Jx[0][0][0], *Yr = &S.Jy[0][0][0];
+      const float *Xm = row_in(Xr, 2 * kCols, kCols, s2m1, s2, g, 0);
+      const float *X0 = row_in(Xr, 2 * kCols, kCols, s2m1, s2, g, 1);
+      const float *Xp = row_in(Xr, 2 * kCols, kCols, s2m1, s2, g, 2);
+      const float *Ym = row_in(Yr, 2 * kCols, kCols, s2m1, s2, g, 0);
+      const float *Y0 = row_in(Yr, 2 * kCols, kCols, s2m1, s2, g, 1);
+      const float *Yp = row_in(Yr, 2 * kCols, kCols, s2m1, s2, g, 2);
+      float sgm = 1.f, sgp = 1.f;  // J_y is odd across a wall
+      if (bot_wall) { nm = np; Xm = Xp; Ym = Yp; sgm = -1.f; }
+      if (top_wall) { np = nm; Xp = Xm; Yp = Ym; sgp = -1.f; }
       const float n = n0[t];
       const float dnx = A.N * (n0[t + 1] - n0[t - 1]) + A.M * ((np[t + 1] - np[t - 1]) + (nm[t + 1] - nm[t - 1]));
       const float dny = A.N * (np[t] - nm[t]) + A.M * ((np[t + 1] - nm[t + 1]) + (np[t - 1] - nm[t - 1]));
-      const int jm = tslot(mrm), j0 = tslot(rD), jp = tslot(mrp);
-      const float sgm = (walls && rD == 0) ? -1.f : 1.f;       // J_y is odd across a wall
-      const float sgp = (walls && rD == ny - 1) ? -1.f : 1.f;
-      const float *Xm = S.Jx[jm], *X0 = S.Jx[j0], *Xp = S.Jx[jp];
-      const float *Ym = S.Jy[jm], *Y0 = S.Jy[j0], *Yp = S.Jy[jp];
       const float dJx = A.N * (X0[t + 1] - X0[t - 1]) + A.M * ((Xp[t + 1] - Xp[t - 1]) + (Xm[t + 1] - Xm[t - 1]));
       const float dJy = A.N * (sgp * Yp[t] - sgm * Ym[t]) +
                         A.M * ((sgp * Yp[t + 1] - sgm * Ym[t + 1]) + (sgp * Yp[t - 1] - sgm * Ym[t - 1]));
       const float divJ = dJx + dJy;
       const float Jx = X0[t], Jy = Y0[t];
-      const float Fx = Fx_prev, Fy = Fy_prev;
+      const float Fx = S.Fx[g ? s2 : s2m1][g ? 0 : 1][t];
+      const float Fy = S.Fy[g ? s2 : s2m1][g ? 0 : 1][t];
 
-      const float(*pm)[kCols] = S.pops[pslot(rD - 1)];
-      const float(*p0)[kCols] = S.pops[pslot(rD)];
-      const float(*pp)[kCols] = S.pops[pslot(rD + 1)];
+      // rows rD-1 .. rD+1 lie one row above the pair grid of the population
+      // ring: pairs (k-2, k-1) for the first row of a pair, (k-1, k) for the
+      // second, entered at the opposite row.
+      const int dlo = g ? s6m1 : s6m2, dhi = g ? s6 : s6m1;
+      const float *pm = row_in(pops, PF, kCols, dlo, dhi, 1 - g, 0);
+      const float *p0 = row_in(pops, PF, kCols, dlo, dhi, 1 - g, 1);
+      const float *pp = row_in(pops, PF, kCols, dlo, dhi, 1 - g, 2);
       float f[9];
-      f[0] = p0[0][t]; f[1] = p0[1][t - 1]; f[3] = p0[3][t + 1];
-      f[2] = pm[2][t]; f[5] = pm[5][t - 1]; f[6] = pm[6][t + 1];
-      f[4] = pp[4][t]; f[7] = pp[7][t + 1]; f[8] = pp[8][t - 1];
+      f[0] = p0[0 * PR + t]; f[1] = p0[1 * PR + t - 1]; f[3] = p0[3 * PR + t + 1];
+      f[2] = pm[2 * PR + t]; f[5] = pm[5 * PR + t - 1]; f[6] = pm[6 * PR + t + 1];
+      f[4] = pp[4 * PR + t]; f[7] = pp[7 * PR + t + 1]; f[8] = pp[8 * PR + t - 1];
       if (bot_wall || top_wall) wall_fill<float>(top_wall, top_wall ? A.u_top : A.u_bot, Fx, Fy, n, f);
 
       const float rn = __frcp_rn(n);
@@ -328,6 +365,8 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
       acc_x += jx;
       acc_y += jy;
     }
+    s6 = s6p1;
+    s3 = inc(s3, 3);
   }
 
   // CTA partial sums of the stored state (FP64, fixed order).
@@ -335,11 +374,11 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
 #pragma unroll
   for (int c = 0; c < 4; ++c)
     for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-  if ((t & 31) == 0)
+  if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) S.red[c][t >> 5] = v[c];
+    for (int c = 0; c < 4; ++c) S.red[c][threadIdx.x >> 5] = v[c];
   __syncthreads();
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     double *out = A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -369,6 +408,35 @@ __global__ void ghost_fill_kernel(float *f, int nx, int ny, int pitch, long long
     const int sy = y < 0 ? y + ny : (y >= ny ? y - ny : y);
     f[q * plane + off + (long long)y * pitch + x] = f[q * plane + off + (long long)sy * pitch + sx];
   }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point.
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUtensorMap *map) {
+  static encode_tiled_fn encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = (encode_tiled_fn)fn;
+  }
+  // 3D view (column, padded row, plane).  One box = the ring slot: kCols
+  // columns x 2 rows x 9 planes, kPairBytes in all.
+  const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ny + 8), 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)plane * 4};
+  const cuuint32_t box[3] = {kCols, 2, 9};
+  static_assert(kCols * 2 * 9 * sizeof(float) == kPairBytes, "TMA box must fill one ring slot");
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t sweep_prepare(size_t *smem_bytes) {
