@@ -270,16 +270,14 @@ int lb_create(const lb_params *p, lb_handle **out) {
   h->elem = fp64(h) ? sizeof(double) : sizeof(float);
   // The FP32 strip-sweep kernel needs x in multiples of 4 (16-byte TMA
   // boxes) and at least 8 sites per direction (one ghost band of 4 each).
-  h->sweep = !fp64(h) && p->nx % 4 == 0 && p->nx >= 8 && p->ny >= 8;
+  h->sweep = !fp64(h) && p->nx % 4 == 0 && p->nx >= 8 && p->ny >= 8 &&
+             9.0 * (double)(((p->nx + 8 + 31) / 32) * 32) * (double)(p->ny + 8) < 2147483647.0;
   if (h->sweep) {
     h->pitch = ((p->nx + 8 + 31) / 32) * 32;
     h->plane = (long long)h->pitch * (p->ny + 8);
     h->off = 4LL * h->pitch + 4;
-    h->sweep_nstrips = (p->nx + 119) / 120;
-    h->sweep_base = 4 * (p->nx / (4 * h->sweep_nstrips));
-    h->sweep_extra = (p->nx - h->sweep_base * h->sweep_nstrips) / 4;
-    h->sweep_seg = p->ny < 64 ? p->ny : 64;
-    h->sweep_nseg = (p->ny + h->sweep_seg - 1) / h->sweep_seg;
+    lbk::sweep_plan(p->nx, p->ny, &h->sweep_nstrips, &h->sweep_base, &h->sweep_extra, &h->sweep_seg,
+                    &h->sweep_nseg);
   } else {
     h->pitch = p->nx;
     h->plane = (long long)h->S;
@@ -456,7 +454,7 @@ int lb_reduce(lb_handle *h, double *out) {
   LB_CUDA(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   LB_CUDA(h, cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   LB_CUDA(h, cudaStreamSynchronize(h->st));
-  if (werr) return fail(h, LB_ERR_TIMEOUT, "lb_reduce: a bounded device wait gave up during a step");
+  if (werr) return fail(h, LB_ERR_TIMEOUT, "lb_reduce: a device-side wait gave up or a layout check failed during a step");
   if (flag) {
     char m[128];
     snprintf(m, sizeof m, "lb_reduce: non-finite or out-of-range density at step %lld", (long long)h->step);

@@ -29,6 +29,9 @@ struct SweepArgs {
 };
 
 cudaError_t sweep_prepare(size_t *smem_bytes);
+// Strips (widths base_w or base_w + 4; the first `extra` are wider) and
+// row segments of the sweep kernel for an nx x ny lattice.
+void sweep_plan(int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg);
 // TMA descriptor of one padded FP32 state buffer, with the box the sweep
 // kernel's ring expects (built next to the kernel so the two cannot differ).
 cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUtensorMap *map);

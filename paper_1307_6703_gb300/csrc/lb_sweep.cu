@@ -40,6 +40,8 @@
 // Every CTA also writes FP64 partial sums of mass and momentum of the state
 // it stored, and a flag for non-finite or out-of-range sites, so that the
 // global reduction of the new state costs one tiny kernel.
+#include <cstddef>
+
 #include <cuda.h>
 
 #include "lb_device.cuh"
@@ -49,28 +51,38 @@ namespace lbk {
 
 namespace {
 
-constexpr int kCols = 128;                 // TMA box width (columns x0-4 .. x0+123)
-constexpr int kPairs = 6;                  // population ring, in pairs of rows
-constexpr int kThreads = 256;              // warps 0-3: first row of a pair, 4-7: second
+constexpr int kCols = 124;                  // TMA box width (columns x0-4 .. x0+119)
+constexpr int kMaxW = kCols - 8;            // interior columns per strip
+constexpr int kPairs = 5;                   // population ring, in pairs of rows
+constexpr int kThreads = kCols;             // one thread per window column
+constexpr int kSeg = 64;                    // rows per segment
 constexpr int kPairFloats = 9 * 2 * kCols;  // one pair of rows of all nine planes
 constexpr unsigned kPairBytes = kPairFloats * sizeof(float);
+// Ring slots start on 128-byte boundaries (TMA destination alignment).
+constexpr int kSlotFloats = ((kPairFloats * 4 + 127) / 128) * 128 / 4;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // Rings of row pairs.  A row y belongs to pair (y - y0) / 2 of a ring with
-// origin y0: populations y0 = ya - 4, density ya - 3, P/L ya - 4, n u* and
-// force ya - 5, chosen so that iteration k writes pair k of every ring.
+// origin y0: populations y0 = ya - 4, density ya - 3, P/L ya - 4, n u*
+// ya - 5, chosen so that iteration k writes pair k of every ring.
 struct __align__(128) SweepSmem {
-  float pops[kPairs][9][2][kCols];
+  float pops[kPairs][kSlotFloats];  // [slot][plane][row of pair][column] + padding
   float n[3][2][kCols];
   float P[2][2][kCols];
   float L[2][2][kCols];
   float Jx[2][2][kCols];
   float Jy[2][2][kCols];
-  float Fx[2][2][kCols];
-  float Fy[2][2][kCols];
   unsigned long long full[kPairs];
-  double red[4][kThreads / 32];
 };
+static_assert(sizeof(float) * kPairs * kSlotFloats >= sizeof(double) * 4 * kThreads,
+              "the end-of-kernel reduction reuses the population ring");
+static_assert((kSlotFloats * sizeof(float)) % 128 == 0, "TMA destinations must be 128-byte aligned");
+static_assert(offsetof(SweepSmem, pops) == 0, "the ring starts the (128-byte aligned) block");
+
+// Row r (0 or 1) of a ring slot; plane q of that row starts q * 2 * kCols later.
+__device__ __forceinline__ const float *pop_row(const SweepSmem &S, int slot, int r) {
+  return &S.pops[slot][r * kCols];
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -97,7 +109,7 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *er
   atomicOr(err, 1);
 }
 
-// Two rows (all nine planes, 128 columns) of the padded state into a ring slot.
+// Two rows (all nine planes, kCols columns) of the padded state into a slot.
 __device__ __forceinline__ void tma_pair(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad,
                                          int ypad) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kPairBytes)
@@ -112,24 +124,74 @@ __device__ __forceinline__ void tma_pair(const CUtensorMap *map, uint32_t dst, u
 __device__ __forceinline__ int dec(int s, int n) { return s == 0 ? n - 1 : s - 1; }
 __device__ __forceinline__ int inc(int s, int n) { return s == n - 1 ? 0 : s + 1; }
 
-// Row j (0, 1, 2 = r-1, r, r+1) of the three rows centred on this thread's
-// row, in a ring of pairs whose pairs `lo` and `hi` hold them.
-__device__ __forceinline__ const float *row_in(const float *ring, int pair_floats, int row_floats,
-                                               int lo, int hi, int g, int j) {
-  const int q = g + j;
-  return ring + (q >> 1 ? hi : lo) * pair_floats + (q & 1) * row_floats;
+// x-derivative, y-derivative and Laplacian stencils of Eqs. (xstencil,
+// laplstencil) at column t of row r1, rows r0 = y-1 and r2 = y+1.
+struct Sten {
+  float N, M, Q, R, four_QR;
+};
+__device__ __forceinline__ float sdx(const Sten &s, const float *r0, const float *r1, const float *r2, int t) {
+  return s.N * (r1[t + 1] - r1[t - 1]) + s.M * ((r2[t + 1] - r2[t - 1]) + (r0[t + 1] - r0[t - 1]));
+}
+__device__ __forceinline__ float sdy(const Sten &s, const float *r0, const float *r2, int t) {
+  return s.N * (r2[t] - r0[t]) + s.M * ((r2[t + 1] - r0[t + 1]) + (r2[t - 1] - r0[t - 1]));
+}
+__device__ __forceinline__ float slap(const Sten &s, const float *r0, const float *r1, const float *r2, int t) {
+  return s.Q * ((r1[t + 1] + r1[t - 1]) + (r2[t] + r0[t])) +
+         s.R * ((r2[t + 1] + r2[t - 1]) + (r0[t + 1] + r0[t - 1])) - s.four_QR * r1[t];
+}
+
+// Propagated populations of the site in column t of row r1 (pull).
+__device__ __forceinline__ void pull(const float *r0, const float *r1, const float *r2, int t, float *f) {
+  constexpr int PR = 2 * kCols;  // plane stride inside a ring slot
+  f[0] = r1[0 * PR + t]; f[1] = r1[1 * PR + t - 1]; f[3] = r1[3 * PR + t + 1];
+  f[2] = r0[2 * PR + t]; f[5] = r0[5 * PR + t - 1]; f[6] = r0[6 * PR + t + 1];
+  f[4] = r2[4 * PR + t]; f[7] = r2[7 * PR + t + 1]; f[8] = r2[8 * PR + t - 1];
+}
+
+// One collision (Eqs. evoleq, eqfunc, forceterm, coeff) in the moment form
+//   f*_i = (1 - omega) f_i + w_i E_i,
+//   E_i = omega n [A_i + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2] + 3 c.B + 9/2 C:cc - 3/2 tr C,
+// with the rest population taken as n minus the other eight.
+__device__ __forceinline__ void collide(const SweepArgs &A, const float *f, float n, float Jx, float Jy,
+                                        float Fx, float Fy, float dnx, float dny, float divJ, float *fs) {
+  const float rn = __fdividef(1.0f, n);
+  const float ux = Jx * rn, uy = Jy * rn;
+  const float Bx = A.g * Fx, By = A.g * Fy;
+  const float Cxx = A.g * (2.f * ux * Fx + A.th * (2.f * ux * dnx + divJ));
+  const float Cyy = A.g * (2.f * uy * Fy + A.th * (2.f * uy * dny + divJ));
+  const float Cxy = A.g * ((ux * Fy + Fx * uy) + A.th * (ux * dny + uy * dnx));
+  const float trC = Cxx + Cyy;
+  const float on = A.omega * n;
+  const float base = -1.5f * (on * (ux * ux + uy * uy) + trC);
+  const float e_ax = on * A.A_ax + base, e_dg = on * A.A_diag + base;
+  const float symx = 4.5f * (on * ux * ux + Cxx), antx = 3.f * (on * ux + Bx);
+  const float symy = 4.5f * (on * uy * uy + Cyy), anty = 3.f * (on * uy + By);
+  const float vp = ux + uy, vm = uy - ux;
+  const float sym5 = 4.5f * (on * vp * vp + trC + 2.f * Cxy), ant5 = 3.f * (on * vp + (Bx + By));
+  const float sym6 = 4.5f * (on * vm * vm + trC - 2.f * Cxy), ant6 = 3.f * (on * vm + (By - Bx));
+  const float om1 = A.one_minus_omega;
+  constexpr float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+  fs[1] = om1 * f[1] + w1 * (e_ax + symx + antx);
+  fs[3] = om1 * f[3] + w1 * (e_ax + symx - antx);
+  fs[2] = om1 * f[2] + w1 * (e_ax + symy + anty);
+  fs[4] = om1 * f[4] + w1 * (e_ax + symy - anty);
+  fs[5] = om1 * f[5] + w5 * (e_dg + sym5 + ant5);
+  fs[7] = om1 * f[7] + w5 * (e_dg + sym5 - ant5);
+  fs[6] = om1 * f[6] + w5 * (e_dg + sym6 + ant6);
+  fs[8] = om1 * f[8] + w5 * (e_dg + sym6 - ant6);
+  // Collision conserves the site's mass exactly (A = 0, sum f^eq = n); the
+  // remainder form keeps rounded weights from biasing the mass.
+  fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 4)
 sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
-  extern __shared__ unsigned char smem_raw[];
-  SweepSmem &S = *reinterpret_cast<SweepSmem *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SweepSmem &S = *reinterpret_cast<SweepSmem *>(smem_raw);
 
-  const int t = threadIdx.x & (kCols - 1);
-  const int g = threadIdx.x >> 7;  // row within the pair
+  const int t = threadIdx.x;
   const int strip = blockIdx.x, seg = blockIdx.y;
   const int x0 = strip * A.base_w + 4 * min(strip, A.extra);
   const int W = A.base_w + (strip < A.extra ? 4 : 0);
@@ -144,247 +206,220 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
   const bool actD = t >= 4 && t <= W + 3;
   const int kmax = (yb - ya + 5) >> 1;  // last iteration
   const int npairs = kmax + 2;          // rows ya-4 .. ya+2*kmax+3
+  const Sten st{A.N, A.M, A.Q, A.R, A.four_QR};
   float sinx = 0.f;
   if (actC) sinx = A.sinx[x < 0 ? x + nx : (x >= nx ? x - nx : x)];
+  float *col = A.fout + A.off + x;  // f* of this column at interior row 0
+  const int pitch = A.pitch, plane = (int)A.plane;
+  const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);  // periodic image column
 
-  if (threadIdx.x == 0) {
+  // TMA writes need 128-byte aligned destinations: refuse to run otherwise.
+  if (smem_u32(&S.pops[0][0]) & 127u) {
+    if (t == 0) atomicOr(A.err, 2);
+    return;
+  }
+  if (t == 0) {
     for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int P = 0; P < min(kPairs, npairs); ++P)
-      tma_pair(&tin, smem_u32(&S.pops[P][0][0][0]), smem_u32(&S.full[P]), x0, ya + 2 * P);
+      tma_pair(&tin, smem_u32(pop_row(S, P, 0)), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
   __syncthreads();
   mbar_wait(smem_u32(&S.full[0]), 0, A.err);
 
-  const float *pops = &S.pops[0][0][0][0];
-  constexpr int PF = kPairFloats, PR = 2 * kCols;  // pair / plane strides in pops
-  float sx_prev = 0.f, sy_prev = 0.f;
+  float sxa[2] = {0.f, 0.f}, sya[2] = {0.f, 0.f};  // raw momentum of rows a-2, a-1 (from last A)
+  float Fx_prev = 0.f, Fy_prev = 0.f;              // force of row a-3 (from last C)
   float acc_m = 0.f, acc_x = 0.f, acc_y = 0.f;
   int bad = 0;
-  // ring slots of pair k (and neighbours) for the rings of 6, 3 and 2 pairs
-  int s6 = 0, s3 = 0;
+  int s5 = 0, s3 = 0;
+  uint32_t par = 0;  // phase parity of pair k+1
 
   for (int k = 0; k <= kmax; ++k) {
-    const int s6m1 = dec(s6, kPairs), s6m2 = dec(s6m1, kPairs), s6p1 = inc(s6, kPairs);
+    const int s5m1 = dec(s5, kPairs), s5m2 = dec(s5m1, kPairs), s5p1 = inc(s5, kPairs);
     const int s3m1 = dec(s3, 3), s3m2 = dec(s3m1, 3);
     const int s2 = k & 1, s2m1 = s2 ^ 1;
-    {
-      const int P = k + 1;  // newest pair needed by this iteration
-      mbar_wait(smem_u32(&S.full[s6p1]), (P / kPairs) & 1, A.err);
-    }
+    mbar_wait(smem_u32(&S.full[s5p1]), par, A.err);  // newest pair needed: k+1
+    if (s5p1 == kPairs - 1) par ^= 1u;
     const int a = ya - 3 + 2 * k;
-    const int rA = a + g, rB = a - 1 + g, rC = a - 2 + g, rD = a - 3 + g;
 
-    // ------------------------------------------------ A: density, raw momentum
-    float sx_new = 0.f, sy_new = 0.f;
-    if (actA && (!walls || (rA >= 0 && rA <= ny - 1))) {
-      const float *pm = row_in(pops, PF, kCols, s6, s6p1, g, 0);
-      const float *p0 = row_in(pops, PF, kCols, s6, s6p1, g, 1);
-      const float *pp = row_in(pops, PF, kCols, s6, s6p1, g, 2);
-      const float f0 = p0[0 * PR + t], f1 = p0[1 * PR + t - 1], f3 = p0[3 * PR + t + 1];
-      const float f2 = pm[2 * PR + t], f5 = pm[5 * PR + t - 1], f6 = pm[6 * PR + t + 1];
-      const float f4 = pp[4 * PR + t], f7 = pp[7 * PR + t + 1], f8 = pp[8 * PR + t - 1];
-      float n;
-      if (walls && rA == 0) {
-        n = p0[0 * PR + t] + p0[4 * PR + t] + p0[7 * PR + t] + p0[8 * PR + t] + f1 + f3 + f4 + f7 + f8;
-      } else if (walls && rA == ny - 1) {
-        n = p0[0 * PR + t] + p0[2 * PR + t] + p0[6 * PR + t] + p0[5 * PR + t] + f1 + f3 + f2 + f6 + f5;
-      } else {
-        n = (((f0 + f1) + (f2 + f3)) + ((f4 + f5) + (f6 + f7))) + f8;
-        sx_new = ((f1 - f3) + (f5 - f6)) + (f8 - f7);
-        sy_new = ((f2 - f4) + (f5 + f6)) - (f7 + f8);
-      }
-      S.n[s3][g][t] = n;
-    }
-    __syncthreads();
-    // The slot of pair k-3 is free (last used by iteration k-1): refill it.
-    if (threadIdx.x == 0 && k >= 3 && k + 3 < npairs) {
-      const int P = k + 3;  // slot (k+3) % 6 == (k-3) % 6
-      tma_pair(&tin, smem_u32(pops + dec(s6m2, kPairs) * PF), smem_u32(&S.full[dec(s6m2, kPairs)]), x0,
-               ya + 2 * P);
-    }
-
-    // ------------------------------------------------ B: P = p^i - p^w, L = lap n
-    if (actB && rB >= ya - 2 && (!walls || (rB >= 0 && rB <= ny - 1))) {
-      const float *nr = &S.n[0][0][0];
-      const float *nm = row_in(nr, 2 * kCols, kCols, s3m1, s3, g, 0);
-      const float *n0 = row_in(nr, 2 * kCols, kCols, s3m1, s3, g, 1);
-      const float *np = row_in(nr, 2 * kCols, kCols, s3m1, s3, g, 2);
-      if (walls && rB == 0) nm = np;
-      if (walls && rB == ny - 1) np = nm;
-      const float c = n0[t];
-      const float lap = A.Q * ((n0[t + 1] + n0[t - 1]) + (np[t] + nm[t])) +
-                        A.R * ((np[t + 1] + np[t - 1]) + (nm[t + 1] + nm[t - 1])) - A.four_QR * c;
-      const float nT = c * A.T;
-      const float pw = nT * __frcp_rn(1.0f - A.b * c) - A.a * c * c;
-      S.P[s2][g][t] = nT - pw;
-      S.L[s2][g][t] = lap;
-    }
-    __syncthreads();
-
-    // ------------------------------------------------ C: force and n u*
-    if (actC && rC >= ya - 1 && (!walls || (rC >= 0 && rC <= ny - 1))) {
-      const float *Pr = &S.P[0][0][0], *Lr = &S.L[0][0][0];
-      const float *Pm = row_in(Pr, 2 * kCols, kCols, s2m1, s2, g, 0);
-      const float *P0 = row_in(Pr, 2 * kCols, kCols, s2m1, s2, g, 1);
-      const float *Pp = row_in(Pr, 2 * kCols, kCols, s2m1, s2, g, 2);
-      const float *Lm = row_in(Lr, 2 * kCols, kCols, s2m1, s2, g, 0);
-      const float *L0 = row_in(Lr, 2 * kCols, kCols, s2m1, s2, g, 1);
-      const float *Lp = row_in(Lr, 2 * kCols, kCols, s2m1, s2, g, 2);
-      if (walls && rC == 0) { Pm = Pp; Lm = Lp; }
-      if (walls && rC == ny - 1) { Pp = Pm; Lp = Lm; }
-      const float dPx = A.N * (P0[t + 1] - P0[t - 1]) + A.M * ((Pp[t + 1] - Pp[t - 1]) + (Pm[t + 1] - Pm[t - 1]));
-      const float dPy = A.N * (Pp[t] - Pm[t]) + A.M * ((Pp[t + 1] - Pm[t + 1]) + (Pp[t - 1] - Pm[t - 1]));
-      const float dLx = A.N * (L0[t + 1] - L0[t - 1]) + A.M * ((Lp[t + 1] - Lp[t - 1]) + (Lm[t + 1] - Lm[t - 1]));
-      const float dLy = A.N * (Lp[t] - Lm[t]) + A.M * ((Lp[t + 1] - Lm[t + 1]) + (Lp[t - 1] - Lm[t - 1]));
-      // density of row rC: pair k-1 (+g) of the density ring
-      const float n = S.n[s3m1][g][t];  // row rC: pair k-1, row g of the density ring
-      const float kn = A.kappa * n;
-      const float Fx = (dPx + kn * dLx) + A.A0 * sinx;
-      const float Fy = dPy + kn * dLy;
-      float sx = sx_prev, sy = sy_prev;
-      if (walls && (rC == 0 || rC == ny - 1)) {
-        const float *pm = row_in(pops, PF, kCols, s6m1, s6, g, 0);
-        const float *p0 = row_in(pops, PF, kCols, s6m1, s6, g, 1);
-        const float *pp = row_in(pops, PF, kCols, s6m1, s6, g, 2);
-        float f[9];
-        f[0] = p0[0 * PR + t]; f[1] = p0[1 * PR + t - 1]; f[3] = p0[3 * PR + t + 1];
-        f[2] = pm[2 * PR + t]; f[5] = pm[5 * PR + t - 1]; f[6] = pm[6 * PR + t + 1];
-        f[4] = pp[4 * PR + t]; f[7] = pp[7 * PR + t + 1]; f[8] = pp[8 * PR + t - 1];
-        const bool top = rC != 0;
-        wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
-        sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
-        sy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
-      }
-      S.Jx[s2][g][t] = sx + 0.5f * Fx;
-      S.Jy[s2][g][t] = sy + 0.5f * Fy;
-      S.Fx[s2][g][t] = Fx;
-      S.Fy[s2][g][t] = Fy;
-    }
-    sx_prev = sx_new;
-    sy_prev = sy_new;
-    __syncthreads();
-
-    // ------------------------------------------------ D: collide and store
-    if (actD && rD >= ya && rD < yb) {
-      const bool bot_wall = walls && rD == 0, top_wall = walls && rD == ny - 1;
-      const float *nr = &S.n[0][0][0];
-      const float *nm = row_in(nr, 2 * kCols, kCols, s3m2, s3m1, g, 0);
-      const float *n0 = row_in(nr, 2 * kCols, kCols, s3m2, s3m1, g, 1);
-      const float *np = row_in(nr, 2 * kCols, kCols, s3m2, s3m1, g, 2);
-      const float *Xr = &S.Jx[0][0][0], *Yr = &S.Jy[0][0][0];
-      const float *Xm = row_in(Xr, 2 * kCols, kCols, s2m1, s2, g, 0);
-      const float *X0 = row_in(Xr, 2 * kCols, kCols, s2m1, s2, g, 1);
-      const float *Xp = row_in(Xr, 2 * kCols, kCols, s2m1, s2, g, 2);
-      const float *Ym = row_in(Yr, 2 * kCols, kCols, s2m1, s2, g, 0);
-      const float *Y0 = row_in(Yr, 2 * kCols, kCols, s2m1, s2, g, 1);
-      const float *Yp = row_in(Yr, 2 * kCols, kCols, s2m1, s2, g, 2);
-      float sgm = 1.f, sgp = 1.f;  // J_y is odd across a wall
-      if (bot_wall) { nm = np; Xm = Xp; Ym = Yp; sgm = -1.f; }
-      if (top_wall) { np = nm; Xp = Xm; Yp = Ym; sgp = -1.f; }
-      const float n = n0[t];
-      const float dnx = A.N * (n0[t + 1] - n0[t - 1]) + A.M * ((np[t + 1] - np[t - 1]) + (nm[t + 1] - nm[t - 1]));
-      const float dny = A.N * (np[t] - nm[t]) + A.M * ((np[t + 1] - nm[t + 1]) + (np[t - 1] - nm[t - 1]));
-      const float dJx = A.N * (X0[t + 1] - X0[t - 1]) + A.M * ((Xp[t + 1] - Xp[t - 1]) + (Xm[t + 1] - Xm[t - 1]));
-      const float dJy = A.N * (sgp * Yp[t] - sgm * Ym[t]) +
-                        A.M * ((sgp * Yp[t + 1] - sgm * Ym[t + 1]) + (sgp * Yp[t - 1] - sgm * Ym[t - 1]));
-      const float divJ = dJx + dJy;
-      const float Jx = X0[t], Jy = Y0[t];
-      const float Fx = S.Fx[g ? s2 : s2m1][g ? 0 : 1][t];
-      const float Fy = S.Fy[g ? s2 : s2m1][g ? 0 : 1][t];
-
-      // rows rD-1 .. rD+1 lie one row above the pair grid of the population
-      // ring: pairs (k-2, k-1) for the first row of a pair, (k-1, k) for the
-      // second, entered at the opposite row.
-      const int dlo = g ? s6m1 : s6m2, dhi = g ? s6 : s6m1;
-      const float *pm = row_in(pops, PF, kCols, dlo, dhi, 1 - g, 0);
-      const float *p0 = row_in(pops, PF, kCols, dlo, dhi, 1 - g, 1);
-      const float *pp = row_in(pops, PF, kCols, dlo, dhi, 1 - g, 2);
-      float f[9];
-      f[0] = p0[0 * PR + t]; f[1] = p0[1 * PR + t - 1]; f[3] = p0[3 * PR + t + 1];
-      f[2] = pm[2 * PR + t]; f[5] = pm[5 * PR + t - 1]; f[6] = pm[6 * PR + t + 1];
-      f[4] = pp[4 * PR + t]; f[7] = pp[7 * PR + t + 1]; f[8] = pp[8 * PR + t - 1];
-      if (bot_wall || top_wall) wall_fill<float>(top_wall, top_wall ? A.u_top : A.u_bot, Fx, Fy, n, f);
-
-      const float rn = __frcp_rn(n);
-      const float ux = Jx * rn, uy = Jy * rn;
-      // Guo coefficients B = g F, C (Eq. coeff with (T0 - T))
-      const float Bx = A.g * Fx, By = A.g * Fy;
-      const float Cxx = A.g * (2.f * ux * Fx + A.th * (2.f * ux * dnx + divJ));
-      const float Cyy = A.g * (2.f * uy * Fy + A.th * (2.f * uy * dny + divJ));
-      const float Cxy = A.g * ((ux * Fy + Fx * uy) + A.th * (ux * dny + uy * dnx));
-      const float trC = Cxx + Cyy;
-      const float on = A.omega * n;
-      const float base = -1.5f * (on * (ux * ux + uy * uy) + trC);
-      const float e_ax = on * A.A_ax + base, e_dg = on * A.A_diag + base;
-      const float symx = 4.5f * (on * ux * ux + Cxx), antx = 3.f * (on * ux + Bx);
-      const float symy = 4.5f * (on * uy * uy + Cyy), anty = 3.f * (on * uy + By);
-      const float vp = ux + uy, vm = uy - ux;
-      const float sym5 = 4.5f * (on * vp * vp + trC + 2.f * Cxy), ant5 = 3.f * (on * vp + (Bx + By));
-      const float sym6 = 4.5f * (on * vm * vm + trC - 2.f * Cxy), ant6 = 3.f * (on * vm + (By - Bx));
-      const float om1 = A.one_minus_omega;
-      constexpr float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-      float fs[9];
-      fs[1] = om1 * f[1] + w1 * (e_ax + symx + antx);
-      fs[3] = om1 * f[3] + w1 * (e_ax + symx - antx);
-      fs[2] = om1 * f[2] + w1 * (e_ax + symy + anty);
-      fs[4] = om1 * f[4] + w1 * (e_ax + symy - anty);
-      fs[5] = om1 * f[5] + w5 * (e_dg + sym5 + ant5);
-      fs[7] = om1 * f[7] + w5 * (e_dg + sym5 - ant5);
-      fs[6] = om1 * f[6] + w5 * (e_dg + sym6 + ant6);
-      fs[8] = om1 * f[8] + w5 * (e_dg + sym6 - ant6);
-      // Collision conserves the site's mass exactly (A = 0 in Eq. forceterm,
-      // sum f^eq = n): take the rest population as the remainder, so that
-      // rounded weights cannot bias the total mass step after step.
-      fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
-
-      const long long idx = A.off + (long long)rD * A.pitch + x;
+    // ---------------------------------------- A: rows a, a+1 -- n, raw momentum
+    {
+      const float *q0 = pop_row(S, s5, 0), *q1 = pop_row(S, s5, 1);    // rows a-1, a
+      const float *q2 = pop_row(S, s5p1, 0), *q3 = pop_row(S, s5p1, 1);  // rows a+1, a+2
+      float sx_new[2] = {0.f, 0.f}, sy_new[2] = {0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < 9; ++q) A.fout[q * A.plane + idx] = fs[q];
-      // periodic images in the ghost band
-      const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);
-      const int gy = walls ? 0 : ((rD < 4) ? ny : ((rD >= ny - 4) ? -ny : 0));
-      if (gx != 0) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) A.fout[q * A.plane + idx + gx] = fs[q];
-      }
-      if (gy != 0) {
-        const long long iy = idx + (long long)gy * A.pitch;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) A.fout[q * A.plane + iy] = fs[q];
-        if (gx != 0) {
-#pragma unroll
-          for (int q = 0; q < 9; ++q) A.fout[q * A.plane + iy + gx] = fs[q];
+      for (int j = 0; j < 2; ++j) {
+        const int y = a + j;
+        const float *r0 = j ? q1 : q0, *r1 = j ? q2 : q1, *r2 = j ? q3 : q2;
+        if (actA && (!walls || (y >= 0 && y <= ny - 1))) {
+          float f[9];
+          pull(r0, r1, r2, t, f);
+          float n;
+          constexpr int PR = 2 * kCols;
+          if (walls && y == 0) {
+            n = r1[0 * PR + t] + r1[4 * PR + t] + r1[7 * PR + t] + r1[8 * PR + t] + f[1] + f[3] + f[4] + f[7] + f[8];
+          } else if (walls && y == ny - 1) {
+            n = r1[0 * PR + t] + r1[2 * PR + t] + r1[6 * PR + t] + r1[5 * PR + t] + f[1] + f[3] + f[2] + f[6] + f[5];
+          } else {
+            n = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+            sx_new[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
+            sy_new[j] = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+          }
+          S.n[s3][j][t] = n;
         }
       }
-      const float m = (((fs[0] + fs[1]) + (fs[2] + fs[3])) + ((fs[4] + fs[5]) + (fs[6] + fs[7]))) + fs[8];
-      const float jx = ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
-      const float jy = ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
-      if (!(m > 0.f && m < A.nmax) || !isfinite(jx) || !isfinite(jy)) bad = 1;
-      acc_m += m;
-      acc_x += jx;
-      acc_y += jy;
+      __syncthreads();
+      // The slot of pair k-3 is free (last used by iteration k-1): refill it
+      // with pair k+2.
+      if (t == 0 && k >= 3 && k + 2 < npairs) {
+        const int slot = dec(s5m2, kPairs);
+        tma_pair(&tin, smem_u32(pop_row(S, slot, 0)), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
+      }
+
+      // -------------------------------------- B: rows a-1, a -- P, lap n
+      {
+        const float *n0 = S.n[s3m1][0], *n1 = S.n[s3m1][1];  // rows a-2, a-1
+        const float *n2 = S.n[s3][0], *n3 = S.n[s3][1];      // rows a, a+1
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int y = a - 1 + j;
+          const float *r0 = j ? n1 : n0, *r1 = j ? n2 : n1, *r2 = j ? n3 : n2;
+          if (actB && y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1))) {
+            if (walls && y == 0) r0 = r2;
+            if (walls && y == ny - 1) r2 = r0;
+            const float c = r1[t];
+            const float nT = c * A.T;
+            const float pw = nT * __fdividef(1.0f, 1.0f - A.b * c) - A.a * c * c;
+            S.P[s2][j][t] = nT - pw;
+            S.L[s2][j][t] = slap(st, r0, r1, r2, t);
+          }
+        }
+      }
+      __syncthreads();
+
+      // -------------------------------------- C: rows a-2, a-1 -- F, n u*
+      float Fx_cur[2] = {0.f, 0.f}, Fy_cur[2] = {0.f, 0.f};
+      {
+        const float *P0 = S.P[s2m1][0], *P1 = S.P[s2m1][1], *P2 = S.P[s2][0], *P3 = S.P[s2][1];
+        const float *L0 = S.L[s2m1][0], *L1 = S.L[s2m1][1], *L2 = S.L[s2][0], *L3 = S.L[s2][1];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int y = a - 2 + j;
+          if (!(actC && y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1)))) continue;
+          const float *p0 = j ? P1 : P0, *p1 = j ? P2 : P1, *p2 = j ? P3 : P2;
+          const float *l0 = j ? L1 : L0, *l1 = j ? L2 : L1, *l2 = j ? L3 : L2;
+          if (walls && y == 0) { p0 = p2; l0 = l2; }
+          if (walls && y == ny - 1) { p2 = p0; l2 = l0; }
+          const float n = S.n[s3m1][j][t];
+          const float kn = A.kappa * n;
+          const float Fx = (sdx(st, p0, p1, p2, t) + kn * sdx(st, l0, l1, l2, t)) + A.A0 * sinx;
+          const float Fy = sdy(st, p0, p2, t) + kn * sdy(st, l0, l2, t);
+          float sx = sxa[j], sy = sya[j];
+          if (walls && (y == 0 || y == ny - 1)) {
+            // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
+            const float *w0 = pop_row(S, s5m1, 0), *w1 = pop_row(S, s5m1, 1);
+            const float *w2 = pop_row(S, s5, 0), *w3 = pop_row(S, s5, 1);
+            float f[9];
+            pull(j ? w1 : w0, j ? w2 : w1, j ? w3 : w2, t, f);
+            const bool top = y != 0;
+            wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
+            sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
+            sy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+          }
+          S.Jx[s2][j][t] = sx + 0.5f * Fx;
+          S.Jy[s2][j][t] = sy + 0.5f * Fy;
+          Fx_cur[j] = Fx;
+          Fy_cur[j] = Fy;
+        }
+      }
+      sxa[0] = sx_new[0]; sxa[1] = sx_new[1];
+      sya[0] = sy_new[0]; sya[1] = sy_new[1];
+      __syncthreads();
+
+      // -------------------------------------- D: rows a-3, a-2 -- collide, store
+      {
+        const float *n0 = S.n[s3m2][0], *n1 = S.n[s3m2][1], *n2 = S.n[s3m1][0], *n3 = S.n[s3m1][1];
+        const float *X0 = S.Jx[s2m1][0], *X1 = S.Jx[s2m1][1], *X2 = S.Jx[s2][0], *X3 = S.Jx[s2][1];
+        const float *Y0 = S.Jy[s2m1][0], *Y1 = S.Jy[s2m1][1], *Y2 = S.Jy[s2][0], *Y3 = S.Jy[s2][1];
+        // population rows a-4 .. a-1: pair k-2 row 1, pair k-1 rows 0, 1, pair k row 0
+        const float *q0p = pop_row(S, s5m2, 1), *q1p = pop_row(S, s5m1, 0);
+        const float *q2p = pop_row(S, s5m1, 1), *q3p = pop_row(S, s5, 0);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int y = a - 3 + j;
+          if (!(actD && y >= ya && y < yb)) continue;
+          const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
+          const float *x0p = j ? X1 : X0, *x1p = j ? X2 : X1, *x2p = j ? X3 : X2;
+          const float *y0p = j ? Y1 : Y0, *y1p = j ? Y2 : Y1, *y2p = j ? Y3 : Y2;
+          const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
+          const bool bot = walls && y == 0, top = walls && y == ny - 1;
+          float dJy;
+          if (bot || top) {
+            // mirror rows across the wall: n and J_x even, J_y odd
+            float sgm = 1.f, sgp = 1.f;
+            if (bot) { m0 = m2; x0p = x2p; y0p = y2p; sgm = -1.f; }
+            if (top) { m2 = m0; x2p = x0p; y2p = y0p; sgp = -1.f; }
+            dJy = st.N * (sgp * y2p[t] - sgm * y0p[t]) +
+                  st.M * ((sgp * y2p[t + 1] - sgm * y0p[t + 1]) + (sgp * y2p[t - 1] - sgm * y0p[t - 1]));
+          } else {
+            dJy = sdy(st, y0p, y2p, t);
+          }
+          const float n = m1[t];
+          const float dnx = sdx(st, m0, m1, m2, t), dny = sdy(st, m0, m2, t);
+          const float divJ = sdx(st, x0p, x1p, x2p, t) + dJy;
+          const float Jx = x1p[t], Jy = y1p[t];
+          float f[9], fs[9];
+          pull(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f);
+          if (bot || top) wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
+          collide(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs);
+
+          float *o = col + (long long)y * pitch;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) o[q * plane] = fs[q];
+          const int gy = walls ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
+          if (gx != 0) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) o[q * plane + gx] = fs[q];
+          }
+          if (gy != 0) {
+            float *oy = o + (long long)gy * pitch;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) oy[q * plane] = fs[q];
+            if (gx != 0) {
+#pragma unroll
+              for (int q = 0; q < 9; ++q) oy[q * plane + gx] = fs[q];
+            }
+          }
+          // Mass and momentum of the stored site: sum f* = n (by
+          // construction), sum f* c = n u* + F/2 (identity of the collision).
+          if (!(n > 0.f && n < A.nmax && fabsf(Jx) + fabsf(Jy) < 3.0e38f)) bad = 1;
+          acc_m += n;
+          acc_x += Jx + 0.5f * Fx;
+          acc_y += Jy + 0.5f * Fy;
+        }
+      }
+      Fx_prev = Fx_cur[1];
+      Fy_prev = Fy_cur[1];
     }
-    s6 = s6p1;
+    s5 = s5p1;
     s3 = inc(s3, 3);
   }
 
-  // CTA partial sums of the stored state (FP64, fixed order).
-  double v[4] = {(double)acc_m, (double)acc_x, (double)acc_y, (double)bad};
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) S.red[c][threadIdx.x >> 5] = v[c];
+  // CTA partial sums of the stored state (FP64, fixed order).  Every TMA
+  // copy has been waited for, so the population ring is free for them.
+  double *red = reinterpret_cast<double *>(&S.pops[0][0]);
   __syncthreads();
-  if (threadIdx.x == 0) {
+  red[0 * kThreads + t] = (double)acc_m;
+  red[1 * kThreads + t] = (double)acc_x;
+  red[2 * kThreads + t] = (double)acc_y;
+  red[3 * kThreads + t] = (double)bad;
+  __syncthreads();
+  if (t == 0) {
     double *out = A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      double s = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s += S.red[c][w];
-      out[c] = s;
+    for (int q = 0; q < 4; ++q) {
+      double sum = 0.0;
+      for (int i = 0; i < kThreads; ++i) sum += red[q * kThreads + i];
+      out[q] = sum;
     }
   }
 }
@@ -439,8 +474,16 @@ cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUten
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+void sweep_plan(int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg) {
+  *nstrips = (nx + kMaxW - 1) / kMaxW;
+  *base_w = 4 * (nx / (4 * *nstrips));
+  *extra = (nx - *base_w * *nstrips) / 4;
+  *seg_h = ny < kSeg ? ny : kSeg;
+  *nseg = (ny + *seg_h - 1) / *seg_h;
+}
+
 cudaError_t sweep_prepare(size_t *smem_bytes) {
-  *smem_bytes = sizeof(SweepSmem) + 128;
+  *smem_bytes = sizeof(SweepSmem);
   return cudaFuncSetAttribute(sweep_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)*smem_bytes);
 }
