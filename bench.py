@@ -37,6 +37,23 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(value: float, dist=None) -> float:
+    """Largest value over all ranks (the job is as slow as its slowest rank).
+    Uses a CUDA tensor with NCCL and a CPU tensor with gloo."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_mlups(sites_per_rank: int, steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job throughput: site updates of all ranks over the slowest rank's time."""
+    return sites_per_rank * steps * world / (t_max_ms * 1e-3) / 1e6
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -186,12 +203,8 @@ def run_ours(args):
     rc, _ = lb_reduce(s.h)
     unstable = rc == LB_ERR_UNSTABLE
 
-    t_max = t_ms
-    if dist is not None:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = sites * args.steps * world / (t_max * 1e-3) / 1e6
+    t_max = max_over_ranks(t_ms, dist)
+    value = job_mlups(sites, args.steps, world, t_max)
     per_launch_s = t_ms * 1e-3 / args.steps
     achieved = B_ALG_FP32 * sites / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
@@ -210,9 +223,9 @@ def run_ours(args):
         lb_step(s.h, 1)
         lb_reduce(s.h)
     lb_moments(s.h, mom[0].data_ptr(), mom[1].data_ptr(), mom[2].data_ptr(), 1, 0)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     barrier()
-    e2e_mlups = sites * k_e2e * world / e2e_s / 1e6
+    e2e_mlups = job_mlups(sites, k_e2e, world, e2e_s * 1e3)
     h2d = n0.numel() * 8 / k_e2e
     d2h = 24 + mom.numel() * 4 / k_e2e
     s.close()

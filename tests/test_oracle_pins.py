@@ -387,3 +387,30 @@ def test_zebra_phase_at_rest(oracle_mod):
     assert abs(n.min() / z["n_V"] - 1) < 0.035
     # One liquid and one vapour stripe per wavelength, locked to the force.
     assert np.argmax(n[0]) != np.argmin(n[0])
+
+
+def test_workload_parameter_readings():
+    """The literal vdW constants a = 9/49, b = 2/21 (n_c = 3.5, T_c = 4/7)
+    with kappa = 0.049, A0 = 0.05 diverge in this scheme within a few hundred
+    steps of a noisy quench at 0.9 T_c; the paper's own parameter set at the
+    same lattice, temperature ratio and the paper's force amplitude stays
+    finite.  This is why the workloads use the paper's set."""
+    import oracle
+    from paper_1307_6703_gb300.workloads import C1, noise_field
+
+    lit = oracle.Params(nx=64, ny=32, walls=True, a=9 / 49, b=2 / 21, T=0.9 * 4 / 7,
+                        kappa=0.049, tau=1.0, A0=0.05, lam=32, N=0.3, Q=2.6)
+    o = oracle.Oracle(lit).init_noise(1, 3.5, 0.01)
+    blew_up = False
+    for _ in range(6):
+        o.step(100)
+        if not np.isfinite(o.f).all():
+            blew_up = True
+            break
+    assert blew_up
+
+    w = C1
+    o = oracle.Oracle(oracle.Params(**w.physics())).init_fields(noise_field(w))
+    o.step(w.steps)
+    n, ux, uy = o.moments()
+    assert np.isfinite(o.f).all() and n.min() > 0 and n.max() < 1 / w.b
