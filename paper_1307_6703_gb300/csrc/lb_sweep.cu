@@ -64,10 +64,14 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 // Rings of row pairs.  A row y belongs to pair (y - y0) / 2 of a ring with
 // origin y0: populations y0 = ya - 4, density ya - 3, P/L ya - 4, n u*
-// ya - 5, chosen so that iteration k writes pair k of every ring.
+// ya - 5, chosen so that iteration k writes pair k of every ring.  Each
+// ring is long enough that no stage overwrites a slot another thread may
+// still read without a barrier in between.
 struct __align__(128) SweepSmem {
   float pops[kPairs][kSlotFloats];  // [slot][plane][row of pair][column] + padding
-  float n[3][2][kCols];
+  // four pairs: stage A of iteration k+1 writes pair k+1 while stage D of
+  // iteration k (no barrier in between) may still read pairs k-2 and k-1
+  float n[4][2][kCols];
   float P[2][2][kCols];
   float L[2][2][kCols];
   float Jx[2][2][kCols];
@@ -236,7 +240,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
 
   for (int k = 0; k <= kmax; ++k) {
     const int s5m1 = dec(s5, kPairs), s5m2 = dec(s5m1, kPairs), s5p1 = inc(s5, kPairs);
-    const int s3m1 = dec(s3, 3), s3m2 = dec(s3m1, 3);
+    const int s3m1 = (s3 + 3) & 3, s3m2 = (s3 + 2) & 3;  // density ring: 4 pairs
     const int s2 = k & 1, s2m1 = s2 ^ 1;
     mbar_wait(smem_u32(&S.full[s5p1]), par, A.err);  // newest pair needed: k+1
     if (s5p1 == kPairs - 1) par ^= 1u;
@@ -402,7 +406,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
       Fy_prev = Fy_cur[1];
     }
     s5 = s5p1;
-    s3 = inc(s3, 3);
+    s3 = (s3 + 1) & 3;
   }
 
   // CTA partial sums of the stored state (FP64, fixed order).  Every TMA
