@@ -74,6 +74,9 @@ def lib():
         _lib.orc_step.restype = C.c_int
         _lib.orc_moments.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp, dp]
         _lib.orc_moments.restype = C.c_int
+        _lib.orc_round_sig.argtypes = [C.c_double, C.c_int, C.c_int]
+        _lib.orc_round_sig.restype = C.c_double
+        _lib.orc_quantize.argtypes = [C.c_int, C.c_int, C.c_double, C.c_size_t, dp, dp]
     return _lib
 
 
@@ -148,6 +151,35 @@ def noise_field(nx: int, ny: int, seed: int, rho_mean: float, amp: float) -> np.
     return out
 
 
+# 16-bit deviation storage formats: (significant bits, smallest exponent).
+FORMATS = {"bf16": (8, -126), "fp16": (11, -14)}
+
+
+def round_sig(x: float, fmt: str) -> float:
+    """x rounded to the format's precision (nearest, ties to even)."""
+    p, emin = FORMATS[fmt]
+    return lib().orc_round_sig(float(x), p, emin)
+
+
+def quantize(f: np.ndarray, fmt: str, rho_ref: float, want_unrounded: bool = False):
+    """State f[9][...] after a store in the 16-bit deviation format (in place
+    on a copy); optionally also the deviations before rounding."""
+    p, emin = FORMATS[fmt]
+    out = np.ascontiguousarray(f, dtype=np.float64).copy()
+    S = out.size // 9
+    dev = np.zeros((8,) + out.shape[1:]) if want_unrounded else None
+    lib().orc_quantize(p, emin, float(rho_ref), S, _ptr(out), _ptr(dev))
+    return (out, dev) if want_unrounded else out
+
+
+def reference_pops(rho_ref: float) -> np.ndarray:
+    """Reference populations r_i of the deviation format (FP32-rounded)."""
+    r = np.zeros(9)
+    r[1:5] = np.float32(rho_ref / 9.0)
+    r[5:9] = np.float32(rho_ref / 36.0)
+    return r
+
+
 # ---------------------------------------------------------------- solver
 
 class Oracle:
@@ -174,11 +206,24 @@ class Oracle:
         self.f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.p.ny, self.p.nx).copy()
         return self
 
-    def step(self, nsteps: int = 1):
-        rc = lib().orc_step(C.byref(self._cp), _ptr(self.f), int(nsteps))
-        if rc != 0:
-            raise RuntimeError("oracle step failed (bad parameters or out of memory)")
+    def step(self, nsteps: int = 1, storage: tuple[str, float] | None = None):
+        """Advance nsteps.  With storage = (fmt, rho_ref) every stored state
+        (after each step) goes through the 16-bit deviation format."""
+        if storage is None:
+            rc = lib().orc_step(C.byref(self._cp), _ptr(self.f), int(nsteps))
+            if rc != 0:
+                raise RuntimeError("oracle step failed (bad parameters or out of memory)")
+        else:
+            for _ in range(int(nsteps)):
+                if lib().orc_step(C.byref(self._cp), _ptr(self.f), 1) != 0:
+                    raise RuntimeError("oracle step failed (bad parameters or out of memory)")
+                self.quantize(*storage)
         self.t += nsteps
+        return self
+
+    def quantize(self, fmt: str, rho_ref: float):
+        """Pass the current state through the 16-bit deviation format."""
+        self.f = quantize(self.f, fmt, rho_ref)
         return self
 
     def moments(self, forces: bool = False):

@@ -472,3 +472,57 @@ int orc_moments(const orc_params *p, const double *f, double *n, double *ux,
   work_free(&w);
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * 16-bit deviation storage (a storage format of this implementation; the
+ * paper stores populations at full precision).
+ *
+ * For i = 1..8 the stored value is the deviation d_i = f_i - r_i from a
+ * reference population r_i (r = rho_ref / 9 on the axis links, rho_ref / 36
+ * on the diagonal links, each rounded to FP32: the reference is part of the
+ * format), rounded to nearest, ties to even, with p significant bits and a
+ * smallest exponent emin (bfloat16: p = 8, emin = -126; IEEE binary16:
+ * p = 11, emin = -14).  The rest population is kept at full precision and
+ * takes the remainder f_0 = n - sum_{i>=1} f_i with n = sum_i f_i of the
+ * unrounded site, so every site keeps its density (Sec. II: mass
+ * conservation of the collision and the wall rule).
+ * ------------------------------------------------------------------------ */
+
+/* x rounded to p significant bits (ties to even); spacing never below
+ * 2^(emin - p + 1) (gradual underflow).  Overflow is not handled: the
+ * deviations stay far below the formats' largest finite values.            */
+double orc_round_sig(double x, int p, int emin) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e;
+  (void)frexp(x, &e); /* |x| in [2^(e-1), 2^e) */
+  int lead = e - 1;
+  if (lead < emin) lead = emin;
+  double ulp = ldexp(1.0, lead - (p - 1));
+  return nearbyint(x / ulp) * ulp; /* x / ulp is exact: ulp is a power of 2 */
+}
+
+/* Reference population of link i (0 for the rest link). */
+static double ref_pop(int i, double rho_ref) {
+  if (i == 0) return 0.0;
+  return (double)(float)(i <= 4 ? rho_ref / 9.0 : rho_ref / 36.0);
+}
+
+/* Replace the state f[9][S] by the value it has after a store in the 16-bit
+ * deviation format.  dev_unrounded (8*S doubles, may be NULL) receives the
+ * deviations before rounding, plane i-1 for link i.                        */
+void orc_quantize(int p, int emin, double rho_ref, size_t S, double *f,
+                  double *dev_unrounded) {
+  for (size_t s = 0; s < S; s++) {
+    double n = 0.0;
+    for (int i = 0; i < 9; i++) n += f[i * S + s];
+    double rest = n;
+    for (int i = 1; i < 9; i++) {
+      double r = ref_pop(i, rho_ref);
+      double d = f[i * S + s] - r;
+      if (dev_unrounded) dev_unrounded[(size_t)(i - 1) * S + s] = d;
+      f[i * S + s] = r + orc_round_sig(d, p, emin);
+      rest -= f[i * S + s];
+    }
+    f[s] = rest;
+  }
+}
