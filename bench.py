@@ -3,9 +3,11 @@
 
 One benchmark step = one full time step (propagation, density, forces, wall
 rule, equilibrium, forcing, collision) over the 4096x1024 sheared workload
-in FP32.  Prints one JSON line (rank 0).
+in FP32 (or, with --precision, 16-bit deviation storage with FP32
+arithmetic).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|bf16dev|fp16dev]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build)
 on the host cores, each step a bounded row band of the same workload.
@@ -25,7 +27,38 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-B_ALG_FP32 = 72.0  # algorithmic bytes per site update: 9 populations read + 9 written
+# Algorithmic bytes per site update: 9 populations read + 9 written.  FP32
+# storage 4 bytes each; 16-bit deviation storage: a 4-byte rest population
+# and eight 2-byte deviations.
+B_ALG = {"fp32": 72.0, "bf16dev": 40.0, "fp16dev": 40.0}
+KERNEL_SRC = os.path.join(ROOT, "paper_1307_6703_gb300", "csrc", "lb_sweep.cu")
+PROFILE = {"fp32": os.path.join(ROOT, "profiles", "lb_step_sweep_fp32_4096x1024.md"),
+           "bf16dev": os.path.join(ROOT, "profiles", "lb_step_sweep_bf16dev_4096x1024.md"),
+           "fp16dev": os.path.join(ROOT, "profiles", "lb_step_sweep_fp16dev_4096x1024.md")}
+
+
+def kernel_source_digest() -> str:
+    import hashlib
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per launch (read + write) of the step kernel from the
+    committed ncu summary, if it was taken on the current kernel source
+    (the summary states the source digest it was taken on); else None."""
+    try:
+        with open(PROFILE[precision]) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    digest, traffic = None, None
+    for line in text.splitlines():
+        if line.startswith("kernel source digest:"):
+            digest = line.split(":", 1)[1].strip().strip("`")
+        if line.startswith("dram bytes per launch:"):
+            traffic = float(line.split(":", 1)[1].split()[0])
+    return traffic if digest == kernel_source_digest() else None
 
 
 def measured_peaks():
@@ -113,9 +146,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_solver(w, stream_handle):
-    from paper_1307_6703_gb300 import LB_FP32, Solver
-    return Solver(w.nx, w.ny, precision=LB_FP32, walls=w.walls, a=w.a, b=w.b, T=w.T,
+def make_solver(w, stream_handle, precision="fp32"):
+    from paper_1307_6703_gb300 import LB_BF16DEV, LB_FP16DEV, LB_FP32, Solver
+    prec = {"fp32": LB_FP32, "bf16dev": LB_BF16DEV, "fp16dev": LB_FP16DEV}[precision]
+    return Solver(w.nx, w.ny, precision=prec, walls=w.walls, a=w.a, b=w.b, T=w.T,
                   kappa=w.kappa, tau=w.tau, A0=w.A0, lam=w.lam, u_bot=w.u_bot,
                   u_top=w.u_top, N=w.N, Q=w.Q, stream=stream_handle)
 
@@ -183,7 +217,8 @@ def run_ours(args):
     w = C4
     sites = w.nx * w.ny
     stream = torch.cuda.Stream()
-    s = make_solver(w, stream.cuda_stream)
+    s = make_solver(w, stream.cuda_stream, args.precision)
+    b_alg = B_ALG[args.precision]
     s.init_noise(w.seed + rank, w.rho_mean, w.noise)
 
     # ------------------------------------------------ device-resident timing
@@ -206,7 +241,7 @@ def run_ours(args):
     t_max = max_over_ranks(t_ms, dist)
     value = job_mlups(sites, args.steps, world, t_max)
     per_launch_s = t_ms * 1e-3 / args.steps
-    achieved = B_ALG_FP32 * sites / per_launch_s / 1e9
+    achieved = b_alg * sites / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
 
     # --------------------------------------------- end to end through the ABI
@@ -237,15 +272,17 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_max / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "storage": args.precision,
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "walls": True,
                        "u_w": w.u_top, "A0": w.A0, "lambda": w.lam, "T_over_Tc": 0.95,
                        "tau": w.tau, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2: two 151 MB FP32 population buffers",
+                       "l2": f"inputs larger than L2: two {b_alg / 2 * sites / 1e6:.0f} MB population buffers",
                        "unstable_after_timing": unstable},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_kind": peak_kind, "kernel": "lb_step (fused)",
-                         "bytes_per_site": B_ALG_FP32},
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": profiled_traffic(args.precision),
+                         "peak_kind": peak_kind, "kernel": "lbk::sweep_step_kernel",
+                         "bytes_per_site": b_alg, "kernel_source_digest": kernel_source_digest()},
             "clocks": clocks,
             "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS",
                     "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
@@ -270,6 +307,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=sorted(B_ALG), default="fp32")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -55,9 +55,19 @@ enum {
   LB_FP64 = 0,    /* FP64 storage and arithmetic, no fused multiply-add:
                      the evaluation order of the FP64 oracle (parity mode) */
   LB_FP32 = 1,    /* FP32 storage and arithmetic (performance path)        */
-  LB_BF16DEV = 2, /* reserved: 16-bit deviation storage                    */
-  LB_FP16DEV = 3  /* reserved: 16-bit deviation storage                    */
+  LB_BF16DEV = 2, /* 16-bit deviation storage, bfloat16 (see below)        */
+  LB_FP16DEV = 3  /* 16-bit deviation storage, IEEE binary16 (see below)   */
 };
+/* 16-bit deviation storage (a storage format of this library; the paper
+ * keeps full-precision populations).  For i = 1..8 the stored value is the
+ * deviation d_i = f*_i - r_i from the reference population r_i = rho_ref/9
+ * (axis links) or rho_ref/36 (diagonal links), each rounded to FP32, itself
+ * rounded to nearest even in the 16-bit format; the rest population f*_0
+ * is stored as FP32 and takes the remainder n - sum_{i>=1} (r_i + d_i), so
+ * every site keeps its density and the total mass is conserved to FP32
+ * round-off (Sec. II: collision and wall rule conserve mass).  Arithmetic
+ * is FP32.  20 bytes per site instead of 36 (FP32).  Needs nx a multiple of
+ * 8, nx >= 8 and ny >= 8.                                                  */
 
 /* Element type selector for lb_moments. */
 enum { LB_DTYPE_F64 = 0, LB_DTYPE_F32 = 1 };
@@ -77,7 +87,7 @@ typedef struct {
   int32_t nx, ny;    /* columns (periodic) and rows; nx >= 1, ny >= 1, and
                         ny >= 3 when walls are on                           */
   int32_t walls;     /* 1: moving walls on rows 0 and ny-1; 0: periodic y  */
-  int32_t precision; /* LB_FP64 or LB_FP32                                 */
+  int32_t precision; /* LB_FP64, LB_FP32, LB_BF16DEV or LB_FP16DEV        */
   double a, b;       /* van der Waals constants (lattice units)            */
   double T;          /* temperature (lattice units; T_c = 8a/(27b))        */
   double kappa;      /* square-gradient (surface tension) coefficient      */
@@ -86,14 +96,18 @@ typedef struct {
                         switches the force off)                            */
   double u_bot, u_top; /* wall x-velocities                                */
   double N, Q;       /* stencil parameters                                 */
-  double rho_ref;    /* reserved (16-bit deviation storage); set 0         */
+  double rho_ref;    /* reference density of 16-bit deviation storage; 0
+                        selects the vdW critical density 1/(3b) (1 if b = 0);
+                        ignored by LB_FP64 and LB_FP32                      */
   void *stream;      /* cudaStream_t to enqueue on; NULL = default stream  */
 } lb_params;
 
 typedef struct lb_handle lb_handle;
 
 /* Create a solver for the problem *p and allocate its device state (two
- * population buffers of 9*nx*ny elements plus small work buffers).
+ * population buffers of 9*nx*ny elements -- 16-bit storage: one float and
+ * eight 16-bit planes -- plus small work buffers; 16-bit storage adds one
+ * float copy of the nine planes for moments, reductions and init).
  * *out receives the handle.  Errors: LB_ERR_ARG (bad sizes, tau <= 1/2,
  * b*n range, precision), LB_ERR_CUDA, LB_ERR_OOM.                          */
 int lb_create(const lb_params *p, lb_handle **out);
@@ -138,8 +152,11 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype,
  * non-finite or any site's post-collision mass lies outside (0, 1/b).     */
 int lb_reduce(lb_handle *h, double *out);
 
-/* Checkpoint: copy the stored populations ([9][ny][nx], storage precision
- * of the handle) to the HOST buffer buf.  *bytes is the buffer size on
+/* Checkpoint: copy the stored populations to the HOST buffer buf:
+ * [9][ny][nx] elements of the storage precision (double for LB_FP64, float
+ * for LB_FP32); for 16-bit storage the float rest plane [ny][nx] followed by
+ * the eight 16-bit deviation planes [8][ny][nx] (raw bfloat16 / binary16
+ * bits), 20 bytes per site.  *bytes is the buffer size on
  * entry and the bytes needed on return; buf = NULL queries the size.
  * Synchronises the stream.  Errors: LB_ERR_ARG (buffer too small).       */
 int lb_get_state(lb_handle *h, void *buf, size_t *bytes);

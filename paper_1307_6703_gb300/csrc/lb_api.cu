@@ -23,8 +23,11 @@ struct lb_handle {
   // tile kernel; padded with 4 ghost columns / rows for the sweep kernel.
   int pitch = 0;
   long long plane = 0, off = 0;
-  bool sweep = false;            // FP32 strip-sweep kernel in use
-  CUtensorMap tmap[2];           // TMA descriptors of the two state buffers
+  bool sweep = false;            // strip-sweep kernel in use
+  int store = 0;                 // its storage format (lbk::kStoreF32, kStoreBF16, kStoreFP16)
+  CUtensorMap tmap[2][2];        // TMA descriptors of the two state buffers
+  float ref_ax = 0.f, ref_dg = 0.f;  // reference populations of 16-bit storage
+  float *wide = nullptr;         // 16-bit storage: nine float planes (moments, reductions, init)
   size_t sweep_smem = 0;
   int sweep_seg = 64, sweep_nstrips = 0, sweep_nseg = 0, sweep_base = 0, sweep_extra = 0;
   double *d_cta = nullptr;       // per-CTA partials written by the sweep kernel
@@ -198,6 +201,38 @@ reduce_cta(const double *__restrict__ cta, int nblocks, double *__restrict__ out
 }
 
 bool fp64(const lb_handle *h) { return h->p.precision == LB_FP64; }
+bool dev16(const lb_handle *h) { return h->p.precision == LB_BF16DEV || h->p.precision == LB_FP16DEV; }
+
+// Bytes of the compact state of lb_get_state / lb_set_state.
+size_t state_bytes(const lb_handle *h) {
+  return dev16(h) ? h->S * (sizeof(float) + 8 * 2) : 9 * h->S * h->elem;
+}
+
+// Plane q of state buffer b: first interior element and element size.
+char *plane_ptr(const lb_handle *h, int b, int q, size_t *esize) {
+  char *base = (char *)h->f[b];
+  if (!dev16(h)) {
+    *esize = h->elem;
+    return base + ((size_t)q * h->plane + h->off) * h->elem;
+  }
+  if (q == 0) {
+    *esize = sizeof(float);
+    return base + (size_t)h->off * sizeof(float);
+  }
+  *esize = 2;
+  return base + (size_t)h->plane * sizeof(float) + ((size_t)(q - 1) * h->plane + h->off) * 2;
+}
+
+// The nine float planes of the current state: the state buffer itself for
+// FP32, else the widened copy.
+cudaError_t current_f32(lb_handle *h, const float **out) {
+  if (!dev16(h)) {
+    *out = (const float *)h->f[h->cur];
+    return cudaSuccess;
+  }
+  *out = h->wide;
+  return lbk::launch_widen(h->store, h->f[h->cur], h->wide, h->plane, h->ref_ax, h->ref_dg, h->st);
+}
 
 lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   const lb_params &p = h->p;
@@ -235,8 +270,11 @@ lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   A.A_ax = (float)(1.0 + k * (1.0 - 2.0 * T0));
   A.A_diag = (float)(1.0 + k * (2.0 - 2.0 * T0));
   A.nmax = p.b > 0.0 ? (float)(1.0 / p.b) : 3.0e38f;
+  A.ref_ax = h->ref_ax;
+  A.ref_dg = h->ref_dg;
   A.sinx = (const float *)h->sinx;
   A.fout = fout;
+  A.fdev = dev16(h) ? (void *)((char *)fout + (size_t)h->plane * sizeof(float)) : nullptr;
   A.partials = h->d_cta;
   A.err = h->d_err;
   return A;
@@ -252,8 +290,14 @@ int lb_create(const lb_params *p, lb_handle **out) {
   if (p->nx < 1 || p->ny < 1) return fail(nullptr, LB_ERR_ARG, "lb_create: nx and ny must be >= 1");
   if (p->walls != 0 && p->walls != 1) return fail(nullptr, LB_ERR_ARG, "lb_create: walls must be 0 or 1");
   if (p->walls && p->ny < 3) return fail(nullptr, LB_ERR_ARG, "lb_create: walls need ny >= 3");
-  if (p->precision != LB_FP64 && p->precision != LB_FP32)
-    return fail(nullptr, LB_ERR_ARG, "lb_create: precision must be LB_FP64 or LB_FP32");
+  if (p->precision != LB_FP64 && p->precision != LB_FP32 && p->precision != LB_BF16DEV &&
+      p->precision != LB_FP16DEV)
+    return fail(nullptr, LB_ERR_ARG, "lb_create: unknown precision");
+  if ((p->precision == LB_BF16DEV || p->precision == LB_FP16DEV) &&
+      !lbk::sweep_supported(p->precision, p->nx, p->ny))
+    return fail(nullptr, LB_ERR_ARG, "lb_create: 16-bit storage needs nx a multiple of 8, nx >= 8 and ny >= 8");
+  if (!(p->rho_ref >= 0.0) || !std::isfinite(p->rho_ref))
+    return fail(nullptr, LB_ERR_ARG, "lb_create: rho_ref must be finite and >= 0");
   if (!(p->tau > 0.5)) return fail(nullptr, LB_ERR_ARG, "lb_create: tau must exceed 1/2");
   if (!(p->T > 0.0) || !(p->b >= 0.0) || !std::isfinite(p->a) || !std::isfinite(p->kappa) ||
       !std::isfinite(p->N) || !std::isfinite(p->Q) || !std::isfinite(p->A0) ||
@@ -268,22 +312,29 @@ int lb_create(const lb_params *p, lb_handle **out) {
   h->st = (cudaStream_t)p->stream;
   h->S = (size_t)p->nx * (size_t)p->ny;
   h->elem = fp64(h) ? sizeof(double) : sizeof(float);
-  // The FP32 strip-sweep kernel needs x in multiples of 4 (16-byte TMA
-  // boxes) and at least 8 sites per direction (one ghost band of 4 each).
-  h->sweep = !fp64(h) && p->nx % 4 == 0 && p->nx >= 8 && p->ny >= 8 &&
-             9.0 * (double)(((p->nx + 8 + 31) / 32) * 32) * (double)(p->ny + 8) < 2147483647.0;
+  if (dev16(h)) {
+    // Reference density of the deviations: the vdW critical density 1/(3b)
+    // unless given.
+    if (h->p.rho_ref == 0.0) h->p.rho_ref = p->b > 0.0 ? 1.0 / (3.0 * p->b) : 1.0;
+    h->ref_ax = (float)(h->p.rho_ref / 9.0);
+    h->ref_dg = (float)(h->p.rho_ref / 36.0);
+  }
+  // The strip-sweep kernel needs x in multiples of its TMA column quantum
+  // and at least 8 sites per direction (one ghost band of 4 each).
+  h->store = p->precision;
+  h->sweep = !fp64(h) && lbk::sweep_supported(h->store, p->nx, p->ny);
   if (h->sweep) {
     h->pitch = ((p->nx + 8 + 31) / 32) * 32;
     h->plane = (long long)h->pitch * (p->ny + 8);
     h->off = 4LL * h->pitch + 4;
-    lbk::sweep_plan(p->nx, p->ny, &h->sweep_nstrips, &h->sweep_base, &h->sweep_extra, &h->sweep_seg,
+    lbk::sweep_plan(h->store, p->nx, p->ny, &h->sweep_nstrips, &h->sweep_base, &h->sweep_extra, &h->sweep_seg,
                     &h->sweep_nseg);
   } else {
     h->pitch = p->nx;
     h->plane = (long long)h->S;
     h->off = 0;
   }
-  const size_t buf_bytes = 9 * (size_t)h->plane * h->elem;
+  const size_t buf_bytes = h->sweep ? lbk::sweep_buffer_bytes(h->store, h->plane) : 9 * (size_t)h->plane * h->elem;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->f[0], buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->f[1], buf_bytes);
@@ -293,10 +344,12 @@ int lb_create(const lb_params *p, lb_handle **out) {
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
   if (e == cudaSuccess && h->sweep) {
     e = cudaMalloc((void **)&h->d_cta, 4 * sizeof(double) * (size_t)h->sweep_nstrips * h->sweep_nseg);
-    if (e == cudaSuccess) e = lbk::sweep_prepare(&h->sweep_smem);
-    if (e == cudaSuccess) e = lbk::sweep_make_map(h->f[0], h->pitch, p->ny, h->plane, &h->tmap[0]);
-    if (e == cudaSuccess) e = lbk::sweep_make_map(h->f[1], h->pitch, p->ny, h->plane, &h->tmap[1]);
+    if (e == cudaSuccess) e = lbk::sweep_prepare(h->store, &h->sweep_smem);
+    for (int b = 0; b < 2 && e == cudaSuccess; b++)
+      e = lbk::sweep_make_maps(h->store, h->f[b], h->pitch, p->ny, h->plane, &h->tmap[b][0], &h->tmap[b][1]);
   }
+  if (e == cudaSuccess && dev16(h)) e = cudaMalloc((void **)&h->wide, 9 * (size_t)h->plane * sizeof(float));
+  if (e == cudaSuccess && dev16(h)) e = cudaMemset(h->wide, 0, 9 * (size_t)h->plane * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->sinx, (size_t)p->nx * h->elem);
   h->red_blocks = (int)std::min<size_t>((h->S + RED_THREADS - 1) / RED_THREADS, 1024);
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_partials, 3 * (size_t)h->red_blocks * sizeof(double));
@@ -348,18 +401,23 @@ int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean, double noise
     }
   }
   h->cur = 0;
+  // 16-bit storage: the float equilibrium goes through the storage format.
+  float *f32 = dev16(h) ? h->wide : (float *)h->f[0];
   cudaError_t e = fp64(h)
                       ? lbk::launch_init((double *)h->f[0], h->p.nx, h->p.ny, h->pitch, h->plane,
                                          h->off, mode, seed, rho_mean, noise_amp, dr, du, dv,
                                          h->p.T, h->st)
-                      : lbk::launch_init((float *)h->f[0], h->p.nx, h->p.ny, h->pitch, h->plane,
+                      : lbk::launch_init(f32, h->p.nx, h->p.ny, h->pitch, h->plane,
                                          h->off, mode, seed, rho_mean, noise_amp, dr, du, dv,
                                          h->p.T, h->st);
   if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: init kernel");
   if (h->sweep) {
-    e = lbk::launch_ghost_fill((float *)h->f[0], h->p.nx, h->p.ny, h->pitch, h->plane, h->off,
-                               h->p.walls, h->st);
+    e = lbk::launch_ghost_fill(f32, 4, 9, h->p.nx, h->p.ny, h->pitch, h->plane, h->off, h->p.walls, h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: ghost fill");
+  }
+  if (dev16(h)) {
+    e = lbk::launch_narrow(h->store, h->wide, h->f[0], h->plane, h->ref_ax, h->ref_dg, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: 16-bit store");
   }
   h->cta_valid = false;
   if (mode == 1) LB_CUDA(h, cudaStreamSynchronize(h->st));
@@ -383,7 +441,7 @@ int lb_step(lb_handle *h, int64_t nsteps) {
   } else if (h->sweep) {
     for (int64_t k = 0; k < nsteps; k++) {
       const lbk::SweepArgs A = sweep_args(h, (float *)h->f[h->cur ^ 1]);
-      cudaError_t e = lbk::launch_sweep(h->tmap[h->cur], A, h->sweep_smem, h->st);
+      cudaError_t e = lbk::launch_sweep(h->store, h->tmap[h->cur][0], h->tmap[h->cur][1], A, h->sweep_smem, h->st);
       if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: sweep kernel");
       h->cur ^= 1;
       h->step++;
@@ -414,8 +472,14 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_de
     du = ux ? base + h->S * es : nullptr;
     dv = uy ? base + 2 * h->S * es : nullptr;
   }
-  cudaError_t e = fp64(h) ? lbk::launch_moments((const double *)h->f[h->cur], make_args<double>(h), dn, du, dv, dtype, h->st)
-                          : lbk::launch_moments((const float *)h->f[h->cur], make_args<float>(h), dn, du, dv, dtype, h->st);
+  cudaError_t e;
+  if (fp64(h)) {
+    e = lbk::launch_moments((const double *)h->f[h->cur], make_args<double>(h), dn, du, dv, dtype, h->st);
+  } else {
+    const float *f32 = nullptr;
+    e = current_f32(h, &f32);
+    if (e == cudaSuccess) e = lbk::launch_moments(f32, make_args<float>(h), dn, du, dv, dtype, h->st);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "lb_moments: kernel");
   if (!on_device) {
     const size_t nb = h->S * es;
@@ -441,10 +505,12 @@ int lb_reduce(lb_handle *h, double *out) {
       reduce_pass1<double><<<h->red_blocks, RED_THREADS, 0, h->st>>>(
           (const double *)h->f[h->cur], h->p.nx, h->S, h->pitch, h->plane, h->off, nmax,
           h->d_partials, h->d_flag);
-    else
+    else {
+      const float *f32 = nullptr;
+      LB_CUDA(h, current_f32(h, &f32));
       reduce_pass1<float><<<h->red_blocks, RED_THREADS, 0, h->st>>>(
-          (const float *)h->f[h->cur], h->p.nx, h->S, h->pitch, h->plane, h->off, nmax,
-          h->d_partials, h->d_flag);
+          f32, h->p.nx, h->S, h->pitch, h->plane, h->off, nmax, h->d_partials, h->d_flag);
+    }
     LB_CUDA(h, cudaGetLastError());
     reduce_pass2<<<1, RED_THREADS, 0, h->st>>>(h->d_partials, h->red_blocks, h->d_out);
   }
@@ -465,7 +531,7 @@ int lb_reduce(lb_handle *h, double *out) {
 
 int lb_get_state(lb_handle *h, void *buf, size_t *bytes) {
   if (!h || !bytes) return h ? fail(h, LB_ERR_ARG, "lb_get_state: null size") : LB_ERR_ARG;
-  const size_t need = 9 * h->S * h->elem;
+  const size_t need = state_bytes(h);
   if (!buf) {
     *bytes = need;
     return LB_OK;
@@ -478,12 +544,14 @@ int lb_get_state(lb_handle *h, void *buf, size_t *bytes) {
   if (h->pitch == h->p.nx && h->off == 0 && (size_t)h->plane == h->S) {
     LB_CUDA(h, cudaMemcpyAsync(buf, h->f[h->cur], need, cudaMemcpyDeviceToHost, h->st));
   } else {
-    const size_t row = (size_t)h->p.nx * h->elem;
+    char *dst = (char *)buf;
     for (int q = 0; q < 9; q++) {
-      const char *src = (const char *)h->f[h->cur] + ((size_t)q * h->plane + h->off) * h->elem;
-      char *dst = (char *)buf + (size_t)q * h->S * h->elem;
-      LB_CUDA(h, cudaMemcpy2DAsync(dst, row, src, (size_t)h->pitch * h->elem, row, h->p.ny,
+      size_t es = 0;
+      const char *src = plane_ptr(h, h->cur, q, &es);
+      const size_t row = (size_t)h->p.nx * es;
+      LB_CUDA(h, cudaMemcpy2DAsync(dst, row, src, (size_t)h->pitch * es, row, h->p.ny,
                                    cudaMemcpyDeviceToHost, h->st));
+      dst += h->S * es;
     }
   }
   LB_CUDA(h, cudaStreamSynchronize(h->st));
@@ -493,21 +561,31 @@ int lb_get_state(lb_handle *h, void *buf, size_t *bytes) {
 
 int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step) {
   if (!h || !buf) return h ? fail(h, LB_ERR_ARG, "lb_set_state: null buffer") : LB_ERR_ARG;
-  const size_t need = 9 * h->S * h->elem;
+  const size_t need = state_bytes(h);
   if (bytes != need) return fail(h, LB_ERR_ARG, "lb_set_state: size mismatch");
   if (step < 0) return fail(h, LB_ERR_ARG, "lb_set_state: negative step");
   if (h->pitch == h->p.nx && h->off == 0 && (size_t)h->plane == h->S) {
     LB_CUDA(h, cudaMemcpyAsync(h->f[h->cur], buf, need, cudaMemcpyHostToDevice, h->st));
   } else {
-    const size_t row = (size_t)h->p.nx * h->elem;
+    const char *src = (const char *)buf;
     for (int q = 0; q < 9; q++) {
-      char *dst = (char *)h->f[h->cur] + ((size_t)q * h->plane + h->off) * h->elem;
-      const char *src = (const char *)buf + (size_t)q * h->S * h->elem;
-      LB_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)h->pitch * h->elem, src, row, row, h->p.ny,
+      size_t es = 0;
+      char *dst = plane_ptr(h, h->cur, q, &es);
+      const size_t row = (size_t)h->p.nx * es;
+      LB_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)h->pitch * es, src, row, row, h->p.ny,
                                    cudaMemcpyHostToDevice, h->st));
+      src += h->S * es;
     }
-    LB_CUDA(h, lbk::launch_ghost_fill((float *)h->f[h->cur], h->p.nx, h->p.ny, h->pitch, h->plane,
-                                      h->off, h->p.walls, h->st));
+    if (dev16(h)) {
+      char *base = (char *)h->f[h->cur];
+      LB_CUDA(h, lbk::launch_ghost_fill(base, 4, 1, h->p.nx, h->p.ny, h->pitch, h->plane, h->off, h->p.walls,
+                                        h->st));
+      LB_CUDA(h, lbk::launch_ghost_fill(base + (size_t)h->plane * sizeof(float), 2, 8, h->p.nx, h->p.ny, h->pitch,
+                                        h->plane, h->off, h->p.walls, h->st));
+    } else {
+      LB_CUDA(h, lbk::launch_ghost_fill(h->f[h->cur], 4, 9, h->p.nx, h->p.ny, h->pitch, h->plane, h->off,
+                                        h->p.walls, h->st));
+    }
   }
   LB_CUDA(h, cudaStreamSynchronize(h->st));
   h->cta_valid = false;
@@ -535,6 +613,7 @@ int lb_destroy(lb_handle *h) {
   cudaFree(h->d_out);
   cudaFree(h->d_cta);
   cudaFree(h->d_err);
+  cudaFree(h->wide);
   delete h;
   return LB_OK;
 }

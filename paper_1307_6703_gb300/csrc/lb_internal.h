@@ -9,10 +9,13 @@
 
 namespace lbk {
 
-// Arguments of the FP32 strip-sweep kernel (lb_sweep.cu).  The state buffers
-// use the padded layout: plane q, interior site (x, y) at element
+// Arguments of the strip-sweep kernel (lb_sweep.cu).  The state buffers use
+// the padded layout: plane q, interior site (x, y) at element
 // q * plane + off + y * pitch + x, with 4 ghost columns and 4 ghost rows on
-// each side.
+// each side.  FP32 storage: nine float planes at fout.  16-bit deviation
+// storage: the rest population as one float plane at fout, the deviations
+// d_i = f_i - r_i (i = 1..8) as eight 16-bit planes at fdev (same pitch,
+// plane and offset, counted in 16-bit elements).
 struct SweepArgs {
   int nx, ny, walls;
   int pitch;
@@ -22,22 +25,46 @@ struct SweepArgs {
   float N, M, Q, R, four_QR;
   float A_rest, A_ax, A_diag;  // rest factors 1 + (T - T0)(c.c - 2 T0) / (2 T0^2)
   float nmax;                  // 1/b (upper bound of a valid density)
+  float ref_ax, ref_dg;        // reference populations r_i of the 16-bit format
   const float *sinx;
   float *fout;
+  void *fdev;
   double *partials;            // 4 doubles per CTA: mass, J_x, J_y, bad-site flag
   int *err;                    // set when a bounded wait gave up
 };
 
-cudaError_t sweep_prepare(size_t *smem_bytes);
-// Strips (widths base_w or base_w + 4; the first `extra` are wider) and
-// row segments of the sweep kernel for an nx x ny lattice.
-void sweep_plan(int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg);
-// TMA descriptor of one padded FP32 state buffer, with the box the sweep
-// kernel's ring expects (built next to the kernel so the two cannot differ).
-cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUtensorMap *map);
-cudaError_t launch_sweep(const CUtensorMap &tin, const SweepArgs &A, size_t smem, cudaStream_t st);
-cudaError_t launch_ghost_fill(float *f, int nx, int ny, int pitch, long long plane, long long off,
-                              int walls, cudaStream_t st);
+// Storage formats of the sweep kernel (values of lb_precision).
+constexpr int kStoreF32 = 1, kStoreBF16 = 2, kStoreFP16 = 3;
+
+// Whether the sweep kernel of storage `store` can run an nx x ny lattice
+// (column quantum of its TMA boxes, ghost bands, 32-bit plane offsets).
+bool sweep_supported(int store, int nx, int ny);
+cudaError_t sweep_prepare(int store, size_t *smem_bytes);
+// Strips (widths base_w or base_w + quantum, the first `extra` wider; the
+// quantum is 4 columns for FP32 storage and 8 for 16-bit storage) and row
+// segments of the sweep kernel for an nx x ny lattice.
+void sweep_plan(int store, int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg);
+// TMA descriptors of one padded state buffer with the boxes the kernel's
+// ring expects (built next to the kernel so the two cannot differ).  FP32:
+// one map of the nine planes (m1 is a copy).  16-bit storage: m0 maps the
+// float rest plane at base, m1 the eight deviation planes that follow it.
+cudaError_t sweep_make_maps(int store, void *base, int pitch, int ny, long long plane, CUtensorMap *m0,
+                            CUtensorMap *m1);
+// Bytes of one padded state buffer of the given storage.
+size_t sweep_buffer_bytes(int store, long long plane);
+cudaError_t launch_sweep(int store, const CUtensorMap &m0, const CUtensorMap &m1, const SweepArgs &A,
+                         size_t smem, cudaStream_t st);
+// Copy the periodic images into the ghost band of `nplanes` planes of
+// `elem_bytes`-byte elements (4 or 2).
+cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,
+                              long long off, int walls, cudaStream_t st);
+// 16-bit storage <-> nine float planes (same padded layout, every element
+// of the planes, ghost bands included).  narrow: d_i = f_i - r_i rounded to
+// nearest even, rest plane = n - sum_{i>=1} (r_i + d_i).
+cudaError_t launch_widen(int store, const void *buf, float *wide, long long plane, float ref_ax, float ref_dg,
+                         cudaStream_t st);
+cudaError_t launch_narrow(int store, const float *wide, void *buf, long long plane, float ref_ax, float ref_dg,
+                          cudaStream_t st);
 
 template <typename real_t>
 struct StepArgs;

@@ -1,15 +1,16 @@
-// lb_sweep.cu -- FP32 strip-sweep kernel: one fused time step of the vdW
-// lattice Boltzmann scheme (arXiv:1307.6703, Sec. II) streamed through
-// shared memory by TMA.
+// lb_sweep.cu -- strip-sweep kernel: one fused time step of the vdW lattice
+// Boltzmann scheme (arXiv:1307.6703, Sec. II) streamed through shared memory
+// by TMA, for FP32 storage and for 16-bit deviation storage.
 //
-// Work decomposition.  The lattice is cut into column strips of W <= 120
-// interior columns and row segments of up to SEG rows.  One CTA (256
-// threads: two warp groups, one per row of a row pair, each with one thread
-// per column of a 128-column window x0-4 .. x0+123) sweeps its segment
-// upwards, two rows per iteration.  Every row of the previous state is read
-// from HBM once by the TMA engine: a 3D tensor copy brings a pair of
-// 128-column rows of all nine population planes into a ring of six pairs in
-// shared memory (mbarrier-tracked), two pairs ahead of use.
+// Work decomposition.  The lattice is cut into column strips of W interior
+// columns (W <= 116 for FP32 storage, <= 112 for 16-bit storage, strip
+// origins on 16-byte TMA coordinates) and row segments of up to 64 rows.  One
+// CTA of 124 threads, one per column of the 124-column window x0-4 ..
+// x0+119 (strip plus 4-column halos), sweeps its segment upwards, two rows
+// per iteration.  Every row of the previous state is read from HBM once by
+// the TMA engine: tensor copies bring a pair of rows of all nine population
+// planes into a 5-slot ring in shared memory (one mbarrier per slot, waits
+// bounded), two pairs ahead of use.
 //
 // Iteration k (a = ya - 3 + 2k) runs four stages, separated by CTA barriers,
 // each on two rows:
@@ -37,12 +38,22 @@
 // the rest population is taken as n minus the other eight, which is the same
 // value in exact arithmetic and keeps the site mass exact in FP32.
 //
+// Storage formats.  FP32: the nine populations as floats.  16-bit deviation
+// storage (bfloat16 or IEEE half): for i = 1..8 the deviation d_i = f_i - r_i
+// from a reference population (r = rho_ref/9 on axis links, rho_ref/36 on
+// diagonal links, rounded to FP32) is stored rounded to nearest even; the
+// rest population stays a float and takes the remainder n - sum_{i>=1} f_i
+// of the ROUNDED values, so each site keeps its density to FP32 round-off.
+// Arithmetic is FP32 in both formats.
+//
 // Every CTA also writes FP64 partial sums of mass and momentum of the state
 // it stored, and a flag for non-finite or out-of-range sites, so that the
 // global reduction of the new state costs one tiny kernel.
 #include <cstddef>
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "lb_device.cuh"
 #include "lb_internal.h"
@@ -51,24 +62,78 @@ namespace lbk {
 
 namespace {
 
-constexpr int kCols = 124;                  // TMA box width (columns x0-4 .. x0+119)
-constexpr int kMaxW = kCols - 8;            // interior columns per strip
+constexpr int kCols = 124;                  // window width (columns x0-4 .. x0+119)
 constexpr int kPairs = 5;                   // population ring, in pairs of rows
 constexpr int kThreads = kCols;             // one thread per window column
 constexpr int kSeg = 64;                    // rows per segment
-constexpr int kPairFloats = 9 * 2 * kCols;  // one pair of rows of all nine planes
-constexpr unsigned kPairBytes = kPairFloats * sizeof(float);
-// Ring slots start on 128-byte boundaries (TMA destination alignment).
-constexpr int kSlotFloats = ((kPairFloats * 4 + 127) / 128) * 128 / 4;
 constexpr uint32_t kWaitLimit = 1u << 22;
+
+constexpr int round128(int b) { return ((b + 127) / 128) * 128; }
+
+// FP32 storage: one 3D box {kCols, 2, 9} (columns, rows, planes) per pair.
+struct StoreF32 {
+  static constexpr bool kDev = false;
+  static constexpr int kQuantum = 4;          // 16-byte x coordinates of float boxes
+  static constexpr int kMaxW = kCols - 8;     // 116
+  static constexpr unsigned kTxBytes = 9 * 2 * kCols * sizeof(float);
+  static constexpr int kSlotBytes = round128(kTxBytes);
+  static constexpr int kMinBlocks = 4;
+  using Row = const float *;  // row r of a slot; plane q starts q * 2 * kCols later
+  __device__ static Row row(const unsigned char *slot, int r) {
+    return reinterpret_cast<const float *>(slot) + r * kCols;
+  }
+  __device__ static float get(Row p, int q, int c, const SweepArgs &) { return p[q * 2 * kCols + c]; }
+};
+
+// 16-bit deviation storage: a float box {kCols, 2, 1} of the rest plane and a
+// 16-bit box {128, 2, 8} of the deviation planes (256-byte rows) per pair.
+template <class H>
+struct StoreDev {
+  static constexpr bool kDev = true;
+  static constexpr int kQuantum = 8;          // 16-byte x coordinates of 16-bit boxes
+  static constexpr int kMaxW = 112;
+  static constexpr int kDevCols = 128;
+  static constexpr int kRestBytes = 2 * kCols * sizeof(float);
+  static constexpr int kDevOffset = round128(kRestBytes);
+  static constexpr int kDevBytes = 8 * 2 * kDevCols * 2;
+  static constexpr unsigned kTxBytes = kRestBytes + kDevBytes;
+  static constexpr int kSlotBytes = round128(kDevOffset + kDevBytes);
+  static constexpr int kMinBlocks = 5;
+  struct Row {
+    const float *f0;
+    const H *d;
+  };
+  __device__ static Row row(const unsigned char *slot, int r) {
+    return {reinterpret_cast<const float *>(slot) + r * kCols,
+            reinterpret_cast<const H *>(slot + kDevOffset) + r * kDevCols};
+  }
+  __device__ static float dec(H v);
+  __device__ static H enc(float v);
+  __device__ static float get(const Row &p, int q, int c, const SweepArgs &A) {
+    if (q == 0) return p.f0[c];
+    return (q <= 4 ? A.ref_ax : A.ref_dg) + dec(p.d[(q - 1) * 2 * kDevCols + c]);
+  }
+};
+template <>
+__device__ __forceinline__ float StoreDev<__nv_bfloat16>::dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 StoreDev<__nv_bfloat16>::enc(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ float StoreDev<__half>::dec(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ __half StoreDev<__half>::enc(float v) { return __float2half_rn(v); }
+
+using StoreBF16 = StoreDev<__nv_bfloat16>;
+using StoreFP16 = StoreDev<__half>;
 
 // Rings of row pairs.  A row y belongs to pair (y - y0) / 2 of a ring with
 // origin y0: populations y0 = ya - 4, density ya - 3, P/L ya - 4, n u*
 // ya - 5, chosen so that iteration k writes pair k of every ring.  Each
 // ring is long enough that no stage overwrites a slot another thread may
 // still read without a barrier in between.
+template <int SlotBytes>
 struct __align__(128) SweepSmem {
-  float pops[kPairs][kSlotFloats];  // [slot][plane][row of pair][column] + padding
+  unsigned char pops[kPairs][SlotBytes];  // one row pair of every plane per slot
   // four pairs: stage A of iteration k+1 writes pair k+1 while stage D of
   // iteration k (no barrier in between) may still read pairs k-2 and k-1
   float n[4][2][kCols];
@@ -77,16 +142,12 @@ struct __align__(128) SweepSmem {
   float Jx[2][2][kCols];
   float Jy[2][2][kCols];
   unsigned long long full[kPairs];
+  static_assert(SlotBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
+  static_assert(kPairs * SlotBytes >= (int)sizeof(double) * 4 * kThreads,
+                "the end-of-kernel reduction reuses the population ring");
 };
-static_assert(sizeof(float) * kPairs * kSlotFloats >= sizeof(double) * 4 * kThreads,
-              "the end-of-kernel reduction reuses the population ring");
-static_assert((kSlotFloats * sizeof(float)) % 128 == 0, "TMA destinations must be 128-byte aligned");
-static_assert(offsetof(SweepSmem, pops) == 0, "the ring starts the (128-byte aligned) block");
-
-// Row r (0 or 1) of a ring slot; plane q of that row starts q * 2 * kCols later.
-__device__ __forceinline__ const float *pop_row(const SweepSmem &S, int slot, int r) {
-  return &S.pops[slot][r * kCols];
-}
+static_assert(offsetof(SweepSmem<StoreF32::kSlotBytes>, pops) == 0, "the ring starts the (128-byte aligned) block");
+static_assert(StoreBF16::kDevOffset % 128 == 0, "16-bit boxes must land on 128-byte boundaries");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -113,16 +174,23 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *er
   atomicOr(err, 1);
 }
 
-// Two rows (all nine planes, kCols columns) of the padded state into a slot.
-__device__ __forceinline__ void tma_pair(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad,
-                                         int ypad) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kPairBytes)
-               : "memory");
+__device__ __forceinline__ void tma_box(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad, int ypad) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(xpad), "r"(ypad), "r"(0), "r"(bar)
       : "memory");
+}
+
+// Two rows (all nine planes, the window's columns) of the padded state into
+// a ring slot, completing on the slot's mbarrier.
+template <class St>
+__device__ __forceinline__ void tma_pair(const CUtensorMap *m0, const CUtensorMap *m1, uint32_t dst, uint32_t bar,
+                                         int xpad, int ypad) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(St::kTxBytes)
+               : "memory");
+  tma_box(m0, dst, bar, xpad, ypad);
+  if constexpr (St::kDev) tma_box(m1, dst + St::kDevOffset, bar, xpad, ypad);
 }
 
 __device__ __forceinline__ int dec(int s, int n) { return s == 0 ? n - 1 : s - 1; }
@@ -145,17 +213,19 @@ __device__ __forceinline__ float slap(const Sten &s, const float *r0, const floa
 }
 
 // Propagated populations of the site in column t of row r1 (pull).
-__device__ __forceinline__ void pull(const float *r0, const float *r1, const float *r2, int t, float *f) {
-  constexpr int PR = 2 * kCols;  // plane stride inside a ring slot
-  f[0] = r1[0 * PR + t]; f[1] = r1[1 * PR + t - 1]; f[3] = r1[3 * PR + t + 1];
-  f[2] = r0[2 * PR + t]; f[5] = r0[5 * PR + t - 1]; f[6] = r0[6 * PR + t + 1];
-  f[4] = r2[4 * PR + t]; f[7] = r2[7 * PR + t + 1]; f[8] = r2[8 * PR + t - 1];
+template <class St>
+__device__ __forceinline__ void pull(const typename St::Row &r0, const typename St::Row &r1,
+                                     const typename St::Row &r2, int t, float *f, const SweepArgs &A) {
+  f[0] = St::get(r1, 0, t, A); f[1] = St::get(r1, 1, t - 1, A); f[3] = St::get(r1, 3, t + 1, A);
+  f[2] = St::get(r0, 2, t, A); f[5] = St::get(r0, 5, t - 1, A); f[6] = St::get(r0, 6, t + 1, A);
+  f[4] = St::get(r2, 4, t, A); f[7] = St::get(r2, 7, t + 1, A); f[8] = St::get(r2, 8, t - 1, A);
 }
 
 // One collision (Eqs. evoleq, eqfunc, forceterm, coeff) in the moment form
 //   f*_i = (1 - omega) f_i + w_i E_i,
 //   E_i = omega n [A_i + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2] + 3 c.B + 9/2 C:cc - 3/2 tr C,
-// with the rest population taken as n minus the other eight.
+// for the eight moving populations (the rest population is the remainder,
+// taken by the caller after any storage rounding).
 __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, float n, float Jx, float Jy,
                                         float Fx, float Fy, float dnx, float dny, float divJ, float *fs) {
   const float rn = __fdividef(1.0f, n);
@@ -183,22 +253,23 @@ __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, floa
   fs[7] = om1 * f[7] + w5 * (e_dg + sym5 - ant5);
   fs[6] = om1 * f[6] + w5 * (e_dg + sym6 + ant6);
   fs[8] = om1 * f[8] + w5 * (e_dg + sym6 - ant6);
-  // Collision conserves the site's mass exactly (A = 0, sum f^eq = n); the
-  // remainder form keeps rounded weights from biasing the mass.
-  fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 4)
-sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
+template <class St>
+__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tdev,
+                  const SweepArgs A) {
+  using Row = typename St::Row;
+  using Smem = SweepSmem<St::kSlotBytes>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  SweepSmem &S = *reinterpret_cast<SweepSmem *>(smem_raw);
+  Smem &S = *reinterpret_cast<Smem *>(smem_raw);
 
   const int t = threadIdx.x;
   const int strip = blockIdx.x, seg = blockIdx.y;
-  const int x0 = strip * A.base_w + 4 * min(strip, A.extra);
-  const int W = A.base_w + (strip < A.extra ? 4 : 0);
+  const int x0 = strip * A.base_w + St::kQuantum * min(strip, A.extra);
+  const int W = A.base_w + (strip < A.extra ? St::kQuantum : 0);
   const int ya = seg * A.seg_h;
   const int yb = min(A.ny, ya + A.seg_h);
   const int nx = A.nx, ny = A.ny;
@@ -213,7 +284,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
   const Sten st{A.N, A.M, A.Q, A.R, A.four_QR};
   float sinx = 0.f;
   if (actC) sinx = A.sinx[x < 0 ? x + nx : (x >= nx ? x - nx : x)];
-  float *col = A.fout + A.off + x;  // f* of this column at interior row 0
+  float *col = A.fout + A.off + x;  // f* (rest plane for 16-bit storage) of this column at interior row 0
   const int pitch = A.pitch, plane = (int)A.plane;
   const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);  // periodic image column
 
@@ -226,7 +297,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
     for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int P = 0; P < min(kPairs, npairs); ++P)
-      tma_pair(&tin, smem_u32(pop_row(S, P, 0)), smem_u32(&S.full[P]), x0, ya + 2 * P);
+      tma_pair<St>(&tin, &tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
   __syncthreads();
   mbar_wait(smem_u32(&S.full[0]), 0, A.err);
@@ -248,22 +319,23 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
 
     // ---------------------------------------- A: rows a, a+1 -- n, raw momentum
     {
-      const float *q0 = pop_row(S, s5, 0), *q1 = pop_row(S, s5, 1);    // rows a-1, a
-      const float *q2 = pop_row(S, s5p1, 0), *q3 = pop_row(S, s5p1, 1);  // rows a+1, a+2
+      const Row q0 = St::row(S.pops[s5], 0), q1 = St::row(S.pops[s5], 1);      // rows a-1, a
+      const Row q2 = St::row(S.pops[s5p1], 0), q3 = St::row(S.pops[s5p1], 1);  // rows a+1, a+2
       float sx_new[2] = {0.f, 0.f}, sy_new[2] = {0.f, 0.f};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int y = a + j;
-        const float *r0 = j ? q1 : q0, *r1 = j ? q2 : q1, *r2 = j ? q3 : q2;
+        const Row r0 = j ? q1 : q0, r1 = j ? q2 : q1, r2 = j ? q3 : q2;
         if (actA && (!walls || (y >= 0 && y <= ny - 1))) {
           float f[9];
-          pull(r0, r1, r2, t, f);
+          pull<St>(r0, r1, r2, t, f, A);
           float n;
-          constexpr int PR = 2 * kCols;
           if (walls && y == 0) {
-            n = r1[0 * PR + t] + r1[4 * PR + t] + r1[7 * PR + t] + r1[8 * PR + t] + f[1] + f[3] + f[4] + f[7] + f[8];
+            n = St::get(r1, 0, t, A) + St::get(r1, 4, t, A) + St::get(r1, 7, t, A) + St::get(r1, 8, t, A) + f[1] +
+                f[3] + f[4] + f[7] + f[8];
           } else if (walls && y == ny - 1) {
-            n = r1[0 * PR + t] + r1[2 * PR + t] + r1[6 * PR + t] + r1[5 * PR + t] + f[1] + f[3] + f[2] + f[6] + f[5];
+            n = St::get(r1, 0, t, A) + St::get(r1, 2, t, A) + St::get(r1, 6, t, A) + St::get(r1, 5, t, A) + f[1] +
+                f[3] + f[2] + f[6] + f[5];
           } else {
             n = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
             sx_new[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
@@ -277,7 +349,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
       // with pair k+2.
       if (t == 0 && k >= 3 && k + 2 < npairs) {
         const int slot = dec(s5m2, kPairs);
-        tma_pair(&tin, smem_u32(pop_row(S, slot, 0)), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
+        tma_pair<St>(&tin, &tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
       }
 
       // -------------------------------------- B: rows a-1, a -- P, lap n
@@ -321,10 +393,10 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
           float sx = sxa[j], sy = sya[j];
           if (walls && (y == 0 || y == ny - 1)) {
             // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
-            const float *w0 = pop_row(S, s5m1, 0), *w1 = pop_row(S, s5m1, 1);
-            const float *w2 = pop_row(S, s5, 0), *w3 = pop_row(S, s5, 1);
+            const Row w0 = St::row(S.pops[s5m1], 0), w1 = St::row(S.pops[s5m1], 1);
+            const Row w2 = St::row(S.pops[s5], 0), w3 = St::row(S.pops[s5], 1);
             float f[9];
-            pull(j ? w1 : w0, j ? w2 : w1, j ? w3 : w2, t, f);
+            pull<St>(j ? w1 : w0, j ? w2 : w1, j ? w3 : w2, t, f, A);
             const bool top = y != 0;
             wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
             sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
@@ -346,8 +418,8 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
         const float *X0 = S.Jx[s2m1][0], *X1 = S.Jx[s2m1][1], *X2 = S.Jx[s2][0], *X3 = S.Jx[s2][1];
         const float *Y0 = S.Jy[s2m1][0], *Y1 = S.Jy[s2m1][1], *Y2 = S.Jy[s2][0], *Y3 = S.Jy[s2][1];
         // population rows a-4 .. a-1: pair k-2 row 1, pair k-1 rows 0, 1, pair k row 0
-        const float *q0p = pop_row(S, s5m2, 1), *q1p = pop_row(S, s5m1, 0);
-        const float *q2p = pop_row(S, s5m1, 1), *q3p = pop_row(S, s5, 0);
+        const Row q0p = St::row(S.pops[s5m2], 1), q1p = St::row(S.pops[s5m1], 0);
+        const Row q2p = St::row(S.pops[s5m1], 1), q3p = St::row(S.pops[s5], 0);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 3 + j;
@@ -373,33 +445,75 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
           const float divJ = sdx(st, x0p, x1p, x2p, t) + dJy;
           const float Jx = x1p[t], Jy = y1p[t];
           float f[9], fs[9];
-          pull(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f);
+          pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f, A);
           if (bot || top) wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
           collide(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs);
-
-          float *o = col + (long long)y * pitch;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) o[q * plane] = fs[q];
           const int gy = walls ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
-          if (gx != 0) {
+          float *o = col + (long long)y * pitch;
+          if constexpr (!St::kDev) {
+            // Collision conserves the site's mass exactly (A = 0, sum f^eq =
+            // n); the remainder form keeps rounded weights from biasing it.
+            fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
 #pragma unroll
-            for (int q = 0; q < 9; ++q) o[q * plane + gx] = fs[q];
-          }
-          if (gy != 0) {
-            float *oy = o + (long long)gy * pitch;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) oy[q * plane] = fs[q];
+            for (int q = 0; q < 9; ++q) o[q * plane] = fs[q];
             if (gx != 0) {
 #pragma unroll
-              for (int q = 0; q < 9; ++q) oy[q * plane + gx] = fs[q];
+              for (int q = 0; q < 9; ++q) o[q * plane + gx] = fs[q];
+            }
+            if (gy != 0) {
+              float *oy = o + (long long)gy * pitch;
+#pragma unroll
+              for (int q = 0; q < 9; ++q) oy[q * plane] = fs[q];
+              if (gx != 0) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) oy[q * plane + gx] = fs[q];
+              }
+            }
+          } else {
+            // Round the deviations, then let the rest population carry the
+            // remainder of the rounded values (site density kept).
+            using H = decltype(St::enc(0.f));
+            H code[8];
+#pragma unroll
+            for (int q = 1; q < 9; ++q) {
+              const float r = q <= 4 ? A.ref_ax : A.ref_dg;
+              code[q - 1] = St::enc(fs[q] - r);
+              fs[q] = r + St::dec(code[q - 1]);
+            }
+            fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
+            H *od = reinterpret_cast<H *>(A.fdev) + (A.off + x + (long long)y * pitch);
+            o[0] = fs[0];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) od[q * plane] = code[q];
+            if (gx != 0) {
+              o[gx] = fs[0];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) od[q * plane + gx] = code[q];
+            }
+            if (gy != 0) {
+              float *oy = o + (long long)gy * pitch;
+              H *ody = od + (long long)gy * pitch;
+              oy[0] = fs[0];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) ody[q * plane] = code[q];
+              if (gx != 0) {
+                oy[gx] = fs[0];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ody[q * plane + gx] = code[q];
+              }
             }
           }
           // Mass and momentum of the stored site: sum f* = n (by
           // construction), sum f* c = n u* + F/2 (identity of the collision).
           if (!(n > 0.f && n < A.nmax && fabsf(Jx) + fabsf(Jy) < 3.0e38f)) bad = 1;
           acc_m += n;
-          acc_x += Jx + 0.5f * Fx;
-          acc_y += Jy + 0.5f * Fy;
+          if constexpr (!St::kDev) {
+            acc_x += Jx + 0.5f * Fx;
+            acc_y += Jy + 0.5f * Fy;
+          } else {  // momentum of the stored (rounded) populations
+            acc_x += ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
+            acc_y += ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
+          }
         }
       }
       Fx_prev = Fx_cur[1];
@@ -428,11 +542,12 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const SweepArgs A) {
   }
 }
 
-// Copy the periodic images into the ghost band of a padded buffer.
-__global__ void ghost_fill_kernel(float *f, int nx, int ny, int pitch, long long plane, long long off,
+// Copy the periodic images into the ghost band of nplanes padded planes.
+template <typename E>
+__global__ void ghost_fill_kernel(E *f, int nplanes, int nx, int ny, int pitch, long long plane, long long off,
                                   int walls) {
   const int rows = ny + 8;
-  const long long total = 9LL * rows * pitch;
+  const long long total = (long long)nplanes * rows * pitch;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
     const int q = (int)(k / ((long long)rows * pitch));
@@ -449,13 +564,50 @@ __global__ void ghost_fill_kernel(float *f, int nx, int ny, int pitch, long long
   }
 }
 
+// 16-bit storage -> nine float planes: f_0 as stored, f_i = r_i + d_i.
+template <class St, typename H>
+__global__ void widen_kernel(const float *__restrict__ f0, const H *__restrict__ d, float *__restrict__ out,
+                             long long plane, float ref_ax, float ref_dg) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
+       e += (long long)gridDim.x * blockDim.x) {
+    out[e] = f0[e];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) out[q * plane + e] = (q <= 4 ? ref_ax : ref_dg) + St::dec(d[(q - 1) * plane + e]);
+  }
+}
+
+// Nine float planes -> 16-bit storage (the rounding of the step kernel's
+// store, with n the float sum of the nine values).
+template <class St, typename H>
+__global__ void narrow_kernel(const float *__restrict__ in, float *__restrict__ f0, H *__restrict__ d,
+                              long long plane, float ref_ax, float ref_dg) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
+       e += (long long)gridDim.x * blockDim.x) {
+    float f[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = in[q * plane + e];
+    const float n = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+      const float r = q <= 4 ? ref_ax : ref_dg;
+      const H c = St::enc(f[q] - r);
+      d[(q - 1) * plane + e] = c;
+      f[q] = r + St::dec(c);
+    }
+    f0[e] = n - (((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8])));
+  }
+}
+
+namespace {
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point.
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUtensorMap *map) {
+cudaError_t encode_map(CUtensorMapDataType type, int esize, void *base, int pitch, int ny, long long plane,
+                       int nplanes, int box_cols, CUtensorMap *map) {
   static encode_tiled_fn encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -465,44 +617,137 @@ cudaError_t sweep_make_map(void *base, int pitch, int ny, long long plane, CUten
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = (encode_tiled_fn)fn;
   }
-  // 3D view (column, padded row, plane).  One box = the ring slot: kCols
-  // columns x 2 rows x 9 planes, kPairBytes in all.
-  const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ny + 8), 9};
-  const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)plane * 4};
-  const cuuint32_t box[3] = {kCols, 2, 9};
-  static_assert(kCols * 2 * 9 * sizeof(float) == kPairBytes, "TMA box must fill one ring slot");
+  // 3D view (column, padded row, plane); one box = box_cols columns x 2
+  // rows x nplanes planes.
+  const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ny + 8), (cuuint64_t)nplanes};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)plane * esize};
+  const cuuint32_t box[3] = {(cuuint32_t)box_cols, 2, (cuuint32_t)nplanes};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = encode(map, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-void sweep_plan(int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg) {
-  *nstrips = (nx + kMaxW - 1) / kMaxW;
-  *base_w = 4 * (nx / (4 * *nstrips));
-  *extra = (nx - *base_w * *nstrips) / 4;
+int quantum_of(int store) {
+  return store == kStoreF32 ? StoreF32::kQuantum : (store == kStoreBF16 ? StoreBF16::kQuantum : StoreFP16::kQuantum);
+}
+int maxw_of(int store) {
+  return store == kStoreF32 ? StoreF32::kMaxW : (store == kStoreBF16 ? StoreBF16::kMaxW : StoreFP16::kMaxW);
+}
+
+template <class St>
+cudaError_t prepare_one(size_t *smem_bytes) {
+  *smem_bytes = sizeof(SweepSmem<St::kSlotBytes>);
+  return cudaFuncSetAttribute(sweep_step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)*smem_bytes);
+}
+
+template <class St>
+cudaError_t launch_one(const CUtensorMap &m0, const CUtensorMap &m1, const SweepArgs &A, size_t smem,
+                       cudaStream_t st) {
+  dim3 grid((unsigned)A.nstrips, (unsigned)A.nseg);
+  sweep_step_kernel<St><<<grid, kThreads, smem, st>>>(m0, m1, A);
+  return cudaGetLastError();
+}
+
+unsigned elementwise_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
+
+}  // namespace
+
+bool sweep_supported(int store, int nx, int ny) {
+  if (store != kStoreF32 && store != kStoreBF16 && store != kStoreFP16) return false;
+  const double pitch = (double)(((nx + 8 + 31) / 32) * 32);
+  return nx % quantum_of(store) == 0 && nx >= 8 && ny >= 8 && 9.0 * pitch * (double)(ny + 8) < 2147483647.0;
+}
+
+size_t sweep_buffer_bytes(int store, long long plane) {
+  return store == kStoreF32 ? 9 * (size_t)plane * sizeof(float) : (size_t)plane * (sizeof(float) + 8 * 2);
+}
+
+cudaError_t sweep_make_maps(int store, void *base, int pitch, int ny, long long plane, CUtensorMap *m0,
+                            CUtensorMap *m1) {
+  if (store == kStoreF32) {
+    static_assert(StoreF32::kTxBytes == 9 * 2 * kCols * sizeof(float), "TMA box must match the slot");
+    cudaError_t e = encode_map(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, pitch, ny, plane, 9, kCols, m0);
+    *m1 = *m0;
+    return e;
+  }
+  static_assert(StoreBF16::kRestBytes == 2 * kCols * sizeof(float) &&
+                    StoreBF16::kDevBytes == 2 * StoreBF16::kDevCols * 8 * 2,
+                "TMA boxes must match the slot");
+  cudaError_t e = encode_map(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, pitch, ny, plane, 1, kCols, m0);
+  if (e != cudaSuccess) return e;
+  void *dev = static_cast<char *>(base) + (size_t)plane * sizeof(float);
+  return encode_map(store == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, dev,
+                    pitch, ny, plane, 8, StoreBF16::kDevCols, m1);
+}
+
+void sweep_plan(int store, int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg) {
+  const int qn = quantum_of(store), maxw = maxw_of(store);
+  *nstrips = (nx + maxw - 1) / maxw;
+  *base_w = qn * (nx / (qn * *nstrips));
+  *extra = (nx - *base_w * *nstrips) / qn;
   *seg_h = ny < kSeg ? ny : kSeg;
   *nseg = (ny + *seg_h - 1) / *seg_h;
 }
 
-cudaError_t sweep_prepare(size_t *smem_bytes) {
-  *smem_bytes = sizeof(SweepSmem);
-  return cudaFuncSetAttribute(sweep_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)*smem_bytes);
+cudaError_t sweep_prepare(int store, size_t *smem_bytes) {
+  switch (store) {
+    case kStoreF32: return prepare_one<StoreF32>(smem_bytes);
+    case kStoreBF16: return prepare_one<StoreBF16>(smem_bytes);
+    case kStoreFP16: return prepare_one<StoreFP16>(smem_bytes);
+  }
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sweep(const CUtensorMap &tin, const SweepArgs &A, size_t smem, cudaStream_t st) {
-  dim3 grid((unsigned)A.nstrips, (unsigned)A.nseg);
-  sweep_step_kernel<<<grid, kThreads, smem, st>>>(tin, A);
+cudaError_t launch_sweep(int store, const CUtensorMap &m0, const CUtensorMap &m1, const SweepArgs &A,
+                         size_t smem, cudaStream_t st) {
+  switch (store) {
+    case kStoreF32: return launch_one<StoreF32>(m0, m1, A, smem, st);
+    case kStoreBF16: return launch_one<StoreBF16>(m0, m1, A, smem, st);
+    case kStoreFP16: return launch_one<StoreFP16>(m0, m1, A, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,
+                              long long off, int walls, cudaStream_t st) {
+  const unsigned blocks = elementwise_blocks((long long)nplanes * (ny + 8) * pitch);
+  if (elem_bytes == 4)
+    ghost_fill_kernel<uint32_t><<<blocks, 256, 0, st>>>((uint32_t *)f, nplanes, nx, ny, pitch, plane, off, walls);
+  else if (elem_bytes == 2)
+    ghost_fill_kernel<uint16_t><<<blocks, 256, 0, st>>>((uint16_t *)f, nplanes, nx, ny, pitch, plane, off, walls);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-cudaError_t launch_ghost_fill(float *f, int nx, int ny, int pitch, long long plane, long long off,
-                              int walls, cudaStream_t st) {
-  const long long total = 9LL * (ny + 8) * pitch;
-  const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 4096);
-  ghost_fill_kernel<<<blocks, 256, 0, st>>>(f, nx, ny, pitch, plane, off, walls);
+cudaError_t launch_widen(int store, const void *buf, float *wide, long long plane, float ref_ax, float ref_dg,
+                         cudaStream_t st) {
+  const float *f0 = static_cast<const float *>(buf);
+  const void *d = static_cast<const char *>(buf) + (size_t)plane * sizeof(float);
+  const unsigned blocks = elementwise_blocks(plane);
+  if (store == kStoreBF16)
+    widen_kernel<StoreBF16><<<blocks, 256, 0, st>>>(f0, (const __nv_bfloat16 *)d, wide, plane, ref_ax, ref_dg);
+  else if (store == kStoreFP16)
+    widen_kernel<StoreFP16><<<blocks, 256, 0, st>>>(f0, (const __half *)d, wide, plane, ref_ax, ref_dg);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(int store, const float *wide, void *buf, long long plane, float ref_ax, float ref_dg,
+                          cudaStream_t st) {
+  float *f0 = static_cast<float *>(buf);
+  void *d = static_cast<char *>(buf) + (size_t)plane * sizeof(float);
+  const unsigned blocks = elementwise_blocks(plane);
+  if (store == kStoreBF16)
+    narrow_kernel<StoreBF16><<<blocks, 256, 0, st>>>(wide, f0, (__nv_bfloat16 *)d, plane, ref_ax, ref_dg);
+  else if (store == kStoreFP16)
+    narrow_kernel<StoreFP16><<<blocks, 256, 0, st>>>(wide, f0, (__half *)d, plane, ref_ax, ref_dg);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

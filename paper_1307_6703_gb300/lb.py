@@ -186,12 +186,13 @@ class Solver:
     def __init__(self, nx: int, ny: int, *, walls: bool = True, precision: int = LB_FP32,
                  a: float, b: float, T: float, kappa: float, tau: float,
                  A0: float = 0.0, lam: float = 0.0, u_bot: float = 0.0, u_top: float = 0.0,
-                 N: float = 0.5, Q: float = 1.0, stream: int | None = None):
+                 N: float = 0.5, Q: float = 1.0, rho_ref: float = 0.0, stream: int | None = None):
         self.nx, self.ny, self.precision = nx, ny, precision
         self.params = lb_params(nx, ny, int(walls), precision, a, b, T, kappa, tau, A0, lam,
-                                u_bot, u_top, N, Q, 0.0, stream)
+                                u_bot, u_top, N, Q, rho_ref, stream)
         self.h = lb_create(self.params)
         self.dtype = np.float64 if precision == LB_FP64 else np.float32
+        self.dev16 = precision in (LB_BF16DEV, LB_FP16DEV)
 
     def init_noise(self, seed: int, rho_mean: float, amp: float):
         lb_init(self.h, 0, seed, rho_mean, amp)
@@ -216,12 +217,27 @@ class Solver:
     def reduce(self):
         return lb_reduce(self.h)
 
-    def get_state(self) -> np.ndarray:
+    def get_state(self):
+        """[9][ny][nx] populations; for 16-bit storage the pair (rest plane
+        float32 [ny][nx], raw deviation bits uint16 [8][ny][nx])."""
+        if self.dev16:
+            S = self.nx * self.ny
+            buf = np.empty(S * 20, dtype=np.uint8)
+            lb_get_state(self.h, buf)
+            f0 = buf[:4 * S].view(np.float32).reshape(self.ny, self.nx).copy()
+            d = buf[4 * S:].view(np.uint16).reshape(8, self.ny, self.nx).copy()
+            return f0, d
         buf = np.empty((9, self.ny, self.nx), dtype=self.dtype)
         lb_get_state(self.h, buf)
         return buf
 
-    def set_state(self, f: np.ndarray, step: int = 0):
+    def set_state(self, f, step: int = 0):
+        if self.dev16:
+            f0, d = f
+            buf = np.concatenate([np.ascontiguousarray(f0, dtype=np.float32).view(np.uint8).ravel(),
+                                  np.ascontiguousarray(d, dtype=np.uint16).view(np.uint8).ravel()])
+            lb_set_state(self.h, buf, step)
+            return self
         lb_set_state(self.h, np.ascontiguousarray(f, dtype=self.dtype), step)
         return self
 

@@ -51,7 +51,8 @@ def test_create_rejects_bad_parameters_without_gpu(lib):
     base = dict(nx=8, ny=8, walls=1, precision=1, a=0.375, b=1 / 3, T=0.3, kappa=0.1,
                 tau=1.0, A0=0.0, lambda_=0.0, u_bot=0.0, u_top=0.0, N=0.5, Q=1.0,
                 rho_ref=0.0, stream=None)
-    for bad in (dict(tau=0.5), dict(nx=0), dict(walls=1, ny=2), dict(precision=7), dict(T=-1.0)):
+    for bad in (dict(tau=0.5), dict(nx=0), dict(walls=1, ny=2), dict(precision=7), dict(T=-1.0),
+                dict(precision=2, nx=12), dict(precision=3, ny=4), dict(precision=2, rho_ref=-1.0)):
         p = lb_params(**{**base, **bad})
         with pytest.raises(LBError) as ei:
             lb_create(p)

@@ -1,0 +1,186 @@
+"""16-bit deviation storage (LB_BF16DEV, LB_FP16DEV) against the oracle's
+model of the same format (FP64 step, then the format's rounding).
+
+The GPU takes each rounding decision on its FP32 value and the oracle on its
+FP64 value, so a stored deviation may differ by one unit in the last place
+where the exact value lies within FP32 error of a rounding midpoint; every
+other stored deviation must match exactly.  Over many steps the GPU's
+distance from the exact-format oracle is held below the format's own error
+(the distance between the exact-format and the full-precision oracle), and
+mass is conserved to FP32 round-off.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import decode_dev, decode_state, dev16_solver, oracle_for, rel_err
+
+pytestmark = pytest.mark.gpu
+
+from paper_1307_6703_gb300 import LB_BF16DEV, LB_FP16DEV  # noqa: E402
+from paper_1307_6703_gb300.workloads import C1, C2, C4, noise_field, slab_field  # noqa: E402
+
+FORMATS = [(LB_BF16DEV, "bf16"), (LB_FP16DEV, "fp16")]
+RHO_REF = 1.0  # the vdW critical density 1/(3b) of the paper's set
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def _ulp(x, fmt):
+    p, emin = oracle.FORMATS[fmt]
+    ax = np.abs(x)
+    e = np.where(ax > 0, np.floor(np.log2(np.where(ax > 0, ax, 1.0))), emin)
+    return 2.0 ** (np.maximum(e, emin) - p + 1)
+
+
+def _check_rounding(dg, do, unrounded, fmt, eps):
+    """dg: GPU deviations, do: oracle's rounded deviations, unrounded: the
+    oracle's values before rounding.  Returns the mismatch fraction."""
+    mism = dg != do
+    if mism.any():
+        a, b, u = dg[mism], do[mism], unrounded[mism]
+        assert np.all(np.abs(a - b) <= _ulp(np.maximum(np.abs(a), np.abs(b)), fmt) * (1 + 1e-9)), \
+            "stored deviations differ by more than one unit in the last place"
+        assert np.all(np.abs(u - 0.5 * (a + b)) <= eps), \
+            "a rounding decision differs away from a rounding midpoint"
+    return float(mism.mean())
+
+
+def _step_case(w, prec, fmt, n0, eps_rel=2e-6, steps_before=0):
+    s = dev16_solver(w, prec, RHO_REF).init_fields(n0)
+    if steps_before:
+        s.step(steps_before)
+    f0, d = s.get_state()
+    F = decode_state(f0, d, fmt, RHO_REF)
+    ref = oracle_for(w).set_state(F).step(1)
+    q, unr = oracle.quantize(ref.f, fmt, RHO_REF, want_unrounded=True)
+    s.step(1)
+    g0, gd = s.get_state()
+    s.close()
+    r = oracle.reference_pops(RHO_REF)
+    dg = decode_dev(gd, fmt)
+    do = q[1:] - r[1:, None, None]
+    eps = eps_rel * np.abs(F).max()
+    frac = _check_rounding(dg, do, unr, fmt, eps)
+    # the rest population carries the remainder of the rounded values
+    slack = np.abs(dg - do).sum(axis=0) + eps
+    assert np.all(np.abs(g0 - q[0]) <= slack)
+    return frac
+
+
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+def test_dev16_init_matches_oracle_format(prec, fmt):
+    """lb_init mode 1 (FP32 equilibrium, then the format) = the oracle's
+    equilibrium passed through the format, decision by decision."""
+    w = C1.with_(nx=248, ny=67, walls=True, u_bot=-0.04, u_top=0.04)
+    n0 = noise_field(w)
+    s = dev16_solver(w, prec, RHO_REF).init_fields(n0)
+    f0, d = s.get_state()
+    s.close()
+    ref = oracle_for(w).init_fields(n0)
+    q, unr = oracle.quantize(ref.f, fmt, RHO_REF, want_unrounded=True)
+    r = oracle.reference_pops(RHO_REF)
+    frac = _check_rounding(decode_dev(d, fmt), q[1:] - r[1:, None, None], unr, fmt,
+                           1e-7 * np.abs(ref.f).max())
+    assert frac <= 1e-3
+    assert np.abs(f0 - q[0]).max() <= 1e-6
+
+
+CASES = [
+    # (nx, ny, walls, u_w): one and several strips, ragged strips and segments
+    (8, 8, True, 0.02),
+    (8, 8, False, 0.0),
+    (248, 67, True, 0.04),
+    (304, 130, False, 0.0),
+    (304, 130, True, 0.05),
+]
+
+
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}")
+def test_dev16_one_step_parity(case, prec, fmt):
+    nx, ny, walls, u_w = case
+    w = C1.with_(nx=nx, ny=ny, walls=walls, u_bot=-u_w, u_top=u_w, lam=float(nx // 2))
+    frac = _step_case(w, prec, fmt, noise_field(w), steps_before=5)
+    assert frac <= 1e-2
+
+
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+def test_dev16_full_size_one_step(prec, fmt):
+    """4096x1024 (the benchmark lattice, same launch path), every site."""
+    w = C4
+    frac = _step_case(w, prec, fmt, noise_field(w))
+    assert frac <= 1e-2
+
+
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+def test_dev16_multi_step_within_format_error(prec, fmt):
+    """Sheared slab, 200 steps: the GPU's distance from the exact-format
+    oracle stays below the format's own error (exact-format oracle against
+    the full-precision oracle)."""
+    w = C2(0.05).with_(nx=256, ny=64, lam=64.0)
+    n0 = slab_field(w.nx, w.ny, 1.46, 0.58)
+    steps = 200
+    s = dev16_solver(w, prec, RHO_REF).init_fields(n0).step(steps)
+    n, _, _ = s.moments()
+    s.close()
+    exact = oracle_for(w).init_fields(n0).quantize(fmt, RHO_REF).step(steps, storage=(fmt, RHO_REF))
+    full = oracle_for(w).init_fields(n0).step(steps)
+    ne, nf = exact.moments()[0], full.moments()[0]
+    gpu_err, fmt_err = rel_err(n, ne), rel_err(ne, nf)
+    print(f"{fmt}: GPU vs exact-format oracle {gpu_err:.3e}; format vs full precision {fmt_err:.3e}")
+    assert gpu_err <= 0.5 * fmt_err + 1e-6
+
+
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+def test_dev16_mass_conservation(prec, fmt):
+    """1000 sheared steps: total mass to FP32 round-off, both through the
+    step kernel's records and the exact sum over the stored state."""
+    w = C2(0.05)
+    s = dev16_solver(w, prec, RHO_REF).init_noise(w.seed, w.rho_mean, w.noise)
+    rc, (m0, _, _) = s.reduce()
+    assert rc == 0
+    s.step(1000)
+    rc, (m1, _, _) = s.reduce()
+    assert rc == 0
+    assert abs(m1 - m0) / m0 < 1e-6
+    # exact FP64 sum over the decoded state (a restore invalidates the records)
+    state = s.get_state()
+    s.set_state(state, step=1000)
+    rc, (m2, _, _) = s.reduce()
+    assert rc == 0 and abs(m2 - m1) / m1 < 1e-6
+    F = decode_state(*state, fmt, RHO_REF)
+    assert abs(F.sum() - m2) / m2 < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+def test_dev16_checkpoint_resume_is_bitwise(prec, fmt):
+    w = C2(0.05).with_(nx=96, ny=48)
+    a = dev16_solver(w, prec, RHO_REF).init_noise(5, w.rho_mean, w.noise).step(200)
+    b = dev16_solver(w, prec, RHO_REF).init_noise(5, w.rho_mean, w.noise).step(100)
+    state = b.get_state()
+    b.close()
+    c = dev16_solver(w, prec, RHO_REF).set_state(state, step=100).step(100)
+    sa, sc = a.get_state(), c.get_state()
+    assert np.array_equal(sa[0], sc[0]) and np.array_equal(sa[1], sc[1])
+    a.close()
+    c.close()
+
+
+def test_dev16_default_reference_is_critical_density():
+    """rho_ref = 0 selects 1/(3b): same trajectory as rho_ref = 1 for b = 1/3."""
+    w = C2(0.05).with_(nx=64, ny=32)
+    a = dev16_solver(w, LB_BF16DEV, 0.0).init_noise(1, w.rho_mean, w.noise).step(20)
+    b = dev16_solver(w, LB_BF16DEV, 1.0).init_noise(1, w.rho_mean, w.noise).step(20)
+    sa, sb = a.get_state(), b.get_state()
+    assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+    a.close()
+    b.close()
