@@ -532,12 +532,26 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant
   red[2 * kThreads + t] = (double)acc_y;
   red[3 * kThreads + t] = (double)bad;
   __syncthreads();
-  if (t == 0) {
-    double *out = A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+  // Warp 0 (a full warp) sums them in a fixed order: lane l takes columns
+  // l, l+32, l+64, l+96, then a shuffle tree.  FP64 throughput is low on
+  // this part, so the tree keeps the FP64 work off the critical path.
+  if (t < 32) {
+    double v[4];
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
       double sum = 0.0;
-      for (int i = 0; i < kThreads; ++i) sum += red[q * kThreads + i];
-      out[q] = sum;
+      for (int i = t; i < kThreads; i += 32) sum += red[q * kThreads + i];
+      v[q] = sum;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    }
+    if (t == 0) {
+      double *out = A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] = v[q];
     }
   }
 }
