@@ -221,6 +221,10 @@ def run_ours(args):
     b_alg = B_ALG[args.precision]
     s.init_noise(w.seed + rank, w.rho_mean, w.noise)
 
+    # Tiling chosen by the library's autotuner (state restored afterwards).
+    from paper_1307_6703_gb300 import lb_autotune
+    seg_h = lb_autotune(s.h, 20)
+
     # ------------------------------------------------ device-resident timing
     lb_step(s.h, args.warmup)
     torch.cuda.synchronize()
@@ -275,7 +279,7 @@ def run_ours(args):
             "storage": args.precision,
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "walls": True,
                        "u_w": w.u_top, "A0": w.A0, "lambda": w.lam, "T_over_Tc": 0.95,
-                       "tau": w.tau, "parallelism": f"replicas{world}",
+                       "tau": w.tau, "parallelism": f"replicas{world}", "seg_h": seg_h,
                        "l2": f"inputs larger than L2: two {b_alg / 2 * sites / 1e6:.0f} MB population buffers",
                        "unstable_after_timing": unstable},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

@@ -167,6 +167,18 @@ int lb_get_state(lb_handle *h, void *buf, size_t *bytes);
  * state is bitwise identical to never having stopped.                      */
 int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step);
 
+/* Tiling autotuner (a performance control of this library; the paper has
+ * no counterpart).  Times `steps` steps of the strip-sweep kernel for each
+ * candidate segment height (rows per CTA, which trades CTAs per SM against
+ * re-read warm-up rows), keeps the fastest for later lb_step calls and
+ * writes it to *seg_h (may be NULL; 0 when the handle uses the tile kernel,
+ * which has no tiling choice).  The state and the step counter are restored
+ * afterwards: the trajectory is the same as without the call.  Needs one
+ * extra state buffer of device memory while it runs; synchronises the
+ * stream.  Errors: LB_ERR_ARG (steps < 1), LB_ERR_STATE, LB_ERR_CUDA,
+ * LB_ERR_OOM.                                                              */
+int lb_autotune(lb_handle *h, int steps, int32_t *seg_h);
+
 /* Number of steps taken since lb_init / lb_set_state. */
 int lb_get_step(const lb_handle *h, int64_t *step);
 

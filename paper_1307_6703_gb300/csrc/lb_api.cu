@@ -1,5 +1,6 @@
 // lb_api.cu -- host side of the C ABI declared in include/lb.h, plus the
 // deterministic FP64 reduction kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -591,6 +592,79 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step) {
   h->cta_valid = false;
   h->step = step;
   h->initialised = true;
+  return LB_OK;
+}
+
+int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
+  if (!h) return LB_ERR_ARG;
+  if (steps < 1) return fail(h, LB_ERR_ARG, "lb_autotune: steps must be >= 1");
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_autotune: state not initialised");
+  if (!h->sweep) {
+    if (seg_h) *seg_h = 0;
+    return LB_OK;  // the tile kernel has no tiling choice
+  }
+  // Candidate segment heights (rows per CTA): fewer rows give more CTAs per
+  // SM and more warm-up rows; the best trade depends on the lattice and on
+  // the storage's occupancy.
+  const int cand[] = {24, 32, 40, 48, 52, 56, 64, 72, 80, 96, 128, 192, 256};
+  const int ny = h->p.ny;
+  int max_nseg = h->sweep_nseg;
+  for (int c : cand) max_nseg = std::max(max_nseg, (ny + std::min(c, ny) - 1) / std::min(c, ny));
+  // Per-CTA records sized for the smallest segments (kept afterwards).
+  double *cta = nullptr;
+  LB_CUDA(h, cudaStreamSynchronize(h->st));
+  LB_CUDA(h, cudaMalloc((void **)&cta, 4 * sizeof(double) * (size_t)h->sweep_nstrips * max_nseg));
+  cudaFree(h->d_cta);
+  h->d_cta = cta;
+  h->cta_valid = false;
+
+  const size_t buf_bytes = lbk::sweep_buffer_bytes(h->store, h->plane);
+  const int cur0 = h->cur;
+  const int64_t step0 = h->step;
+  const int seg0 = h->sweep_seg;
+  void *save = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = seg0, rc = LB_OK;
+  float best_ms = 3.0e38f;
+  cudaError_t e = cudaMalloc(&save, buf_bytes);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(save, h->f[cur0], buf_bytes, cudaMemcpyDeviceToDevice, h->st);
+  int last = -1;
+  for (int c : cand) {
+    if (e != cudaSuccess || rc != LB_OK) break;
+    const int sh = std::min(c, ny);
+    if (sh == last) continue;
+    last = sh;
+    h->sweep_seg = sh;
+    h->sweep_nseg = (ny + sh - 1) / sh;
+    float ms = 0.f;
+    rc = lb_step(h, 2);  // warm-up
+    if (rc == LB_OK) e = cudaEventRecord(e0, h->st);
+    if (rc == LB_OK && e == cudaSuccess) rc = lb_step(h, steps);
+    if (rc == LB_OK && e == cudaSuccess) e = cudaEventRecord(e1, h->st);
+    if (rc == LB_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (rc == LB_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == LB_OK && e == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = sh;
+    }
+    // back to the saved state for the next candidate
+    h->cur = cur0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->f[cur0], save, buf_bytes, cudaMemcpyDeviceToDevice, h->st);
+  }
+  h->cur = cur0;
+  h->step = step0;
+  h->sweep_seg = (rc == LB_OK && e == cudaSuccess) ? best : seg0;
+  h->sweep_nseg = (ny + h->sweep_seg - 1) / h->sweep_seg;
+  h->cta_valid = false;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFree(save);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lb_autotune");
+  if (rc != LB_OK) return rc;
+  if (seg_h) *seg_h = h->sweep_seg;
   return LB_OK;
 }
 

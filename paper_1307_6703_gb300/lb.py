@@ -77,9 +77,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_last_error.argtypes = [P]
         lib.lb_last_error.restype = C.c_char_p
         lib.lb_reduce_noalloc.argtypes = [P, C.c_int, C.c_int32, C.c_int32, C.c_double, P, P, P]
+        lib.lb_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
         for name in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_reduce",
                      "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy",
-                     "lb_reduce_noalloc"):
+                     "lb_reduce_noalloc", "lb_autotune"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -173,6 +174,13 @@ def lb_reduce_noalloc(f, precision: int, nx: int, ny: int, b: float, out, flag=N
     return rc
 
 
+def lb_autotune(h, steps: int = 20) -> int:
+    """Returns the chosen segment height (0: tile kernel, nothing to tune)."""
+    seg = C.c_int32(0)
+    _check(load_library().lb_autotune(h, steps, C.byref(seg)), h)
+    return seg.value
+
+
 def lb_last_error(h) -> str:
     s = load_library().lb_last_error(h)
     return s.decode() if s else ""
@@ -216,6 +224,9 @@ class Solver:
 
     def reduce(self):
         return lb_reduce(self.h)
+
+    def autotune(self, steps: int = 20) -> int:
+        return lb_autotune(self.h, steps)
 
     def get_state(self):
         """[9][ny][nx] populations; for 16-bit storage the pair (rest plane
