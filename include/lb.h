@@ -179,6 +179,47 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step);
  * LB_ERR_OOM.                                                              */
 int lb_autotune(lb_handle *h, int steps, int32_t *seg_h);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: many independent lattices (different sizes and physical
+ * parameters) advanced together, one kernel launch per step over a work
+ * list of every instance's strips and segments (longest first), pairs of
+ * steps replayed as a CUDA graph.  The paper solves one lattice at a time;
+ * this is a throughput layer for parameter sweeps (e.g. over T, A0, lambda
+ * and the wall velocity).
+ * ------------------------------------------------------------------------ */
+typedef struct lb_batch lb_batch;
+
+/* Create `count` instances from ps[0..count-1].  All share one stream and
+ * one precision (LB_FP32, LB_BF16DEV or LB_FP16DEV) and must satisfy the
+ * sweep kernel's size rules (nx a multiple of 4, or of 8 for 16-bit
+ * storage; nx, ny >= 8).  Errors: LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM
+ * (message from lb_batch_last_error(NULL)).                                */
+int lb_batch_create(const lb_params *ps, int32_t count, lb_batch **out);
+
+/* Instance i as an lb_handle, for lb_init, lb_moments, lb_reduce,
+ * lb_get_state, lb_set_state, lb_get_step and lb_autotune (not lb_destroy:
+ * the batch owns it).  Stepping it alone with lb_step is allowed.  NULL if
+ * i is out of range.                                                       */
+lb_handle *lb_batch_handle(lb_batch *b, int32_t i);
+
+/* Advance every instance by nsteps >= 0 steps (asynchronous on the stream).
+ * Afterwards lb_reduce of each instance costs one small kernel.
+ * Errors: LB_ERR_STATE (an instance not initialised), LB_ERR_CUDA.         */
+int lb_batch_step(lb_batch *b, int64_t nsteps);
+
+/* Tiling autotuner for the batch: times `steps` batch steps for each
+ * candidate segment height, first one height for all instances, then per
+ * lattice class (ny <= 96, <= 160, > 160) with the others fixed, and keeps
+ * the fastest.  seg_h (count entries, may be NULL) receives each instance's
+ * choice.  States and step counters are restored.  Synchronises.          */
+int lb_batch_autotune(lb_batch *b, int steps, int32_t *seg_h);
+
+/* Release the batch and all its instances.  NULL is accepted. */
+int lb_batch_destroy(lb_batch *b);
+
+/* Last error message of a batch call (NULL: of the last lb_batch_create). */
+const char *lb_batch_last_error(const lb_batch *b);
+
 /* Number of steps taken since lb_init / lb_set_state. */
 int lb_get_step(const lb_handle *h, int64_t *step);
 

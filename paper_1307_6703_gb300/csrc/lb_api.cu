@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lb.h"
 #include "lb_device.cuh"
@@ -32,6 +33,8 @@ struct lb_handle {
   size_t sweep_smem = 0;
   int sweep_seg = 64, sweep_nstrips = 0, sweep_nseg = 0, sweep_base = 0, sweep_extra = 0;
   double *d_cta = nullptr;       // per-CTA partials written by the sweep kernel
+  size_t cta_bytes = 0;
+  int plan_gen = 0;              // bumped when the tiling or the record array changes
   bool cta_valid = false;        // d_cta describes the current state
   int *d_err = nullptr;          // bounded-wait failure flag
   void *f[2] = {nullptr, nullptr};
@@ -281,6 +284,31 @@ lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   return A;
 }
 
+// Segment height of a sweep handle; the per-CTA record array must already
+// be large enough (see ensure_records).
+void set_segments(lb_handle *h, int seg_h) {
+  h->sweep_seg = std::max(1, std::min(seg_h, h->p.ny));
+  h->sweep_nseg = (h->p.ny + h->sweep_seg - 1) / h->sweep_seg;
+  h->cta_valid = false;
+  h->plan_gen++;
+}
+
+// Grow the per-CTA record array to hold `nseg` segments of records.
+cudaError_t ensure_records(lb_handle *h, int nseg) {
+  const size_t need = 4 * sizeof(double) * (size_t)h->sweep_nstrips * nseg;
+  if (need <= h->cta_bytes) return cudaSuccess;
+  double *p = nullptr;
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&p, need);
+  if (e != cudaSuccess) return e;
+  cudaFree(h->d_cta);
+  h->d_cta = p;
+  h->cta_bytes = need;
+  h->cta_valid = false;
+  h->plan_gen++;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -344,7 +372,8 @@ int lb_create(const lb_params *p, lb_handle **out) {
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
   if (e == cudaSuccess && h->sweep) {
-    e = cudaMalloc((void **)&h->d_cta, 4 * sizeof(double) * (size_t)h->sweep_nstrips * h->sweep_nseg);
+    h->cta_bytes = 4 * sizeof(double) * (size_t)h->sweep_nstrips * h->sweep_nseg;
+    e = cudaMalloc((void **)&h->d_cta, h->cta_bytes);
     if (e == cudaSuccess) e = lbk::sweep_prepare(h->store, &h->sweep_smem);
     for (int b = 0; b < 2 && e == cudaSuccess; b++)
       e = lbk::sweep_make_maps(h->store, h->f[b], h->pitch, p->ny, h->plane, &h->tmap[b][0], &h->tmap[b][1]);
@@ -611,11 +640,7 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   int max_nseg = h->sweep_nseg;
   for (int c : cand) max_nseg = std::max(max_nseg, (ny + std::min(c, ny) - 1) / std::min(c, ny));
   // Per-CTA records sized for the smallest segments (kept afterwards).
-  double *cta = nullptr;
-  LB_CUDA(h, cudaStreamSynchronize(h->st));
-  LB_CUDA(h, cudaMalloc((void **)&cta, 4 * sizeof(double) * (size_t)h->sweep_nstrips * max_nseg));
-  cudaFree(h->d_cta);
-  h->d_cta = cta;
+  LB_CUDA(h, ensure_records(h, max_nseg));
   h->cta_valid = false;
 
   const size_t buf_bytes = lbk::sweep_buffer_bytes(h->store, h->plane);
@@ -636,8 +661,7 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
     const int sh = std::min(c, ny);
     if (sh == last) continue;
     last = sh;
-    h->sweep_seg = sh;
-    h->sweep_nseg = (ny + sh - 1) / sh;
+    set_segments(h, sh);
     float ms = 0.f;
     rc = lb_step(h, 2);  // warm-up
     if (rc == LB_OK) e = cudaEventRecord(e0, h->st);
@@ -655,9 +679,7 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   }
   h->cur = cur0;
   h->step = step0;
-  h->sweep_seg = (rc == LB_OK && e == cudaSuccess) ? best : seg0;
-  h->sweep_nseg = (ny + h->sweep_seg - 1) / h->sweep_seg;
-  h->cta_valid = false;
+  set_segments(h, (rc == LB_OK && e == cudaSuccess) ? best : seg0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   cudaFree(save);
   if (e0) cudaEventDestroy(e0);
@@ -695,6 +717,332 @@ int lb_destroy(lb_handle *h) {
 const char *lb_last_error(const lb_handle *h) {
   if (!h) return g_create_err.c_str();
   return h->err.c_str();
+}
+
+}  // extern "C"
+
+/* ------------------------------------------------------------------------
+ * Batched sweep over many independent lattices (one launch per step).
+ * ------------------------------------------------------------------------ */
+
+struct lb_batch {
+  std::vector<lb_handle *> hs;
+  cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture
+  int store = 0;
+  size_t smem = 0;
+  lbk::BatchItem *d_items = nullptr;
+  lbk::SweepArgs *d_args = nullptr;
+  CUtensorMap *d_maps = nullptr;
+  int nitems = 0, items_cap = 0;
+  std::vector<int> par0;  // input-buffer parity of each instance at kpar = 0
+  std::vector<int> gen;   // plan_gen of each instance when the list was built
+  int kpar = 0;           // parity of the next batch step
+  bool dirty = true;      // device work list out of date
+  cudaGraphExec_t graph = nullptr;  // two consecutive steps, kpar 0 then 1
+  std::string err;
+};
+
+namespace {
+
+int bfail(lb_batch *b, int code, const std::string &msg) {
+  if (b) b->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+#define LB_BCUDA(b, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,                \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+// Rebuild the work list, the per-instance arguments and tensor maps.
+int batch_rebuild(lb_batch *b) {
+  const int n = (int)b->hs.size();
+  std::vector<lbk::BatchItem> items;
+  std::vector<lbk::SweepArgs> args(2 * (size_t)n);
+  std::vector<CUtensorMap> maps(4 * (size_t)n);
+  b->par0.assign(n, 0);
+  b->gen.assign(n, 0);
+  for (int i = 0; i < n; i++) {
+    lb_handle *h = b->hs[i];
+    b->par0[i] = h->cur;
+    b->gen[i] = h->plan_gen;
+    for (int p = 0; p < 2; p++) {
+      args[2 * i + p] = sweep_args(h, (float *)h->f[p ^ 1]);
+      maps[4 * i + 2 * p + 0] = h->tmap[p][0];
+      maps[4 * i + 2 * p + 1] = h->tmap[p][1];
+    }
+    for (int sg = 0; sg < h->sweep_nseg; sg++)
+      for (int sp = 0; sp < h->sweep_nstrips; sp++)
+        items.push_back({i, sp, sg, sg * h->sweep_nstrips + sp, h->cur});
+  }
+  // Longest CTAs first (rows of the segment plus the 7-row warm-up), so the
+  // block scheduler fills the tail with the short ones.
+  auto rows = [&](const lbk::BatchItem &it) {
+    const lb_handle *h = b->hs[it.inst];
+    const int ya = it.seg * h->sweep_seg;
+    return std::min(h->p.ny, ya + h->sweep_seg) - ya;
+  };
+  std::stable_sort(items.begin(), items.end(),
+                   [&](const lbk::BatchItem &x, const lbk::BatchItem &y) { return rows(x) > rows(y); });
+  if ((int)items.size() > b->items_cap) {
+    LB_BCUDA(b, cudaStreamSynchronize(b->st));
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    LB_BCUDA(b, cudaMalloc((void **)&b->d_items, items.size() * sizeof(lbk::BatchItem)));
+    b->items_cap = (int)items.size();
+  }
+  b->nitems = (int)items.size();
+  LB_BCUDA(b, cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(lbk::BatchItem),
+                              cudaMemcpyHostToDevice, b->st));
+  LB_BCUDA(b, cudaMemcpyAsync(b->d_args, args.data(), args.size() * sizeof(lbk::SweepArgs),
+                              cudaMemcpyHostToDevice, b->st));
+  LB_BCUDA(b, cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                              cudaMemcpyHostToDevice, b->st));
+  LB_BCUDA(b, cudaStreamSynchronize(b->st));  // host arrays go out of scope
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->kpar = 0;
+  b->dirty = false;
+  return LB_OK;
+}
+
+// Two consecutive batch steps (kpar 0, then 1) as one CUDA graph.
+int batch_graph(lb_batch *b) {
+  if (b->graph) return LB_OK;
+  cudaGraph_t g = nullptr;
+  LB_BCUDA(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e1 = lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 0, b->smem, b->cap);
+  cudaError_t e2 = lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 1, b->smem, b->cap);
+  cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return bfail(b, LB_ERR_CUDA, "lb_batch_step: graph capture failed");
+  }
+  cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return bfail(b, LB_ERR_CUDA, std::string("lb_batch_step: graph instantiation: ") + cudaGetErrorString(e));
+  }
+  return LB_OK;
+}
+
+// Whether every instance's buffers are where the device work list expects.
+bool batch_in_sync(const lb_batch *b) {
+  if (b->dirty) return false;
+  for (size_t i = 0; i < b->hs.size(); i++)
+    if (b->hs[i]->cur != (b->par0[i] ^ b->kpar) || b->hs[i]->plan_gen != b->gen[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_create(const lb_params *ps, int32_t count, lb_batch **out) {
+  if (!ps || !out || count < 1) return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < count; i++) {
+    if (ps[i].stream != ps[0].stream)
+      return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: all instances must share one stream");
+    if (ps[i].precision != ps[0].precision)
+      return bfail(nullptr, LB_ERR_ARG, "lb_batch_create: all instances must share one precision");
+    if (ps[i].precision == LB_FP64 || !lbk::sweep_supported(ps[i].precision, ps[i].nx, ps[i].ny))
+      return bfail(nullptr, LB_ERR_ARG,
+                   "lb_batch_create: every instance must run the sweep kernel (FP32 or 16-bit storage, nx a "
+                   "multiple of 4 (8 for 16-bit storage), nx, ny >= 8)");
+  }
+  lb_batch *b = new (std::nothrow) lb_batch();
+  if (!b) return bfail(nullptr, LB_ERR_OOM, "lb_batch_create: host allocation failed");
+  b->st = (cudaStream_t)ps[0].stream;
+  b->store = ps[0].precision;
+  for (int i = 0; i < count; i++) {
+    lb_handle *h = nullptr;
+    int rc = lb_create(&ps[i], &h);
+    if (rc != LB_OK) {
+      std::string m = std::string("lb_batch_create: instance ") + std::to_string(i) + ": " + g_create_err;
+      lb_batch_destroy(b);
+      return bfail(nullptr, rc, m);
+    }
+    b->hs.push_back(h);
+  }
+  cudaError_t e = lbk::sweep_prepare(b->store, &b->smem);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_args, 2 * (size_t)count * sizeof(lbk::SweepArgs));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_maps, 4 * (size_t)count * sizeof(CUtensorMap));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    std::string m = std::string("lb_batch_create: ") + cudaGetErrorString(e);
+    lb_batch_destroy(b);
+    return bfail(nullptr, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, m);
+  }
+  *out = b;
+  return LB_OK;
+}
+
+lb_handle *lb_batch_handle(lb_batch *b, int32_t i) {
+  if (!b || i < 0 || i >= (int)b->hs.size()) return nullptr;
+  return b->hs[i];  // changes made through it are detected by lb_batch_step
+}
+
+int lb_batch_step(lb_batch *b, int64_t nsteps) {
+  if (!b) return LB_ERR_ARG;
+  if (nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: nsteps < 0");
+  for (lb_handle *h : b->hs)
+    if (!h->initialised) return bfail(b, LB_ERR_STATE, "lb_batch_step: an instance is not initialised");
+  if (nsteps == 0) return LB_OK;
+  if (!batch_in_sync(b)) {
+    int rc = batch_rebuild(b);
+    if (rc != LB_OK) return rc;
+  }
+  int64_t k = 0;
+  if (b->kpar == 1) {  // one plain step to reach kpar 0
+    LB_BCUDA(b, lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 1, b->smem, b->st));
+    b->kpar = 0;
+    k = 1;
+  }
+  if (nsteps - k >= 2) {
+    int rc = batch_graph(b);
+    if (rc != LB_OK) return rc;
+    for (; k + 2 <= nsteps; k += 2) LB_BCUDA(b, cudaGraphLaunch(b->graph, b->st));
+  }
+  if (k < nsteps) {
+    LB_BCUDA(b, lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 0, b->smem, b->st));
+    b->kpar = 1;
+    k++;
+  }
+  for (lb_handle *h : b->hs) {
+    h->cur ^= (int)(nsteps & 1);
+    h->step += nsteps;
+    h->cta_valid = true;
+  }
+  return LB_OK;
+}
+
+int lb_batch_autotune(lb_batch *b, int steps, int32_t *seg_h) {
+  if (!b) return LB_ERR_ARG;
+  if (steps < 1) return bfail(b, LB_ERR_ARG, "lb_batch_autotune: steps must be >= 1");
+  const int n = (int)b->hs.size();
+  for (lb_handle *h : b->hs)
+    if (!h->initialised) return bfail(b, LB_ERR_STATE, "lb_batch_autotune: an instance is not initialised");
+  const int cand[] = {24, 32, 40, 48, 56, 64, 80, 96, 128};
+  // Lattice classes by height: short, medium, tall.
+  auto cls = [](int ny) { return ny <= 96 ? 0 : (ny <= 160 ? 1 : 2); };
+  for (lb_handle *h : b->hs) {
+    int mx = h->sweep_nseg;
+    for (int c : cand) mx = std::max(mx, (h->p.ny + std::min(c, h->p.ny) - 1) / std::min(c, h->p.ny));
+    LB_BCUDA(b, ensure_records(h, mx));
+  }
+  // Save every state; each trial starts from it.
+  std::vector<void *> save(n, nullptr);
+  std::vector<int> cur0(n), seg0(n);
+  std::vector<int64_t> step0(n);
+  int rc = LB_OK;
+  cudaError_t e = cudaSuccess;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  for (int i = 0; i < n && e == cudaSuccess; i++) {
+    lb_handle *h = b->hs[i];
+    cur0[i] = h->cur;
+    seg0[i] = h->sweep_seg;
+    step0[i] = h->step;
+    const size_t bytes = lbk::sweep_buffer_bytes(h->store, h->plane);
+    e = cudaMalloc(&save[i], bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save[i], h->f[h->cur], bytes, cudaMemcpyDeviceToDevice, b->st);
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto restore = [&]() -> cudaError_t {
+    for (int i = 0; i < n; i++) {
+      lb_handle *h = b->hs[i];
+      h->cur = cur0[i];
+      h->step = step0[i];
+      cudaError_t r = cudaMemcpyAsync(h->f[h->cur], save[i], lbk::sweep_buffer_bytes(h->store, h->plane),
+                                      cudaMemcpyDeviceToDevice, b->st);
+      if (r != cudaSuccess) return r;
+    }
+    b->dirty = true;
+    return cudaSuccess;
+  };
+  auto trial = [&](float *ms) -> int {
+    b->dirty = true;
+    int r = lb_batch_step(b, 2);
+    if (r == LB_OK) e = cudaEventRecord(e0, b->st);
+    if (r == LB_OK && e == cudaSuccess) r = lb_batch_step(b, steps);
+    if (r == LB_OK && e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+    if (r == LB_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (r == LB_OK && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    if (r == LB_OK && e == cudaSuccess) e = restore();
+    return r;
+  };
+  // Pass 1: one segment height for all; pass 2: per class, others fixed.
+  int best_all = 64;
+  float best_ms = 3.0e38f;
+  for (int c : cand) {
+    if (e != cudaSuccess || rc != LB_OK) break;
+    for (lb_handle *h : b->hs) set_segments(h, c);
+    float ms = 0.f;
+    rc = trial(&ms);
+    if (rc == LB_OK && e == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best_all = c;
+    }
+  }
+  int best_cls[3] = {best_all, best_all, best_all};
+  for (int k = 0; k < 3; k++) {
+    bool any = false;
+    for (lb_handle *h : b->hs) any = any || cls(h->p.ny) == k;
+    if (!any) continue;
+    for (int c : cand) {
+      if (e != cudaSuccess || rc != LB_OK) break;
+      if (c == best_cls[k]) continue;
+      for (lb_handle *h : b->hs) set_segments(h, cls(h->p.ny) == k ? c : best_cls[cls(h->p.ny)]);
+      float ms = 0.f;
+      rc = trial(&ms);
+      if (rc == LB_OK && e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best_cls[k] = c;
+      }
+    }
+  }
+  for (int i = 0; i < n; i++) {
+    lb_handle *h = b->hs[i];
+    set_segments(h, (rc == LB_OK && e == cudaSuccess) ? best_cls[cls(h->p.ny)] : seg0[i]);
+    if (seg_h) seg_h[i] = h->sweep_seg;
+  }
+  if (e == cudaSuccess) e = restore();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  for (void *p : save) cudaFree(p);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->dirty = true;
+  if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("lb_batch_autotune: ") + cudaGetErrorString(e));
+  if (rc != LB_OK) return bfail(b, rc, "lb_batch_autotune: a trial step failed: " + b->err);
+  return LB_OK;
+}
+
+int lb_batch_destroy(lb_batch *b) {
+  if (!b) return LB_OK;
+  if (b->st || !b->hs.empty()) cudaStreamSynchronize(b->st);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (lb_handle *h : b->hs) lb_destroy(h);
+  cudaFree(b->d_items);
+  cudaFree(b->d_args);
+  cudaFree(b->d_maps);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return LB_OK;
+}
+
+const char *lb_batch_last_error(const lb_batch *b) {
+  if (!b) return g_create_err.c_str();
+  return b->err.c_str();
 }
 
 }  // extern "C"

@@ -54,6 +54,18 @@ cudaError_t sweep_make_maps(int store, void *base, int pitch, int ny, long long 
 size_t sweep_buffer_bytes(int store, long long plane);
 cudaError_t launch_sweep(int store, const CUtensorMap &m0, const CUtensorMap &m1, const SweepArgs &A,
                          size_t smem, cudaStream_t st);
+
+// One CTA of the batched sweep: instance `inst`, its strip and segment, the
+// index of its mass/momentum record in the instance's record array, and the
+// parity of the instance's input buffer at kpar = 0.
+struct BatchItem {
+  int inst, strip, seg, rec, par0;
+};
+// Batched step over a work list.  args: 2 per instance (input buffer 0, 1);
+// maps: 4 per instance ([input buffer][map], map 1 = deviation planes of
+// 16-bit storage or a copy of map 0), 64-byte aligned device memory.
+cudaError_t launch_sweep_batch(int store, const BatchItem *items, int nitems, const SweepArgs *args,
+                               const CUtensorMap *maps, int kpar, size_t smem, cudaStream_t st);
 // Copy the periodic images into the ghost band of `nplanes` planes of
 // `elem_bytes`-byte elements (4 or 2).
 cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,

@@ -257,17 +257,18 @@ __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, floa
 
 }  // namespace
 
+// One CTA's work: strip `strip`, segment `seg` of the lattice described by
+// A, whose input state the tensor maps tin (and tdev, the deviation planes
+// of 16-bit storage) describe; the CTA's mass/momentum record goes to rec.
 template <class St>
-__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
-sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tdev,
-                  const SweepArgs A) {
+__device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
+                                           const int strip, const int seg, double *rec) {
   using Row = typename St::Row;
   using Smem = SweepSmem<St::kSlotBytes>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem &S = *reinterpret_cast<Smem *>(smem_raw);
 
   const int t = threadIdx.x;
-  const int strip = blockIdx.x, seg = blockIdx.y;
   const int x0 = strip * A.base_w + St::kQuantum * min(strip, A.extra);
   const int W = A.base_w + (strip < A.extra ? St::kQuantum : 0);
   const int ya = seg * A.seg_h;
@@ -297,7 +298,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant
     for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int P = 0; P < min(kPairs, npairs); ++P)
-      tma_pair<St>(&tin, &tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
+      tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
   __syncthreads();
   mbar_wait(smem_u32(&S.full[0]), 0, A.err);
@@ -349,7 +350,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant
       // with pair k+2.
       if (t == 0 && k >= 3 && k + 2 < npairs) {
         const int slot = dec(s5m2, kPairs);
-        tma_pair<St>(&tin, &tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
+        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
       }
 
       // -------------------------------------- B: rows a-1, a -- P, lap n
@@ -549,11 +550,40 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant
       for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
     }
     if (t == 0) {
-      double *out = A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = v[q];
+      for (int q = 0; q < 4; ++q) rec[q] = v[q];
     }
   }
+}
+
+template <class St>
+__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tdev,
+                  const SweepArgs A) {
+  sweep_body<St>(&tin, &tdev, A, blockIdx.x, blockIdx.y,
+                 A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// Batched step: CTA b works on items[b] (instance, strip, segment) of a
+// work list over many independent lattices.  Arguments and tensor maps of
+// each instance sit in device memory for both buffer parities; an instance
+// reads buffer (item.par0 ^ kpar).
+template <class St>
+__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+sweep_batch_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restrict__ args,
+                   const CUtensorMap *__restrict__ maps, int kpar) {
+  __shared__ SweepArgs A;
+  const BatchItem it = items[blockIdx.x];
+  const int par = it.par0 ^ kpar;
+  const CUtensorMap *m = maps + 4 * it.inst + 2 * par;  // [instance][input buffer][map]
+  if (threadIdx.x == 0) {
+    A = args[2 * it.inst + par];
+    // the maps were written through the generic proxy (a host copy)
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m + 1) : "memory");
+  }
+  __syncthreads();
+  sweep_body<St>(m, m + 1, A, it.strip, it.seg, A.partials + 4 * (size_t)it.rec);
 }
 
 // Copy the periodic images into the ghost band of nplanes padded planes.
@@ -653,8 +683,18 @@ int maxw_of(int store) {
 template <class St>
 cudaError_t prepare_one(size_t *smem_bytes) {
   *smem_bytes = sizeof(SweepSmem<St::kSlotBytes>);
-  return cudaFuncSetAttribute(sweep_step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)*smem_bytes);
+  cudaError_t e = cudaFuncSetAttribute(sweep_step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)*smem_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_batch_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_bytes);
+  return e;
+}
+
+template <class St>
+cudaError_t launch_batch_one(const BatchItem *items, int nitems, const SweepArgs *args, const CUtensorMap *maps,
+                             int kpar, size_t smem, cudaStream_t st) {
+  sweep_batch_kernel<St><<<nitems, kThreads, smem, st>>>(items, args, maps, kpar);
+  return cudaGetLastError();
 }
 
 template <class St>
@@ -721,6 +761,17 @@ cudaError_t launch_sweep(int store, const CUtensorMap &m0, const CUtensorMap &m1
     case kStoreF32: return launch_one<StoreF32>(m0, m1, A, smem, st);
     case kStoreBF16: return launch_one<StoreBF16>(m0, m1, A, smem, st);
     case kStoreFP16: return launch_one<StoreFP16>(m0, m1, A, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_batch(int store, const BatchItem *items, int nitems, const SweepArgs *args,
+                               const CUtensorMap *maps, int kpar, size_t smem, cudaStream_t st) {
+  if (nitems < 1) return cudaSuccess;
+  switch (store) {
+    case kStoreF32: return launch_batch_one<StoreF32>(items, nitems, args, maps, kpar, smem, st);
+    case kStoreBF16: return launch_batch_one<StoreBF16>(items, nitems, args, maps, kpar, smem, st);
+    case kStoreFP16: return launch_batch_one<StoreFP16>(items, nitems, args, maps, kpar, smem, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -78,9 +78,18 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_last_error.restype = C.c_char_p
         lib.lb_reduce_noalloc.argtypes = [P, C.c_int, C.c_int32, C.c_int32, C.c_double, P, P, P]
         lib.lb_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+        lib.lb_batch_create.argtypes = [C.POINTER(lb_params), C.c_int32, C.POINTER(P)]
+        lib.lb_batch_handle.argtypes = [P, C.c_int32]
+        lib.lb_batch_handle.restype = P
+        lib.lb_batch_step.argtypes = [P, C.c_int64]
+        lib.lb_batch_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+        lib.lb_batch_destroy.argtypes = [P]
+        lib.lb_batch_last_error.argtypes = [P]
+        lib.lb_batch_last_error.restype = C.c_char_p
         for name in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_reduce",
                      "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy",
-                     "lb_reduce_noalloc", "lb_autotune"):
+                     "lb_reduce_noalloc", "lb_autotune", "lb_batch_create", "lb_batch_step",
+                     "lb_batch_autotune", "lb_batch_destroy"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
     return _lib
@@ -181,6 +190,46 @@ def lb_autotune(h, steps: int = 20) -> int:
     return seg.value
 
 
+def _bcheck(rc: int, b) -> int:
+    if rc != LB_OK:
+        s = load_library().lb_batch_last_error(b)
+        raise LBError(rc, s.decode() if s else "")
+    return rc
+
+
+def lb_batch_create(ps) -> int:
+    arr = (lb_params * len(ps))(*ps)
+    b = C.c_void_p()
+    _bcheck(load_library().lb_batch_create(arr, len(ps), C.byref(b)), None)
+    return b.value
+
+
+def lb_batch_handle(b, i: int) -> int:
+    h = load_library().lb_batch_handle(b, i)
+    if not h:
+        raise LBError(LB_ERR_ARG, f"lb_batch_handle: no instance {i}")
+    return h
+
+
+def lb_batch_step(b, nsteps: int) -> int:
+    return _bcheck(load_library().lb_batch_step(b, nsteps), b)
+
+
+def lb_batch_autotune(b, steps: int, count: int) -> list[int]:
+    seg = (C.c_int32 * count)()
+    _bcheck(load_library().lb_batch_autotune(b, steps, seg), b)
+    return list(seg)
+
+
+def lb_batch_destroy(b) -> int:
+    return load_library().lb_batch_destroy(b)
+
+
+def lb_batch_last_error(b) -> str:
+    s = load_library().lb_batch_last_error(b)
+    return s.decode() if s else ""
+
+
 def lb_last_error(h) -> str:
     s = load_library().lb_last_error(h)
     return s.decode() if s else ""
@@ -266,3 +315,66 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Owns one lb_batch: many independent lattices stepped together.
+    ``batch[i]`` is a :class:`Solver`-like view of instance i (same methods,
+    no ownership)."""
+
+    def __init__(self, params: list, stream: int | None = None):
+        ps = []
+        for p in params:
+            q = lb_params()
+            C.memmove(C.byref(q), C.byref(p), C.sizeof(lb_params))
+            q.stream = stream
+            ps.append(q)
+        self.params = ps
+        self.b = lb_batch_create(ps)
+        self.views = [_View(self, i) for i in range(len(ps))]
+
+    def __len__(self):
+        return len(self.views)
+
+    def __getitem__(self, i):
+        return self.views[i]
+
+    def step(self, nsteps: int = 1):
+        lb_batch_step(self.b, nsteps)
+        return self
+
+    def autotune(self, steps: int = 10) -> list[int]:
+        return lb_batch_autotune(self.b, steps, len(self.views))
+
+    def close(self):
+        if self.b:
+            lb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _View(Solver):
+    """Instance i of a Batch (the batch owns the handle)."""
+
+    def __init__(self, batch: Batch, i: int):  # noqa: super().__init__ is not called
+        p = batch.params[i]
+        self.nx, self.ny, self.precision = p.nx, p.ny, p.precision
+        self.params = p
+        self._batch, self._i = batch, i
+        self.dtype = np.float64 if p.precision == LB_FP64 else np.float32
+        self.dev16 = p.precision in (LB_BF16DEV, LB_FP16DEV)
+
+    @property
+    def h(self):
+        return lb_batch_handle(self._batch.b, self._i)
+
+    def close(self):
+        pass
+
+    def __del__(self):
+        pass

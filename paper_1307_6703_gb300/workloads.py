@@ -89,3 +89,30 @@ def slab_field(nx: int, ny: int, n_in: float, n_out: float, width: float = 3.0) 
     """Liquid slab in the middle half of the rows (two flat interfaces)."""
     y = np.arange(ny)[:, None] * np.ones((1, nx))
     return n_out + (n_in - n_out) * 0.5 * (np.tanh((y - ny / 4) / width) - np.tanh((y - 3 * ny / 4) / width))
+
+
+# Stencil parameters (N, Q) of Table 1 (OVC column) at the tabulated reduced
+# temperatures used here.
+_TABLE1_NQ = {0.85: (0.3, 2.3), 0.90: (0.3, 2.6), 0.95: (0.3, 2.0)}
+
+
+def batch_workloads(count: int = 64, seed: int = 7) -> list[Workload]:
+    """Seeded ensemble of independent sheared lattices for the batched
+    solver: nx uniform over multiples of 32 in [128, 1024], ny over multiples
+    of 16 in [64, 256]; wall speed U_w ~ U[0, 0.1] (walls at -U_w, +U_w);
+    A0 ~ U[1e-4, 1e-3] (the paper's range); lambda = nx/4 or nx/2 by a fair
+    coin; T_r ~ U[0.85, 0.95] with (N, Q) of the nearest Table 1 row; tau = 1.
+    About 5.9 M sites for 64 lattices."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx = 32 * int(rng.integers(4, 33))
+        ny = 16 * int(rng.integers(4, 17))
+        uw = float(rng.uniform(0.0, 0.1))
+        a0 = float(rng.uniform(1e-4, 1e-3))
+        lam = float(nx // 4 if rng.integers(0, 2) == 0 else nx // 2)
+        tr = float(rng.uniform(0.85, 0.95))
+        nq = _TABLE1_NQ[min(_TABLE1_NQ, key=lambda t: abs(t - tr))]
+        out.append(Workload(f"batch{i}_{nx}x{ny}", nx, ny, True, tr * TC, 1.0, a0, lam, -uw, uw,
+                            nq[0], nq[1], 1000, seed=seed * 1000 + i))
+    return out

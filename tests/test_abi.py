@@ -68,3 +68,19 @@ def test_product_path_does_not_touch_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text
                 assert "lb_oracle" not in text
+
+
+def test_batch_create_rejects_bad_parameters_without_gpu(lib):
+    """Batch argument validation happens before any CUDA call."""
+    from paper_1307_6703_gb300 import LB_ERR_ARG, LBError, lb_batch_create, lb_params
+    base = dict(nx=8, ny=8, walls=1, precision=1, a=0.375, b=1 / 3, T=0.3, kappa=0.1,
+                tau=1.0, A0=0.0, lambda_=0.0, u_bot=0.0, u_top=0.0, N=0.5, Q=1.0,
+                rho_ref=0.0, stream=None)
+    for bad in ([dict(), dict(precision=2)],          # mixed precision
+                [dict(), dict(nx=10)],                # not a sweep lattice
+                [dict(precision=0), dict(precision=0)],  # FP64 has no sweep kernel
+                [dict(precision=2, nx=12)]):
+        ps = [lb_params(**{**base, **b}) for b in bad]
+        with pytest.raises(LBError) as ei:
+            lb_batch_create(ps)
+        assert ei.value.code == LB_ERR_ARG

@@ -1,0 +1,118 @@
+"""Batched solver (lb_batch_*): many independent lattices in one launch per
+step.  Every instance must follow exactly the trajectory it follows alone
+(the same per-site arithmetic; only the CTA that computes a site changes),
+through plain launches, the two-step CUDA graph, odd step counts, instances
+stepped or restored individually in between, and the autotuner."""
+import numpy as np
+import pytest
+
+from gpu_util import dev16_solver, oracle_for, rel_err, solver_for
+
+pytestmark = pytest.mark.gpu
+
+from paper_1307_6703_gb300 import LB_BF16DEV, LB_FP32, Batch  # noqa: E402
+from paper_1307_6703_gb300.workloads import batch_workloads, noise_field  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def _ensemble(count, prec):
+    ws = batch_workloads(count, seed=11)
+    if prec != LB_FP32:  # 16-bit storage: nx a multiple of 8 (all multiples of 32 here)
+        pass
+    return ws
+
+
+def _make(ws, prec):
+    alone = [solver_for(w, prec) if prec == LB_FP32 else dev16_solver(w, prec, 1.0) for w in ws]
+    batch = Batch([s.params for s in alone])
+    for s, v, w in zip(alone, batch, ws):
+        n0 = noise_field(w)
+        s.init_fields(n0)
+        v.init_fields(n0)
+    return alone, batch
+
+
+def _same(a, b):
+    sa, sb = a.get_state(), b.get_state()
+    if isinstance(sa, tuple):
+        return np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+    return np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("prec", [LB_FP32, LB_BF16DEV], ids=["fp32", "bf16dev"])
+def test_batch_matches_instances_alone(prec):
+    ws = _ensemble(7, prec)
+    alone, batch = _make(ws, prec)
+    # plain step, graph pairs, odd counts
+    for k in (1, 4, 3, 2):
+        batch.step(k)
+        for s in alone:
+            s.step(k)
+    for s, v in zip(alone, batch):
+        assert v.t == s.t == 10
+        assert _same(s, v)
+        rs, rv = s.reduce(), v.reduce()
+        assert rs[0] == rv[0] == 0 and abs(rs[1][0] - rv[1][0]) <= 1e-7 * rs[1][0]
+    for s in alone:
+        s.close()
+    batch.close()
+
+
+def test_batch_instance_touched_in_between():
+    """An instance stepped alone, or restored from a checkpoint, between
+    batch steps: the batch picks up its new buffer parity."""
+    ws = _ensemble(4, LB_FP32)
+    alone, batch = _make(ws, LB_FP32)
+    batch.step(3)
+    batch[1].step(1)          # instance 1 alone
+    state = batch[2].get_state()
+    batch[2].set_state(state, step=3)  # restore instance 2 (same state)
+    batch.step(2)
+    steps = [5, 6, 5, 5]
+    for s, n in zip(alone, steps):
+        s.step(n)
+    for s, v in zip(alone, batch):
+        assert _same(s, v)
+    for s in alone:
+        s.close()
+    batch.close()
+
+
+def test_batch_instance_against_oracle():
+    """One instance of a stepped batch against the FP64 oracle."""
+    ws = _ensemble(3, LB_FP32)
+    ws = [w.with_(nx=min(w.nx, 256), ny=min(w.ny, 96)) for w in ws]
+    batch = Batch([solver_for(w, LB_FP32).params for w in ws])
+    n0s = [noise_field(w) for w in ws]
+    for v, n0 in zip(batch, n0s):
+        v.init_fields(n0)
+    batch.step(40)
+    for v, w, n0 in zip(batch, ws, n0s):
+        ref = oracle_for(w).init_fields(n0).step(40)
+        n, _, _ = v.moments()
+        assert rel_err(n, ref.moments()[0]) <= 1e-5
+    batch.close()
+
+
+def test_batch_autotune_keeps_trajectories():
+    ws = _ensemble(6, LB_FP32)
+    alone, batch = _make(ws, LB_FP32)
+    batch.step(5)
+    segs = batch.autotune(3)
+    assert len(segs) == 6 and all(1 <= s_ <= w.ny for s_, w in zip(segs, ws))
+    batch.step(7)
+    for s in alone:
+        s.step(12)
+    for s, v in zip(alone, batch):
+        assert v.t == 12 and _same(s, v)
+    for s in alone:
+        s.close()
+    batch.close()
