@@ -336,15 +336,17 @@ def run_batch(args):
         torch.cuda.synchronize()
     t_ms = ev0.elapsed_time(ev1)
     unstable = [i for i, v in enumerate(batch) if v.reduce()[0] != 0]
-    # the same lattices one by one (one lb_step launch per lattice and step)
+    # The same lattices one by one: each stepped k_seq times alone (its own
+    # lb_step launches), device times summed.
     k_seq = max(min(args.steps, 200), 1)
-    ev0.record(stream)
-    for _ in range(k_seq):
-        for v in batch:
-            lb_step(v.h, 1)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = ev0.elapsed_time(ev1)
+    seq_ms = 0.0
+    for v in batch:
+        v.autotune(5)  # each lattice with its own best tiling
+        ev0.record(stream)
+        lb_step(v.h, k_seq)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += ev0.elapsed_time(ev1)
     batch.close()
     value = sites * args.steps / (t_ms * 1e-3) / 1e6
     seq = sites * k_seq / (seq_ms * 1e-3) / 1e6

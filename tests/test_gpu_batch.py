@@ -127,3 +127,23 @@ def test_batch_autotune_keeps_trajectories():
     for s in alone:
         s.close()
     batch.close()
+
+
+def test_batch_ensemble_is_stable():
+    """The 64-lattice ensemble of the batch benchmark stays physical for
+    3000 steps (every instance's lb_reduce returns LB_OK)."""
+    from paper_1307_6703_gb300.workloads import batch_workloads
+    ws = batch_workloads(64, seed=7)
+    batch = Batch([solver_params(w) for w in ws])
+    for v, w in zip(batch, ws):
+        v.init_fields(noise_field(w))
+    batch.step(3000)
+    bad = [i for i, v in enumerate(batch) if v.reduce()[0] != 0]
+    batch.close()
+    assert bad == []
+
+
+def solver_params(w):
+    from paper_1307_6703_gb300 import lb_params
+    return lb_params(w.nx, w.ny, int(w.walls), LB_FP32, w.a, w.b, w.T, w.kappa, w.tau, w.A0, w.lam,
+                     w.u_bot, w.u_top, w.N, w.Q, 0.0, None)
