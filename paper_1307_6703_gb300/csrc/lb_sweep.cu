@@ -50,6 +50,7 @@
 // it stored, and a flag for non-finite or out-of-range sites, so that the
 // global reduction of the new state costs one tiny kernel.
 #include <cstddef>
+#include <type_traits>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -310,7 +311,12 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   int s5 = 0, s3 = 0;
   uint32_t par = 0;  // phase parity of pair k+1
 
-  for (int k = 0; k <= kmax; ++k) {
+  // One iteration; kSteady instantiates it for iterations whose rows are all
+  // interior rows of the segment (no wall rows or their mirrors, no warm-up
+  // rows, no periodic ghost images in y), where every per-row condition
+  // below is known to hold and the two rows of a stage are independent.
+  auto iteration = [&](const int k, auto steady_tag) {
+    constexpr bool kSteady = decltype(steady_tag)::value;
     const int s5m1 = dec(s5, kPairs), s5m2 = dec(s5m1, kPairs), s5p1 = inc(s5, kPairs);
     const int s3m1 = (s3 + 3) & 3, s3m2 = (s3 + 2) & 3;  // density ring: 4 pairs
     const int s2 = k & 1, s2m1 = s2 ^ 1;
@@ -327,14 +333,14 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       for (int j = 0; j < 2; ++j) {
         const int y = a + j;
         const Row r0 = j ? q1 : q0, r1 = j ? q2 : q1, r2 = j ? q3 : q2;
-        if (actA && (!walls || (y >= 0 && y <= ny - 1))) {
+        if (actA && (kSteady || !walls || (y >= 0 && y <= ny - 1))) {
           float f[9];
           pull<St>(r0, r1, r2, t, f, A);
           float n;
-          if (walls && y == 0) {
+          if (!kSteady && walls && y == 0) {
             n = St::get(r1, 0, t, A) + St::get(r1, 4, t, A) + St::get(r1, 7, t, A) + St::get(r1, 8, t, A) + f[1] +
                 f[3] + f[4] + f[7] + f[8];
-          } else if (walls && y == ny - 1) {
+          } else if (!kSteady && walls && y == ny - 1) {
             n = St::get(r1, 0, t, A) + St::get(r1, 2, t, A) + St::get(r1, 6, t, A) + St::get(r1, 5, t, A) + f[1] +
                 f[3] + f[2] + f[6] + f[5];
           } else {
@@ -361,9 +367,9 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
         for (int j = 0; j < 2; ++j) {
           const int y = a - 1 + j;
           const float *r0 = j ? n1 : n0, *r1 = j ? n2 : n1, *r2 = j ? n3 : n2;
-          if (actB && y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1))) {
-            if (walls && y == 0) r0 = r2;
-            if (walls && y == ny - 1) r2 = r0;
+          if (actB && (kSteady || (y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1))))) {
+            if (!kSteady && walls && y == 0) r0 = r2;
+            if (!kSteady && walls && y == ny - 1) r2 = r0;
             const float c = r1[t];
             const float nT = c * A.T;
             const float pw = nT * __fdividef(1.0f, 1.0f - A.b * c) - A.a * c * c;
@@ -382,17 +388,17 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 2 + j;
-          if (!(actC && y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1)))) continue;
+          if (!(actC && (kSteady || (y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1)))))) continue;
           const float *p0 = j ? P1 : P0, *p1 = j ? P2 : P1, *p2 = j ? P3 : P2;
           const float *l0 = j ? L1 : L0, *l1 = j ? L2 : L1, *l2 = j ? L3 : L2;
-          if (walls && y == 0) { p0 = p2; l0 = l2; }
-          if (walls && y == ny - 1) { p2 = p0; l2 = l0; }
+          if (!kSteady && walls && y == 0) { p0 = p2; l0 = l2; }
+          if (!kSteady && walls && y == ny - 1) { p2 = p0; l2 = l0; }
           const float n = S.n[s3m1][j][t];
           const float kn = A.kappa * n;
           const float Fx = (sdx(st, p0, p1, p2, t) + kn * sdx(st, l0, l1, l2, t)) + A.A0 * sinx;
           const float Fy = sdy(st, p0, p2, t) + kn * sdy(st, l0, l2, t);
           float sx = sxa[j], sy = sya[j];
-          if (walls && (y == 0 || y == ny - 1)) {
+          if (!kSteady && walls && (y == 0 || y == ny - 1)) {
             // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
             const Row w0 = St::row(S.pops[s5m1], 0), w1 = St::row(S.pops[s5m1], 1);
             const Row w2 = St::row(S.pops[s5], 0), w3 = St::row(S.pops[s5], 1);
@@ -424,12 +430,12 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 3 + j;
-          if (!(actD && y >= ya && y < yb)) continue;
+          if (!(actD && (kSteady || (y >= ya && y < yb)))) continue;
           const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
           const float *x0p = j ? X1 : X0, *x1p = j ? X2 : X1, *x2p = j ? X3 : X2;
           const float *y0p = j ? Y1 : Y0, *y1p = j ? Y2 : Y1, *y2p = j ? Y3 : Y2;
           const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
-          const bool bot = walls && y == 0, top = walls && y == ny - 1;
+          const bool bot = !kSteady && walls && y == 0, top = !kSteady && walls && y == ny - 1;
           float dJy;
           if (bot || top) {
             // mirror rows across the wall: n and J_x even, J_y odd
@@ -449,7 +455,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f, A);
           if (bot || top) wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
           collide(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs);
-          const int gy = walls ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
+          const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
             // Collision conserves the site's mass exactly (A = 0, sum f^eq =
@@ -522,6 +528,16 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
     }
     s5 = s5p1;
     s3 = (s3 + 1) & 3;
+  };
+  for (int k = 0; k <= kmax; ++k) {
+    const int a = ya - 3 + 2 * k;
+    // every row of the four stages is interior (see the lambda's note)
+    const bool steady = k >= 3 && a - 2 < yb &&
+                        (walls ? (a - 3 >= 1 && a + 1 <= ny - 2) : (a - 3 >= 4 && a + 1 < ny - 4));
+    if (steady)
+      iteration(k, std::true_type{});
+    else
+      iteration(k, std::false_type{});
   }
 
   // CTA partial sums of the stored state (FP64, fixed order).  Every TMA
