@@ -25,6 +25,7 @@ UNITS = {
     "lb_f64.cu": ["--fmad=false"],
     "lb_noalloc.cu": [],
     "lb_sweep.cu": [],
+    "fno.cu": [],
 }
 
 
@@ -36,6 +37,7 @@ def _nvcc() -> str:
 def _sources_mtime() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     paths.append(os.path.join(ROOT, "include", "lb.h"))
+    paths.append(os.path.join(ROOT, "include", "fno.h"))
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 
@@ -62,7 +64,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")

@@ -1,0 +1,760 @@
+// fno.cu -- the learned warm start (include/fno.h): forward and backward
+// passes of a small Fourier neural operator, its loss and its Adam update,
+// as CUDA kernels of this library.  The truncated Fourier transforms along x
+// and the per-site channel mixing are plain GEMMs and go to cuBLAS (BF16
+// inputs, FP32 accumulation, tensor cores); the transforms along y, the
+// per-mode complex channel mixing, the lift, the projection, the
+// activations, the loss, every reduction of the backward pass and the
+// optimizer are the kernels below.
+//
+// Activation layout: [batch][channel][ny][nx] (x fastest).  A "row" of the
+// x-transform is one (batch, channel, y) line, so the x-transform of all
+// channels of all fields is a single GEMM [B*C*ny, nx] x [nx, 2*mx].
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "fno.h"
+
+namespace {
+
+constexpr int kMaxLayers = 8;
+constexpr int kFeatures = 5;
+constexpr int kThreads = 256;
+
+struct Offsets {
+  size_t P, p, W[kMaxLayers], w[kMaxLayers], Rr[kMaxLayers], Ri[kMaxLayers], Q1, q1, Q2, q2, total;
+};
+
+Offsets make_offsets(const fno_config &c) {
+  Offsets o{};
+  size_t at = 0;
+  const size_t C = c.width, H = c.hidden, M = (size_t)c.modes_x * c.modes_y;
+  o.P = at; at += C * kFeatures;
+  o.p = at; at += C;
+  for (int l = 0; l < c.layers; l++) {
+    o.W[l] = at; at += C * C;
+    o.w[l] = at; at += C;
+    o.Rr[l] = at; at += M * C * C;
+    o.Ri[l] = at; at += M * C * C;
+  }
+  o.Q1 = at; at += H * C;
+  o.q1 = at; at += H;
+  o.Q2 = at; at += H;
+  o.q2 = at; at += 1;
+  o.total = at;
+  return o;
+}
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ float gelu(float z) { return z * normcdff(z); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return normcdff(z) + z * (0.3989422804014327f * expf(-0.5f * z * z));
+}
+
+// Kept y-mode number of mode index k (0..my-1): 0..my/2-1, then -my/2..-1.
+__device__ __forceinline__ int ymode(int k, int my) { return k < my / 2 ? k : k - my; }
+
+// Deterministic block sum of one double per thread (blockDim = kThreads).
+__device__ double block_sum(double v, double *sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+unsigned blocks_for(long long n) { return (unsigned)std::min<long long>((n + kThreads - 1) / kThreads, 8192); }
+
+// ------------------------------------------------------------------ kernels
+
+// Input features of each field from its parameters (U_w, A0, lambda, T_r).
+__global__ void features_kernel(const float *__restrict__ prm, int B, int nx, int ny, float *__restrict__ x0) {
+  const long long S = (long long)nx * ny, total = (long long)B * S;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / S);
+    const long long s = i - (long long)b * S;
+    const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+    const float uw = prm[4 * b], a0 = prm[4 * b + 1], lam = prm[4 * b + 2], tr = prm[4 * b + 3];
+    float sn, cs;
+    sincospif(2.0f * (float)x / lam, &sn, &cs);
+    const float yy = 2.0f * (float)y / (float)(ny - 1) - 1.0f;
+    float *o = x0 + (long long)b * kFeatures * S + s;
+    o[0] = (a0 / 1e-3f) * sn;
+    o[S] = (a0 / 1e-3f) * cs;
+    o[2 * S] = (uw / 0.05f) * yy;
+    o[3 * S] = (tr - 0.94f) / 0.02f;
+    o[4 * S] = yy;
+  }
+}
+
+// v0[b, o, s] = sum_c P[o, c] x0[b, c, s] + p[o]
+__global__ void lift_kernel(const float *__restrict__ x0, const float *__restrict__ P, const float *__restrict__ pb,
+                            int B, int C, long long S, float *__restrict__ v, __nv_bfloat16 *__restrict__ vb) {
+  const long long total = (long long)B * C * S;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i % S;
+    const int o = (int)((i / S) % C), b = (int)(i / (S * C));
+    const float *xb = x0 + (long long)b * kFeatures * S + s;
+    float acc = pb[o];
+#pragma unroll
+    for (int c = 0; c < kFeatures; c++) acc += P[o * kFeatures + c] * xb[c * S];
+    v[i] = acc;
+    vb[i] = __float2bfloat16_rn(acc);
+  }
+}
+
+// y-transform of the x-transformed lines: A[bc][y][j] (j < mx real part,
+// j >= mx imaginary part of mode j - mx) -> Sh[bc][ky][kx][2].
+__global__ void ydft_kernel(const float *__restrict__ A, int ny, int mx, int my, float *__restrict__ Sh) {
+  const int bc = blockIdx.x;
+  const float *a = A + (long long)bc * ny * 2 * mx;
+  for (int t = threadIdx.x; t < my * mx; t += blockDim.x) {
+    const int k = t / mx, kx = t - k * mx;
+    const int ky = ymode(k, my);
+    float sr = 0.f, si = 0.f;
+    for (int y = 0; y < ny; y++) {
+      float sn, cs;
+      sincospif(2.0f * (float)(ky * y) / (float)ny, &sn, &cs);
+      const float ar = a[y * 2 * mx + kx], ai = a[y * 2 * mx + mx + kx];
+      sr += ar * cs + ai * sn;
+      si += ai * cs - ar * sn;
+    }
+    float *o = Sh + (((long long)bc * my + k) * mx + kx) * 2;
+    o[0] = sr;
+    o[1] = si;
+  }
+}
+
+// Per-mode complex channel mixing, then the inverse y-transform:
+// Y[o, ky] = sum_c S[c, ky] R[ky, kx, c, o];  G[o][y][kx] = sum_ky Y e^{+i theta}.
+// One block per (kx, b); shared memory: Y[C][my][2].
+__global__ void mix_iy_kernel(const float *__restrict__ Sh, const float *__restrict__ Rr, const float *__restrict__ Ri,
+                              int C, int ny, int mx, int my, float *__restrict__ G, __nv_bfloat16 *__restrict__ Gb) {
+  extern __shared__ float ysm[];
+  const int kx = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
+    const int o = t / my, k = t - o * my;
+    float yr = 0.f, yi = 0.f;
+    const long long rbase = ((long long)(k * mx + kx) * C) * C + o;
+    for (int c = 0; c < C; c++) {
+      const float *s = Sh + ((((long long)b * C + c) * my + k) * mx + kx) * 2;
+      const float rr = Rr[rbase + (long long)c * C], ri = Ri[rbase + (long long)c * C];
+      yr += s[0] * rr - s[1] * ri;
+      yi += s[0] * ri + s[1] * rr;
+    }
+    ysm[(o * my + k) * 2] = yr;
+    ysm[(o * my + k) * 2 + 1] = yi;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < C * ny; t += blockDim.x) {
+    const int o = t / ny, y = t - o * ny;
+    float gr = 0.f, gi = 0.f;
+    for (int k = 0; k < my; k++) {
+      float sn, cs;
+      sincospif(2.0f * (float)(ymode(k, my) * y) / (float)ny, &sn, &cs);
+      const float yr = ysm[(o * my + k) * 2], yi = ysm[(o * my + k) * 2 + 1];
+      gr += yr * cs - yi * sn;
+      gi += yr * sn + yi * cs;
+    }
+    const long long g = (((long long)b * C + o) * ny + y) * 2 * mx;
+    G[g + kx] = gr;
+    G[g + mx + kx] = gi;
+    Gb[g + kx] = __float2bfloat16_rn(gr);
+    Gb[g + mx + kx] = __float2bfloat16_rn(gi);
+  }
+}
+
+// z += w (per channel); v' = gelu(z) (or z for the last layer).
+__global__ void bias_act_kernel(float *__restrict__ z, const float *__restrict__ w, int C, long long S, long long total,
+                                int act, float *__restrict__ v, __nv_bfloat16 *__restrict__ vb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)((i / S) % C);
+    const float zz = z[i] + w[o];
+    z[i] = zz;
+    const float vv = act ? gelu(zz) : zz;
+    v[i] = vv;
+    vb[i] = __float2bfloat16_rn(vv);
+  }
+}
+
+// hp += q1 (kept); out[b, s] = sum_h Q2[h] gelu(hp[b, h, s]) + q2.
+__global__ void project_kernel(float *__restrict__ hp, const float *__restrict__ q1, const float *__restrict__ Q2,
+                               const float *__restrict__ q2, int B, int H, long long S, float *__restrict__ out,
+                               float *__restrict__ out_user) {
+  const long long total = (long long)B * S;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / S);
+    const long long s = i - (long long)b * S;
+    float *h = hp + (long long)b * H * S + s;
+    float acc = q2[0];
+    for (int k = 0; k < H; k++) {
+      const float z = h[k * S] + q1[k];
+      h[k * S] = z;
+      acc += Q2[k] * gelu(z);
+    }
+    out[i] = acc;
+    if (out_user) out_user[i] = acc;
+  }
+}
+
+// Loss partial sums and d loss / d out = 2 (out - target) / (B S).
+__global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ tgt, long long total,
+                            float *__restrict__ dout, double *__restrict__ partial) {
+  __shared__ double sm[kThreads];
+  double acc = 0.0;
+  const float scale = 2.0f / (float)total;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const float d = out[i] - tgt[i];
+    dout[i] = scale * d;
+    acc += (double)d * (double)d;
+  }
+  const double r = block_sum(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+__global__ void finish_loss_kernel(const double *__restrict__ partial, int n, long long total, double *__restrict__ loss) {
+  __shared__ double sm[kThreads];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+  const double r = block_sum(acc, sm);
+  if (threadIdx.x == 0) *loss = r / (double)total;
+}
+
+// dhp[b, h, s] = Q2[h] dout[b, s] gelu'(hp[b, h, s])
+__global__ void project_back_kernel(const float *__restrict__ hp, const float *__restrict__ Q2,
+                                    const float *__restrict__ dout, int H, long long S, long long total,
+                                    float *__restrict__ dhp, __nv_bfloat16 *__restrict__ dhpb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i % S;
+    const int k = (int)((i / S) % H), b = (int)(i / (S * H));
+    const float d = Q2[k] * dout[(long long)b * S + s] * gelu_grad(hp[i]);
+    dhp[i] = d;
+    dhpb[i] = __float2bfloat16_rn(d);
+  }
+}
+
+// Per-channel sums over (b, s): out[ch] = sum a[b, ch, s] (* f(other)),
+// one block per channel.  mode 0: plain sum; 1: a * gelu(other[b, ch, s]);
+// 2: a[b, ch, s] * other[b, ch2, s] for the lift weights (ch = o * 5 + c2).
+__global__ void chan_sum_kernel(const float *__restrict__ a, const float *__restrict__ other, int mode, int B, int C,
+                                int C2, long long S, float *__restrict__ out) {
+  __shared__ double sm[kThreads];
+  const int ch = blockIdx.x;
+  const int o = mode == 2 ? ch / C2 : ch, c2 = mode == 2 ? ch % C2 : 0;
+  double acc = 0.0;
+  const long long n = (long long)B * S;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const int b = (int)(i / S);
+    const long long s = i - (long long)b * S;
+    const float av = a[((long long)b * C + o) * S + s];
+    float v = av;
+    if (mode == 1) v = av * gelu(other[((long long)b * C + o) * S + s]);
+    if (mode == 2) v = av * other[((long long)b * C2 + c2) * S + s];
+    acc += (double)v;
+  }
+  const double r = block_sum(acc, sm);
+  if (threadIdx.x == 0) out[ch] = (float)r;
+}
+
+// dQ2[k] = sum_{b, s} dout[b, s] gelu(hp[b, k, s]); one block per k.
+__global__ void dQ2_kernel(const float *__restrict__ dout, const float *__restrict__ hp, int B, int H, long long S,
+                           float *__restrict__ out) {
+  __shared__ double sm[kThreads];
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  const long long n = (long long)B * S;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const int b = (int)(i / S);
+    const long long s = i - (long long)b * S;
+    acc += (double)(dout[i] * gelu(hp[((long long)b * H + k) * S + s]));
+  }
+  const double r = block_sum(acc, sm);
+  if (threadIdx.x == 0) out[k] = (float)r;
+}
+
+// dz = dv * gelu'(z) (or dv for the last layer), with a BF16 copy.
+__global__ void act_back_kernel(const float *__restrict__ dv, const float *__restrict__ z, long long total, int act,
+                                float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const float d = act ? dv[i] * gelu_grad(z[i]) : dv[i];
+    dz[i] = d;
+    dzb[i] = __float2bfloat16_rn(d);
+  }
+}
+
+// Adjoint of the inverse y-transform, then of the mode mixing (for the
+// inputs): dY[o, ky] = sum_y dG e^{-i theta} (adjoint form), dS[c, ky] =
+// sum_o (R^H-like products).  One block per (kx, b); dY kept for dR.
+__global__ void mix_iy_back_kernel(const float *__restrict__ dG, const float *__restrict__ Rr, const float *__restrict__ Ri,
+                                   int C, int ny, int mx, int my, float *__restrict__ dY, float *__restrict__ dS) {
+  extern __shared__ float ysm[];
+  const int kx = blockIdx.x, b = blockIdx.y;
+  for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
+    const int o = t / my, k = t - o * my;
+    const int ky = ymode(k, my);
+    const float *g = dG + (((long long)b * C + o) * ny) * 2 * mx;
+    float yr = 0.f, yi = 0.f;
+    for (int y = 0; y < ny; y++) {
+      float sn, cs;
+      sincospif(2.0f * (float)(ky * y) / (float)ny, &sn, &cs);
+      const float gr = g[y * 2 * mx + kx], gi = g[y * 2 * mx + mx + kx];
+      yr += gr * cs + gi * sn;
+      yi += -gr * sn + gi * cs;
+    }
+    ysm[(o * my + k) * 2] = yr;
+    ysm[(o * my + k) * 2 + 1] = yi;
+    float *d = dY + ((((long long)b * C + o) * my + k) * mx + kx) * 2;
+    d[0] = yr;
+    d[1] = yi;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
+    const int c = t / my, k = t - c * my;
+    const long long rbase = ((long long)(k * mx + kx) * C + c) * C;
+    float sr = 0.f, si = 0.f;
+    for (int o = 0; o < C; o++) {
+      const float yr = ysm[(o * my + k) * 2], yi = ysm[(o * my + k) * 2 + 1];
+      const float rr = Rr[rbase + o], ri = Ri[rbase + o];
+      sr += yr * rr + yi * ri;
+      si += -yr * ri + yi * rr;
+    }
+    float *d = dS + ((((long long)b * C + c) * my + k) * mx + kx) * 2;
+    d[0] = sr;
+    d[1] = si;
+  }
+}
+
+// dR[m, c, o] = sum_b (S_r dY_r + S_i dY_i, -S_i dY_r + S_r dY_i): one block per mode.
+__global__ void dR_kernel(const float *__restrict__ Sh, const float *__restrict__ dY, int B, int C, int mx, int my,
+                          float *__restrict__ dRr, float *__restrict__ dRi) {
+  const int m = blockIdx.x;
+  const int k = m / mx, kx = m - k * mx;
+  for (int t = threadIdx.x; t < C * C; t += blockDim.x) {
+    const int c = t / C, o = t - c * C;
+    float ar = 0.f, ai = 0.f;
+    for (int b = 0; b < B; b++) {
+      const float *s = Sh + ((((long long)b * C + c) * my + k) * mx + kx) * 2;
+      const float *d = dY + ((((long long)b * C + o) * my + k) * mx + kx) * 2;
+      ar += s[0] * d[0] + s[1] * d[1];
+      ai += -s[1] * d[0] + s[0] * d[1];
+    }
+    dRr[((long long)m * C + c) * C + o] = ar;
+    dRi[((long long)m * C + c) * C + o] = ai;
+  }
+}
+
+// Adjoint of the y-transform: dA[bc][y][kx] (re / im parts) from dS.
+__global__ void ydft_back_kernel(const float *__restrict__ dS, int ny, int mx, int my, float *__restrict__ dA,
+                                 __nv_bfloat16 *__restrict__ dAb) {
+  const int bc = blockIdx.x;
+  const float *d = dS + (long long)bc * my * mx * 2;
+  for (int t = threadIdx.x; t < ny * mx; t += blockDim.x) {
+    const int y = t / mx, kx = t - y * mx;
+    float ar = 0.f, ai = 0.f;
+    for (int k = 0; k < my; k++) {
+      float sn, cs;
+      sincospif(2.0f * (float)(ymode(k, my) * y) / (float)ny, &sn, &cs);
+      const float sr = d[(k * mx + kx) * 2], si = d[(k * mx + kx) * 2 + 1];
+      ar += sr * cs - si * sn;
+      ai += sr * sn + si * cs;
+    }
+    const long long a = ((long long)bc * ny + y) * 2 * mx;
+    dA[a + kx] = ar;
+    dA[a + mx + kx] = ai;
+    dAb[a + kx] = __float2bfloat16_rn(ar);
+    dAb[a + mx + kx] = __float2bfloat16_rn(ai);
+  }
+}
+
+// Truncated DFT matrices for nx: Fx[x][j] (forward, e^{-i phi}) and
+// Fxi[j][x] (real inverse with c_kx and 1/(nx ny)).
+__global__ void dft_tables_kernel(int nx, int ny, int mx, float *Fx, float *Fxi, __nv_bfloat16 *Fxb,
+                                  __nv_bfloat16 *Fxib) {
+  const int n = nx * mx;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int x = i / mx, k = i - x * mx;
+    float sn, cs;
+    sincospif(2.0f * (float)((long long)k * x % nx) / (float)nx, &sn, &cs);
+    Fx[x * 2 * mx + k] = cs;
+    Fx[x * 2 * mx + mx + k] = -sn;
+    const float sc = (k == 0 ? 1.0f : 2.0f) / ((float)nx * (float)ny);
+    Fxi[k * nx + x] = sc * cs;
+    Fxi[(mx + k) * nx + x] = -sc * sn;
+    Fxb[x * 2 * mx + k] = __float2bfloat16_rn(cs);
+    Fxb[x * 2 * mx + mx + k] = __float2bfloat16_rn(-sn);
+    Fxib[k * nx + x] = __float2bfloat16_rn(sc * cs);
+    Fxib[(mx + k) * nx + x] = __float2bfloat16_rn(-sc * sn);
+  }
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, __nv_bfloat16 *__restrict__ pb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ a, long long n, __nv_bfloat16 *__restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+
+struct fno_handle {
+  fno_config c{};
+  cudaStream_t st = nullptr;
+  cublasHandle_t blas = nullptr;
+  Offsets o{};
+  float *prm = nullptr, *grd = nullptr, *m1 = nullptr, *m2 = nullptr;
+  __nv_bfloat16 *prmb = nullptr;
+  long long cap_bcs = 0, cap_bs = 0, cap_bhs = 0, cap_line = 0, cap_modes = 0;  // workspace sizes (elements)
+  float *x0 = nullptr, *V[kMaxLayers + 1] = {}, *Z[kMaxLayers] = {}, *Sh[kMaxLayers] = {};
+  __nv_bfloat16 *Vb[kMaxLayers + 1] = {};
+  float *A = nullptr, *G = nullptr, *hp = nullptr, *out = nullptr;
+  __nv_bfloat16 *Gb = nullptr;
+  float *dout = nullptr, *dhp = nullptr, *dV = nullptr, *dZ = nullptr, *dG = nullptr, *dA = nullptr, *dY = nullptr,
+        *dS = nullptr;
+  __nv_bfloat16 *dhpb = nullptr, *dZb = nullptr, *dAb = nullptr;
+  double *partial = nullptr, *loss = nullptr;
+  float *Fx = nullptr, *Fxi = nullptr;
+  __nv_bfloat16 *Fxb = nullptr, *Fxib = nullptr;
+  int tab_nx = 0, tab_ny = 0;
+  int B = 0, nx = 0, ny = 0;  // shape of the last forward pass
+  bool have_forward = false;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int ffail(fno_handle *h, int code, const std::string &m) {
+  if (h) h->err = m;
+  else g_err = m;
+  return code;
+}
+
+#define FNO_CUDA(h, call)                                                                                      \
+  do {                                                                                                         \
+    cudaError_t e_ = (call);                                                                                   \
+    if (e_ != cudaSuccess)                                                                                     \
+      return ffail(h, e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,                              \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                                        \
+  } while (0)
+
+#define FNO_BLAS(h, call)                                                                                      \
+  do {                                                                                                         \
+    cublasStatus_t s_ = (call);                                                                                \
+    if (s_ != CUBLAS_STATUS_SUCCESS) return ffail(h, LB_ERR_CUDA, std::string(#call) + ": cuBLAS status " + std::to_string((int)s_)); \
+  } while (0)
+
+// Row-major C[m x n] = op(A)[m x k] op(B)[k x n] + beta C, strided batches.
+// A16 / B16: BF16 copies used when the handle's GEMMs run in BF16.
+cublasStatus_t gemm(fno_handle *h, bool tA, bool tB, int m, int n, int k, const float *A32,
+                    const __nv_bfloat16 *A16, int lda, long long sA, const float *B32, const __nv_bfloat16 *B16, int ldb,
+                    long long sB, float *C, int ldc, long long sC, int batch, float beta) {
+  const bool bf = h->c.gemm_bf16 != 0;
+  const void *A = bf ? (const void *)A16 : (const void *)A32;
+  const void *Bm = bf ? (const void *)B16 : (const void *)B32;
+  const cudaDataType_t t = bf ? CUDA_R_16BF : CUDA_R_32F;
+  const float alpha = 1.0f;
+  return cublasGemmStridedBatchedEx(h->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N, tA ? CUBLAS_OP_T : CUBLAS_OP_N, n, m, k,
+                                    &alpha, Bm, t, ldb, sB, A, t, lda, sA, &beta, C, CUDA_R_32F, ldc, sC, batch,
+                                    CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+}
+
+template <typename T>
+cudaError_t alloc(T **p, long long n) {
+  return cudaMalloc((void **)p, (size_t)std::max<long long>(n, 1) * sizeof(T));
+}
+
+void free_workspace(fno_handle *h) {
+  void *ps[] = {h->x0, h->A, h->G, h->Gb, h->hp, h->out, h->dout, h->dhp, h->dhpb, h->dV, h->dZ, h->dZb, h->dG,
+                h->dA, h->dAb, h->dY, h->dS, h->partial, h->loss, h->Fx, h->Fxi, h->Fxb, h->Fxib};
+  for (void *p : ps) cudaFree(p);
+  for (int l = 0; l <= kMaxLayers; l++) {
+    cudaFree(h->V[l]);
+    cudaFree(h->Vb[l]);
+    h->V[l] = nullptr;
+    h->Vb[l] = nullptr;
+  }
+  for (int l = 0; l < kMaxLayers; l++) {
+    cudaFree(h->Z[l]);
+    cudaFree(h->Sh[l]);
+    h->Z[l] = nullptr;
+    h->Sh[l] = nullptr;
+  }
+}
+
+cudaError_t alloc_workspace(fno_handle *h) {
+  const fno_config &c = h->c;
+  const long long S = (long long)c.nx_max * c.ny_max, B = c.batch_max;
+  h->cap_bcs = B * c.width * S;
+  h->cap_bs = B * S;
+  h->cap_bhs = B * c.hidden * S;
+  h->cap_line = B * c.width * (long long)c.ny_max * 2 * c.modes_x;
+  h->cap_modes = B * c.width * (long long)c.modes_x * c.modes_y * 2;
+  cudaError_t e = alloc(&h->x0, B * kFeatures * S);
+  for (int l = 0; l <= c.layers && e == cudaSuccess; l++) {
+    e = alloc(&h->V[l], h->cap_bcs);
+    if (e == cudaSuccess) e = alloc(&h->Vb[l], h->cap_bcs);
+  }
+  for (int l = 0; l < c.layers && e == cudaSuccess; l++) {
+    e = alloc(&h->Z[l], h->cap_bcs);
+    if (e == cudaSuccess) e = alloc(&h->Sh[l], h->cap_modes);
+  }
+  if (e == cudaSuccess) e = alloc(&h->A, h->cap_line);
+  if (e == cudaSuccess) e = alloc(&h->G, h->cap_line);
+  if (e == cudaSuccess) e = alloc(&h->Gb, h->cap_line);
+  if (e == cudaSuccess) e = alloc(&h->hp, h->cap_bhs);
+  if (e == cudaSuccess) e = alloc(&h->out, h->cap_bs);
+  if (e == cudaSuccess) e = alloc(&h->dout, h->cap_bs);
+  if (e == cudaSuccess) e = alloc(&h->dhp, h->cap_bhs);
+  if (e == cudaSuccess) e = alloc(&h->dhpb, h->cap_bhs);
+  if (e == cudaSuccess) e = alloc(&h->dV, h->cap_bcs);
+  if (e == cudaSuccess) e = alloc(&h->dZ, h->cap_bcs);
+  if (e == cudaSuccess) e = alloc(&h->dZb, h->cap_bcs);
+  if (e == cudaSuccess) e = alloc(&h->dG, h->cap_line);
+  if (e == cudaSuccess) e = alloc(&h->dA, h->cap_line);
+  if (e == cudaSuccess) e = alloc(&h->dAb, h->cap_line);
+  if (e == cudaSuccess) e = alloc(&h->dY, h->cap_modes);
+  if (e == cudaSuccess) e = alloc(&h->dS, h->cap_modes);
+  if (e == cudaSuccess) e = alloc(&h->partial, 8192);
+  if (e == cudaSuccess) e = alloc(&h->loss, 1);
+  if (e == cudaSuccess) e = alloc(&h->Fx, (long long)c.nx_max * 2 * c.modes_x);
+  if (e == cudaSuccess) e = alloc(&h->Fxi, (long long)c.nx_max * 2 * c.modes_x);
+  if (e == cudaSuccess) e = alloc(&h->Fxb, (long long)c.nx_max * 2 * c.modes_x);
+  if (e == cudaSuccess) e = alloc(&h->Fxib, (long long)c.nx_max * 2 * c.modes_x);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fno_create(const fno_config *cfg, fno_handle **out) {
+  if (!cfg || !out) return ffail(nullptr, LB_ERR_ARG, "fno_create: null argument");
+  *out = nullptr;
+  const fno_config &c = *cfg;
+  if (c.width < 1 || c.hidden < 1 || c.layers < 1 || c.layers > kMaxLayers || c.modes_x < 1 || c.modes_y < 2 ||
+      c.modes_y % 2 != 0 || c.batch_max < 1 || c.nx_max < 2 || c.ny_max < 2 || 2 * c.modes_x > c.nx_max ||
+      c.modes_y > c.ny_max || c.width * c.modes_y * 2 * (int)sizeof(float) > 48 * 1024)
+    return ffail(nullptr, LB_ERR_ARG, "fno_create: bad sizes");
+  fno_handle *h = new (std::nothrow) fno_handle();
+  if (!h) return ffail(nullptr, LB_ERR_OOM, "fno_create: host allocation failed");
+  h->c = c;
+  h->st = (cudaStream_t)c.stream;
+  h->o = make_offsets(c);
+  const long long np = (long long)h->o.total;
+  cudaError_t e = alloc(&h->prm, np);
+  if (e == cudaSuccess) e = alloc(&h->grd, np);
+  if (e == cudaSuccess) e = alloc(&h->m1, np);
+  if (e == cudaSuccess) e = alloc(&h->m2, np);
+  if (e == cudaSuccess) e = alloc(&h->prmb, np);
+  if (e == cudaSuccess) e = cudaMemset(h->prm, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(h->grd, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(h->m1, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(h->m2, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(h->prmb, 0, np * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = alloc_workspace(h);
+  if (e != cudaSuccess) {
+    std::string m = std::string("fno_create: ") + cudaGetErrorString(e);
+    fno_destroy(h);
+    return ffail(nullptr, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, m);
+  }
+  if (cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(h->blas, h->st) != CUBLAS_STATUS_SUCCESS) {
+    fno_destroy(h);
+    return ffail(nullptr, LB_ERR_CUDA, "fno_create: cuBLAS initialisation failed");
+  }
+  *out = h;
+  return LB_OK;
+}
+
+int64_t fno_param_count(const fno_handle *h) { return h ? (int64_t)h->o.total : 0; }
+
+int fno_set_params(fno_handle *h, const float *host) {
+  if (!h || !host) return ffail(h, LB_ERR_ARG, "fno_set_params: null argument");
+  const long long np = (long long)h->o.total;
+  FNO_CUDA(h, cudaMemcpyAsync(h->prm, host, np * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  to_bf16_kernel<<<blocks_for(np), kThreads, 0, h->st>>>(h->prm, np, h->prmb);
+  FNO_CUDA(h, cudaGetLastError());
+  FNO_CUDA(h, cudaStreamSynchronize(h->st));
+  return LB_OK;
+}
+
+int fno_get_params(fno_handle *h, float *host) {
+  if (!h || !host) return ffail(h, LB_ERR_ARG, "fno_get_params: null argument");
+  FNO_CUDA(h, cudaMemcpyAsync(host, h->prm, h->o.total * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+  FNO_CUDA(h, cudaStreamSynchronize(h->st));
+  return LB_OK;
+}
+
+int fno_get_grads(fno_handle *h, float *host) {
+  if (!h || !host) return ffail(h, LB_ERR_ARG, "fno_get_grads: null argument");
+  FNO_CUDA(h, cudaMemcpyAsync(host, h->grd, h->o.total * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+  FNO_CUDA(h, cudaStreamSynchronize(h->st));
+  return LB_OK;
+}
+
+int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *params_dev, float *out) {
+  if (!h || !params_dev) return ffail(h, LB_ERR_ARG, "fno_forward: null argument");
+  const fno_config &c = h->c;
+  if (B < 1 || B > c.batch_max || nx > c.nx_max || ny > c.ny_max || nx < 2 * c.modes_x || ny < c.modes_y)
+    return ffail(h, LB_ERR_ARG, "fno_forward: batch or lattice outside the workspace bounds");
+  const int C = c.width, H = c.hidden, L = c.layers, mx = c.modes_x, my = c.modes_y;
+  const long long S = (long long)nx * ny, BCS = (long long)B * C * S;
+  const int R = B * C * ny;
+  cudaStream_t st = h->st;
+  if (h->tab_nx != nx || h->tab_ny != ny) {
+    dft_tables_kernel<<<blocks_for((long long)nx * mx), kThreads, 0, st>>>(nx, ny, mx, h->Fx, h->Fxi, h->Fxb, h->Fxib);
+    FNO_CUDA(h, cudaGetLastError());
+    h->tab_nx = nx;
+    h->tab_ny = ny;
+  }
+  const float *P = h->prm;
+  features_kernel<<<blocks_for((long long)B * S), kThreads, 0, st>>>(params_dev, B, nx, ny, h->x0);
+  lift_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->x0, P + h->o.P, P + h->o.p, B, C, S, h->V[0], h->Vb[0]);
+  FNO_CUDA(h, cudaGetLastError());
+  for (int l = 0; l < L; l++) {
+    // x-transform of every line: A[R, 2mx] = V[R, nx] Fx[nx, 2mx]
+    FNO_BLAS(h, gemm(h, false, false, R, 2 * mx, nx, h->V[l], h->Vb[l], nx, 0, h->Fx, h->Fxb, 2 * mx, 0, h->A, 2 * mx,
+                     0, 1, 0.f));
+    ydft_kernel<<<B * C, kThreads, 0, st>>>(h->A, ny, mx, my, h->Sh[l]);
+    mix_iy_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->Sh[l], P + h->o.Rr[l], P + h->o.Ri[l],
+                                                                          C, ny, mx, my, h->G, h->Gb);
+    FNO_CUDA(h, cudaGetLastError());
+    // inverse x-transform into z: Z[R, nx] = G[R, 2mx] Fxi[2mx, nx]
+    FNO_BLAS(h, gemm(h, false, false, R, nx, 2 * mx, h->G, h->Gb, 2 * mx, 0, h->Fxi, h->Fxib, nx, 0, h->Z[l], nx, 0, 1,
+                     0.f));
+    // z[b] += W v[b]  (one GEMM per field, strided)
+    FNO_BLAS(h, gemm(h, false, false, C, (int)S, C, P + h->o.W[l], h->prmb + h->o.W[l], C, 0, h->V[l], h->Vb[l], (int)S,
+                     (long long)C * S, h->Z[l], (int)S, (long long)C * S, B, 1.f));
+    bias_act_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->Z[l], P + h->o.w[l], C, S, BCS, l < L - 1 ? 1 : 0,
+                                                           h->V[l + 1], h->Vb[l + 1]);
+    FNO_CUDA(h, cudaGetLastError());
+  }
+  // projection: hp[b] = Q1 v_L[b]; out = Q2 gelu(hp + q1) + q2
+  FNO_BLAS(h, gemm(h, false, false, H, (int)S, C, P + h->o.Q1, h->prmb + h->o.Q1, C, 0, h->V[L], h->Vb[L], (int)S,
+                   (long long)C * S, h->hp, (int)S, (long long)H * S, B, 0.f));
+  project_kernel<<<blocks_for((long long)B * S), kThreads, 0, st>>>(h->hp, P + h->o.q1, P + h->o.Q2, P + h->o.q2, B, H,
+                                                                     S, h->out, out);
+  FNO_CUDA(h, cudaGetLastError());
+  h->B = B;
+  h->nx = nx;
+  h->ny = ny;
+  h->have_forward = true;
+  return LB_OK;
+}
+
+int fno_backward(fno_handle *h, const float *target, double *loss) {
+  if (!h || !target) return ffail(h, LB_ERR_ARG, "fno_backward: null argument");
+  if (!h->have_forward) return ffail(h, LB_ERR_STATE, "fno_backward: no forward pass");
+  const fno_config &c = h->c;
+  const int B = h->B, nx = h->nx, ny = h->ny, C = c.width, H = c.hidden, L = c.layers, mx = c.modes_x, my = c.modes_y;
+  const long long S = (long long)nx * ny, BCS = (long long)B * C * S, BS = (long long)B * S;
+  const int R = B * C * ny;
+  cudaStream_t st = h->st;
+  const float *P = h->prm;
+  const Offsets &o = h->o;
+  float *g = h->grd;
+  const unsigned lb = blocks_for(BS);
+  loss_kernel<<<lb, kThreads, 0, st>>>(h->out, target, BS, h->dout, h->partial);
+  finish_loss_kernel<<<1, kThreads, 0, st>>>(h->partial, (int)lb, BS, h->loss);
+  // projection: dq2, dQ2, dhp, dq1, dQ1, dV = Q1^T dhp
+  chan_sum_kernel<<<1, kThreads, 0, st>>>(h->dout, nullptr, 0, B, 1, 1, S, g + o.q2);
+  dQ2_kernel<<<H, kThreads, 0, st>>>(h->dout, h->hp, B, H, S, g + o.Q2);
+  project_back_kernel<<<blocks_for((long long)B * H * S), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, S,
+                                                                             (long long)B * H * S, h->dhp, h->dhpb);
+  chan_sum_kernel<<<H, kThreads, 0, st>>>(h->dhp, nullptr, 0, B, H, 1, S, g + o.q1);
+  FNO_CUDA(h, cudaGetLastError());
+  for (int b = 0; b < B; b++)
+    FNO_BLAS(h, gemm(h, false, true, H, C, (int)S, h->dhp + (long long)b * H * S, h->dhpb + (long long)b * H * S,
+                     (int)S, 0, h->V[L] + (long long)b * C * S, h->Vb[L] + (long long)b * C * S, (int)S, 0, g + o.Q1, C,
+                     0, 1, b ? 1.f : 0.f));
+  FNO_BLAS(h, gemm(h, true, false, C, (int)S, H, P + o.Q1, h->prmb + o.Q1, C, 0, h->dhp, h->dhpb, (int)S,
+                   (long long)H * S, h->dV, (int)S, (long long)C * S, B, 0.f));
+  for (int l = L - 1; l >= 0; l--) {
+    act_back_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->dV, h->Z[l], BCS, l < L - 1 ? 1 : 0, h->dZ, h->dZb);
+    chan_sum_kernel<<<C, kThreads, 0, st>>>(h->dZ, nullptr, 0, B, C, 1, S, g + o.w[l]);
+    FNO_CUDA(h, cudaGetLastError());
+    // dW = sum_b dz[b] v[b]^T
+    for (int b = 0; b < B; b++)
+      FNO_BLAS(h, gemm(h, false, true, C, C, (int)S, h->dZ + (long long)b * C * S, h->dZb + (long long)b * C * S,
+                       (int)S, 0, h->V[l] + (long long)b * C * S, h->Vb[l] + (long long)b * C * S, (int)S, 0,
+                       g + o.W[l], C, 0, 1, b ? 1.f : 0.f));
+    // spectral path: dG = dz Fxi^T, then the adjoints of the mixing and of the y-transform
+    FNO_BLAS(h, gemm(h, false, true, R, 2 * mx, nx, h->dZ, h->dZb, nx, 0, h->Fxi, h->Fxib, nx, 0, h->dG, 2 * mx, 0, 1,
+                     0.f));
+    mix_iy_back_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->dG, P + o.Rr[l], P + o.Ri[l], C, ny,
+                                                                               mx, my, h->dY, h->dS);
+    dR_kernel<<<my * mx, kThreads, 0, st>>>(h->Sh[l], h->dY, B, C, mx, my, g + o.Rr[l], g + o.Ri[l]);
+    ydft_back_kernel<<<B * C, kThreads, 0, st>>>(h->dS, ny, mx, my, h->dA, h->dAb);
+    FNO_CUDA(h, cudaGetLastError());
+    // dv = W^T dz (pointwise path) + dA Fx^T (spectral path)
+    FNO_BLAS(h, gemm(h, true, false, C, (int)S, C, P + o.W[l], h->prmb + o.W[l], C, 0, h->dZ, h->dZb, (int)S,
+                     (long long)C * S, h->dV, (int)S, (long long)C * S, B, 0.f));
+    FNO_BLAS(h, gemm(h, false, true, R, nx, 2 * mx, h->dA, h->dAb, 2 * mx, 0, h->Fx, h->Fxb, 2 * mx, 0, h->dV, nx, 0, 1,
+                     1.f));
+  }
+  // lift: dp = sum dv0, dP[o, c] = sum dv0[b, o, s] x0[b, c, s]
+  chan_sum_kernel<<<C, kThreads, 0, st>>>(h->dV, nullptr, 0, B, C, 1, S, g + o.p);
+  chan_sum_kernel<<<C * kFeatures, kThreads, 0, st>>>(h->dV, h->x0, 2, B, C, kFeatures, S, g + o.P);
+  FNO_CUDA(h, cudaGetLastError());
+  if (loss) {
+    FNO_CUDA(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FNO_CUDA(h, cudaStreamSynchronize(st));
+  }
+  return LB_OK;
+}
+
+int fno_adam(fno_handle *h, float lr, float beta1, float beta2, float eps, int32_t t) {
+  if (!h || t < 1) return ffail(h, LB_ERR_ARG, "fno_adam: bad arguments");
+  const long long np = (long long)h->o.total;
+  const float c1 = 1.0f - powf(beta1, (float)t), c2 = 1.0f - powf(beta2, (float)t);
+  adam_kernel<<<blocks_for(np), kThreads, 0, h->st>>>(h->prm, h->grd, h->m1, h->m2, np, lr, beta1, beta2, eps, c1, c2,
+                                                       h->prmb);
+  FNO_CUDA(h, cudaGetLastError());
+  return LB_OK;
+}
+
+int fno_destroy(fno_handle *h) {
+  if (!h) return LB_OK;
+  cudaStreamSynchronize(h->st);
+  free_workspace(h);
+  cudaFree(h->prm);
+  cudaFree(h->grd);
+  cudaFree(h->m1);
+  cudaFree(h->m2);
+  cudaFree(h->prmb);
+  if (h->blas) cublasDestroy(h->blas);
+  delete h;
+  return LB_OK;
+}
+
+const char *fno_last_error(const fno_handle *h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

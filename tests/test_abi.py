@@ -10,10 +10,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+def declared_functions(header="lb.h", prefix="lb_"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -31,6 +31,19 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_library_exports_every_network_symbol(lib):
+    names = declared_functions("fno.h", "fno_")
+    assert "fno_forward" in names and "fno_backward" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_network_binding_has_same_names():
+    from paper_1307_6703_gb300 import fno
+    for name in declared_functions("fno.h", "fno_"):
+        assert callable(getattr(fno, name)), name
 
 
 def test_binding_has_same_names():
