@@ -61,13 +61,16 @@ def profiled_traffic(precision: str):
     return traffic if digest == kernel_source_digest() else None
 
 
-def measured_peaks():
+def measured_peaks(key: str = "hbm_gbs"):
+    """Measured peak from MEASURED_PEAKS.json (HBM copy GB/s, or dense bf16
+    TFLOP/s), else the fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        if key in d:
+            return float(d[key]), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}[key], "fallback"
 
 
 def max_over_ranks(value: float, dist=None) -> float:
@@ -375,6 +378,104 @@ def run_batch(args):
     return 0
 
 
+def run_warmstart(args):
+    """Learned warm start: train the network on solver-generated steady
+    states, then steps (and wall time, network inference included) to the
+    steady state from the prediction against from a noisy uniform state, on
+    held-out draws at 512x128 and 2048x512."""
+    import torch
+    from paper_1307_6703_gb300 import warmstart as ws
+    from paper_1307_6703_gb300.fno import Fno
+    from oracle import fno as ref  # seeded initial weights only (the tests use the same)
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ptr = ws.sample_params(1024, seed=1)
+    n1, d1 = ws.generate(ptr[:768], 256, 64, 25000, seed=1)
+    n2, d2 = ws.generate(ptr[768:], 512, 128, 30000, seed=2)
+    k1, k2 = d1 <= ws.STEADY_TOL, d2 <= ws.STEADY_TOL
+    gen_s = time.perf_counter() - t0
+    net = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=16,
+              nx_max=512, ny_max=128, gemm_bf16=True)
+    p = ref.init_params(32, 64, 4, 16, 8, seed=0, outputs=3)
+    names = ["P", "p"] + sum([[f"W{l}", f"w{l}", f"Rr{l}", f"Ri{l}"] for l in range(4)], []) + ["Q1", "q1", "Q2", "q2"]
+    net.set_params(np.concatenate([np.asarray(p[k]).ravel() for k in names]).astype(np.float32))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = ws.train(net, [(ptr[:768][k1], n1[k1]), (ptr[768:][k2], n2[k2])], steps=6000, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # network throughput on one training batch (256x64, 16 fields), device time
+    prm = torch.tensor(ptr[:16], dtype=torch.float32, device="cuda")
+    tgt = torch.zeros((16, 3, 64, 256), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(tgt)
+    for _ in range(3):
+        net.forward(prm, 256, 64, out)
+    ev0.record()
+    for _ in range(20):
+        net.forward(prm, 256, 64, out)
+    ev1.record()
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / 20
+    ev0.record()
+    for _ in range(20):
+        net.forward(prm, 256, 64, out)
+        net.backward(tgt, want_loss=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    step_ms = ev0.elapsed_time(ev1) / 20
+    S = 256 * 64
+    flop_fwd = 16 * S * (4 * (2 * 32 * 32 * 2 + 2 * 32 * 32) + 2 * 64 * 32 + 2 * 3 * 64)
+    results = {}
+    for (nx, ny, n, block, cap) in ((512, 128, 16, 500, 40000), (2048, 512, 4, 5000, 1500000)):
+        pte = ws.sample_params(n, seed=99 if nx == 512 else 123)
+        big = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=1,
+                  nx_max=nx, ny_max=ny, gemm_bf16=True)
+        big.set_params(net.get_params())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pred = np.concatenate([ws.mass_projected(ws.predict(big, pte[i:i + 1], nx, ny)) for i in range(n)])
+        infer_s = time.perf_counter() - t0
+        big.close()
+        t0 = time.perf_counter()
+        s_noise = ws.steps_to_steady(pte, nx, ny, None, seed=7, block=block, max_steps=cap)
+        noise_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        s_pred = ws.steps_to_steady(pte, nx, ny, pred, seed=7, block=block, max_steps=cap)
+        pred_s = time.perf_counter() - t0
+        results[f"{nx}x{ny}"] = {
+            "lattices": n, "steps_noise": s_noise.tolist(), "steps_warm": s_pred.tolist(),
+            "mean_steps_noise": float(s_noise.mean()), "mean_steps_warm": float(s_pred.mean()),
+            "step_ratio": round(float(s_pred.mean() / s_noise.mean()), 3),
+            "wall_s_noise": round(noise_s, 2), "wall_s_warm": round(pred_s + infer_s, 2),
+            "inference_s": round(infer_s, 3)}
+    net.close()
+    r = results["512x128"]
+    peak, peak_kind = measured_peaks("bf16_tflops")
+    achieved = 3 * flop_fwd / (step_ms * 1e-3) / 1e12
+    line = {
+        "metric": "steps_to_steady_ratio", "value": r["step_ratio"], "unit": "warm/noisy",
+        "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (network GEMMs bf16)", "data": "synthetic (solver-generated)",
+        "config": {"workload": "warm_start_512x128_and_2048x512", "train_fields": int(k1.sum() + k2.sum()),
+                   "train_steps": 6000, "data_gen_s": round(gen_s, 1), "train_s": round(train_s, 1),
+                   "final_loss": hist[-1][1], "steady_tol_per_1000_steps": ws.STEADY_TOL},
+        "results": results,
+        "network": {"forward_ms_batch16_256x64": round(fwd_ms, 3),
+                    "train_step_ms_batch16_256x64": round(step_ms, 3)},
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 5) if peak else None,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "network training step (forward + backward, ~3x forward FLOPs)"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +485,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=sorted(B_ALG), default="fp32")
-    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "warmstart"], default="single",
                     help="single: the 4096x1024 lattice; batch: the seeded ensemble of "
                          "independent lattices through the batched solver")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -397,6 +498,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

@@ -1,11 +1,12 @@
 /*
  * fno.h -- C ABI of the learned warm start: a small Fourier neural operator
  * that maps the problem parameters (wall speed U_w, potential amplitude A0,
- * wavelength lambda, reduced temperature T_r) to the steady density field
- * n(x, y) of the lattice Boltzmann solver (include/lb.h), used as its
- * initial condition.  The paper has no counterpart: its steady states come
- * from running the scheme of Sec. II; the network only shortens that run,
- * and the solver remains the judge of the result.
+ * wavelength lambda, reduced temperature T_r) to the steady fields of the
+ * lattice Boltzmann solver (include/lb.h) -- density and velocity,
+ * `outputs` channels -- used as its initial condition.  The paper has no
+ * counterpart: its steady states come from running the scheme of Sec. II;
+ * the network only shortens that run, and the solver remains the judge of
+ * the result.
  *
  * Network (all sizes from fno_config; FP32 parameters and activations,
  * GEMMs in BF16 with FP32 accumulation unless gemm_bf16 = 0):
@@ -17,15 +18,16 @@
  *             kx = 0..modes_x-1 and y-modes 0..modes_y/2-1, -modes_y/2..-1;
  *             the inverse is the real transform of the kept modes with kx > 0
  *             counted twice and scale 1/(nx ny).
- *   project   out = Q2 gelu(Q1 v_L + q1) + q2;   loss = mean (out - target)^2
+ *   project   out = Q2 gelu(Q1 v_L + q1) + q2  (`outputs` channels);
+ *             loss = mean over fields, channels and sites of (out - target)^2
  * gelu(z) = z Phi(z), Phi the standard normal distribution function.
  *
  * Parameter vector (FP32, this order): P [width][5], p [width]; for each
  * layer: W [width][width], w [width], Rr [modes_y][modes_x][width(in)][width(out)],
- * Ri (same shape); Q1 [hidden][width], q1 [hidden], Q2 [hidden], q2 [1].
+ * Ri (same shape); Q1 [hidden][width], q1 [hidden], Q2 [outputs][hidden], q2 [outputs].
  *
  * Layouts: params_dev [batch][4] = (U_w, A0, lambda, T_r) as float;
- * fields [batch][ny][nx] float, x fastest.  All field and parameter
+ * fields [batch][outputs][ny][nx] float, x fastest.  All field and parameter
  * pointers of fno_forward / fno_backward are DEVICE pointers; the calls
  * enqueue work on the handle's stream.  Return values are the LB_* codes
  * of lb.h (0 = success).
@@ -42,7 +44,7 @@ extern "C" {
 #endif
 
 typedef struct {
-  int32_t width, hidden, layers, modes_x, modes_y;
+  int32_t width, hidden, layers, modes_x, modes_y, outputs;
   int32_t batch_max, nx_max, ny_max; /* workspace bounds                   */
   int32_t gemm_bf16;                 /* 1: BF16 GEMM inputs; 0: FP32       */
   void *stream;                      /* cudaStream_t; NULL = default       */
@@ -65,13 +67,13 @@ int fno_set_params(fno_handle *h, const float *host);
 int fno_get_params(fno_handle *h, float *host);
 int fno_get_grads(fno_handle *h, float *host);
 
-/* Forward pass over `batch` fields of nx x ny: out[batch][ny][nx] (device).
- * Keeps the activations for fno_backward.                                  */
+/* Forward pass over `batch` fields of nx x ny: out[batch][outputs][ny][nx]
+ * (device).  Keeps the activations for fno_backward.                       */
 int fno_forward(fno_handle *h, int32_t batch, int32_t nx, int32_t ny, const float *params_dev, float *out);
 
-/* Loss of the last forward pass against target[batch][ny][nx] (device),
- * and its gradient with respect to every parameter, which REPLACES the
- * gradient buffer.  *loss (host, may be NULL) receives the loss
+/* Loss of the last forward pass against target[batch][outputs][ny][nx]
+ * (device), and its gradient with respect to every parameter, which
+ * REPLACES the gradient buffer.  *loss (host, may be NULL) receives the loss
  * (synchronises the stream when non-NULL).                                */
 int fno_backward(fno_handle *h, const float *target, double *loss);
 

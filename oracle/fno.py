@@ -16,8 +16,9 @@ The network (definitions written out plainly, no blocking or fusion):
             -my/2..-1, a complex width x width matrix per mode, and the
             real inverse transform of those modes (kx > 0 counted twice for
             the conjugate half, scale 1/(nx ny))
-  project   h = gelu(Q1 v4 + q1),  out = Q2 h + q2     (Q1: hidden x width)
-  loss      mean over b, y, x of (out - target)^2
+  project   h = gelu(Q1 v4 + q1),  out = Q2 h + q2     (Q1: hidden x width,
+            Q2: outputs x hidden)
+  loss      mean over b, output channel, y, x of (out - target)^2
 gelu(z) = z Phi(z) with Phi the standard normal distribution function.
 """
 from __future__ import annotations
@@ -81,7 +82,8 @@ def idft_modes(V: np.ndarray, ny: int, nx: int) -> np.ndarray:
     return out.real / (nx * ny)
 
 
-def init_params(width: int, hidden: int, layers: int, mx: int, my: int, seed: int) -> dict:
+def init_params(width: int, hidden: int, layers: int, mx: int, my: int, seed: int,
+                outputs: int = 1) -> dict:
     """Seeded initial parameters (the CUDA network is given the same values)."""
     rng = np.random.default_rng(seed)
     p = {"P": rng.standard_normal((width, N_FEATURES)) / math.sqrt(N_FEATURES),
@@ -94,13 +96,13 @@ def init_params(width: int, hidden: int, layers: int, mx: int, my: int, seed: in
         p[f"Ri{l}"] = s * rng.uniform(0, 1, (my, mx, width, width))
     p["Q1"] = rng.standard_normal((hidden, width)) / math.sqrt(width)
     p["q1"] = np.zeros(hidden)
-    p["Q2"] = rng.standard_normal((1, hidden)) / math.sqrt(hidden)
-    p["q2"] = np.zeros(1)
+    p["Q2"] = rng.standard_normal((outputs, hidden)) / math.sqrt(hidden)
+    p["q2"] = np.zeros(outputs)
     return p
 
 
 def forward(p: dict, x: np.ndarray, layers: int, mx: int, my: int) -> np.ndarray:
-    """x[b, 5, ny, nx] -> out[b, ny, nx]."""
+    """x[b, 5, ny, nx] -> out[b, outputs, ny, nx]."""
     ny, nx = x.shape[-2:]
     v = np.einsum("oc,bcyx->boyx", p["P"], x) + p["p"][None, :, None, None]
     for l in range(layers):
@@ -111,8 +113,7 @@ def forward(p: dict, x: np.ndarray, layers: int, mx: int, my: int) -> np.ndarray
         z = np.einsum("oc,bcyx->boyx", p[f"W{l}"], v) + p[f"w{l}"][None, :, None, None] + K
         v = gelu(z) if l < layers - 1 else z
     h = gelu(np.einsum("hc,bcyx->bhyx", p["Q1"], v) + p["q1"][None, :, None, None])
-    out = np.einsum("oh,bhyx->boyx", p["Q2"], h) + p["q2"][None, :, None, None]
-    return out[:, 0]
+    return np.einsum("oh,bhyx->boyx", p["Q2"], h) + p["q2"][None, :, None, None]
 
 
 def loss(p: dict, x: np.ndarray, target: np.ndarray, layers: int, mx: int, my: int) -> float:

@@ -47,8 +47,8 @@ Offsets make_offsets(const fno_config &c) {
   }
   o.Q1 = at; at += H * C;
   o.q1 = at; at += H;
-  o.Q2 = at; at += H;
-  o.q2 = at; at += 1;
+  o.Q2 = at; at += (size_t)c.outputs * H;
+  o.q2 = at; at += c.outputs;
   o.total = at;
   return o;
 }
@@ -190,23 +190,33 @@ __global__ void bias_act_kernel(float *__restrict__ z, const float *__restrict__
   }
 }
 
-// hp += q1 (kept); out[b, s] = sum_h Q2[h] gelu(hp[b, h, s]) + q2.
+constexpr int kMaxOutputs = 4;
+
+// hp += q1 (kept); out[b, j, s] = sum_h Q2[j, h] gelu(hp[b, h, s]) + q2[j].
 __global__ void project_kernel(float *__restrict__ hp, const float *__restrict__ q1, const float *__restrict__ Q2,
-                               const float *__restrict__ q2, int B, int H, long long S, float *__restrict__ out,
+                               const float *__restrict__ q2, int B, int H, int O, long long S, float *__restrict__ out,
                                float *__restrict__ out_user) {
   const long long total = (long long)B * S;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(i / S);
     const long long s = i - (long long)b * S;
     float *h = hp + (long long)b * H * S + s;
-    float acc = q2[0];
+    float acc[kMaxOutputs];
+#pragma unroll
+    for (int j = 0; j < kMaxOutputs; j++) acc[j] = j < O ? q2[j] : 0.f;
     for (int k = 0; k < H; k++) {
       const float z = h[k * S] + q1[k];
       h[k * S] = z;
-      acc += Q2[k] * gelu(z);
+      const float a = gelu(z);
+#pragma unroll
+      for (int j = 0; j < kMaxOutputs; j++)
+        if (j < O) acc[j] += Q2[j * H + k] * a;
     }
-    out[i] = acc;
-    if (out_user) out_user[i] = acc;
+    for (int j = 0; j < O; j++) {
+      const long long e = ((long long)b * O + j) * S + s;
+      out[e] = acc[j];
+      if (out_user) out_user[e] = acc[j];
+    }
   }
 }
 
@@ -233,14 +243,16 @@ __global__ void finish_loss_kernel(const double *__restrict__ partial, int n, lo
   if (threadIdx.x == 0) *loss = r / (double)total;
 }
 
-// dhp[b, h, s] = Q2[h] dout[b, s] gelu'(hp[b, h, s])
+// dhp[b, h, s] = sum_j Q2[j, h] dout[b, j, s] gelu'(hp[b, h, s])
 __global__ void project_back_kernel(const float *__restrict__ hp, const float *__restrict__ Q2,
-                                    const float *__restrict__ dout, int H, long long S, long long total,
+                                    const float *__restrict__ dout, int H, int O, long long S, long long total,
                                     float *__restrict__ dhp, __nv_bfloat16 *__restrict__ dhpb) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long s = i % S;
     const int k = (int)((i / S) % H), b = (int)(i / (S * H));
-    const float d = Q2[k] * dout[(long long)b * S + s] * gelu_grad(hp[i]);
+    float acc = 0.f;
+    for (int j = 0; j < O; j++) acc += Q2[j * H + k] * dout[((long long)b * O + j) * S + s];
+    const float d = acc * gelu_grad(hp[i]);
     dhp[i] = d;
     dhpb[i] = __float2bfloat16_rn(d);
   }
@@ -269,20 +281,20 @@ __global__ void chan_sum_kernel(const float *__restrict__ a, const float *__rest
   if (threadIdx.x == 0) out[ch] = (float)r;
 }
 
-// dQ2[k] = sum_{b, s} dout[b, s] gelu(hp[b, k, s]); one block per k.
-__global__ void dQ2_kernel(const float *__restrict__ dout, const float *__restrict__ hp, int B, int H, long long S,
-                           float *__restrict__ out) {
+// dQ2[j, k] = sum_{b, s} dout[b, j, s] gelu(hp[b, k, s]); one block per (j, k).
+__global__ void dQ2_kernel(const float *__restrict__ dout, const float *__restrict__ hp, int B, int H, int O,
+                           long long S, float *__restrict__ out) {
   __shared__ double sm[kThreads];
-  const int k = blockIdx.x;
+  const int j = blockIdx.x / H, k = blockIdx.x - j * H;
   double acc = 0.0;
   const long long n = (long long)B * S;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     const int b = (int)(i / S);
     const long long s = i - (long long)b * S;
-    acc += (double)(dout[i] * gelu(hp[((long long)b * H + k) * S + s]));
+    acc += (double)(dout[((long long)b * O + j) * S + s] * gelu(hp[((long long)b * H + k) * S + s]));
   }
   const double r = block_sum(acc, sm);
-  if (threadIdx.x == 0) out[k] = (float)r;
+  if (threadIdx.x == 0) out[blockIdx.x] = (float)r;
 }
 
 // dz = dv * gelu'(z) (or dv for the last layer), with a BF16 copy.
@@ -514,7 +526,7 @@ cudaError_t alloc_workspace(fno_handle *h) {
   const fno_config &c = h->c;
   const long long S = (long long)c.nx_max * c.ny_max, B = c.batch_max;
   h->cap_bcs = B * c.width * S;
-  h->cap_bs = B * S;
+  h->cap_bs = B * c.outputs * S;
   h->cap_bhs = B * c.hidden * S;
   h->cap_line = B * c.width * (long long)c.ny_max * 2 * c.modes_x;
   h->cap_modes = B * c.width * (long long)c.modes_x * c.modes_y * 2;
@@ -562,7 +574,8 @@ int fno_create(const fno_config *cfg, fno_handle **out) {
   const fno_config &c = *cfg;
   if (c.width < 1 || c.hidden < 1 || c.layers < 1 || c.layers > kMaxLayers || c.modes_x < 1 || c.modes_y < 2 ||
       c.modes_y % 2 != 0 || c.batch_max < 1 || c.nx_max < 2 || c.ny_max < 2 || 2 * c.modes_x > c.nx_max ||
-      c.modes_y > c.ny_max || c.width * c.modes_y * 2 * (int)sizeof(float) > 48 * 1024)
+      c.modes_y > c.ny_max || c.width * c.modes_y * 2 * (int)sizeof(float) > 48 * 1024 || c.outputs < 1 ||
+      c.outputs > kMaxOutputs)
     return ffail(nullptr, LB_ERR_ARG, "fno_create: bad sizes");
   fno_handle *h = new (std::nothrow) fno_handle();
   if (!h) return ffail(nullptr, LB_ERR_OOM, "fno_create: host allocation failed");
@@ -661,7 +674,7 @@ int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *p
   FNO_BLAS(h, gemm(h, false, false, H, (int)S, C, P + h->o.Q1, h->prmb + h->o.Q1, C, 0, h->V[L], h->Vb[L], (int)S,
                    (long long)C * S, h->hp, (int)S, (long long)H * S, B, 0.f));
   project_kernel<<<blocks_for((long long)B * S), kThreads, 0, st>>>(h->hp, P + h->o.q1, P + h->o.Q2, P + h->o.q2, B, H,
-                                                                     S, h->out, out);
+                                                                     c.outputs, S, h->out, out);
   FNO_CUDA(h, cudaGetLastError());
   h->B = B;
   h->nx = nx;
@@ -675,7 +688,8 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
   if (!h->have_forward) return ffail(h, LB_ERR_STATE, "fno_backward: no forward pass");
   const fno_config &c = h->c;
   const int B = h->B, nx = h->nx, ny = h->ny, C = c.width, H = c.hidden, L = c.layers, mx = c.modes_x, my = c.modes_y;
-  const long long S = (long long)nx * ny, BCS = (long long)B * C * S, BS = (long long)B * S;
+  const int O = c.outputs;
+  const long long S = (long long)nx * ny, BCS = (long long)B * C * S, BS = (long long)B * O * S;
   const int R = B * C * ny;
   cudaStream_t st = h->st;
   const float *P = h->prm;
@@ -685,9 +699,9 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
   loss_kernel<<<lb, kThreads, 0, st>>>(h->out, target, BS, h->dout, h->partial);
   finish_loss_kernel<<<1, kThreads, 0, st>>>(h->partial, (int)lb, BS, h->loss);
   // projection: dq2, dQ2, dhp, dq1, dQ1, dV = Q1^T dhp
-  chan_sum_kernel<<<1, kThreads, 0, st>>>(h->dout, nullptr, 0, B, 1, 1, S, g + o.q2);
-  dQ2_kernel<<<H, kThreads, 0, st>>>(h->dout, h->hp, B, H, S, g + o.Q2);
-  project_back_kernel<<<blocks_for((long long)B * H * S), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, S,
+  chan_sum_kernel<<<O, kThreads, 0, st>>>(h->dout, nullptr, 0, B, O, 1, S, g + o.q2);
+  dQ2_kernel<<<O * H, kThreads, 0, st>>>(h->dout, h->hp, B, H, O, S, g + o.Q2);
+  project_back_kernel<<<blocks_for((long long)B * H * S), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, O, S,
                                                                              (long long)B * H * S, h->dhp, h->dhpb);
   chan_sum_kernel<<<H, kThreads, 0, st>>>(h->dhp, nullptr, 0, B, H, 1, S, g + o.q1);
   FNO_CUDA(h, cudaGetLastError());

@@ -15,7 +15,8 @@ from .lb import LBError, load_library
 
 class fno_config(C.Structure):
     _fields_ = [("width", C.c_int32), ("hidden", C.c_int32), ("layers", C.c_int32),
-                ("modes_x", C.c_int32), ("modes_y", C.c_int32), ("batch_max", C.c_int32),
+                ("modes_x", C.c_int32), ("modes_y", C.c_int32), ("outputs", C.c_int32),
+                ("batch_max", C.c_int32),
                 ("nx_max", C.c_int32), ("ny_max", C.c_int32), ("gemm_bf16", C.c_int32),
                 ("stream", C.c_void_p)]
 
@@ -71,10 +72,11 @@ def fno_create(cfg: fno_config) -> int:
 class Fno:
     """Network handle: width, hidden, layers, modes and workspace bounds."""
 
-    def __init__(self, *, width=32, hidden=64, layers=4, modes_x=16, modes_y=8, batch_max=16,
-                 nx_max=512, ny_max=128, gemm_bf16=True, stream=None):
-        self.cfg = fno_config(width, hidden, layers, modes_x, modes_y, batch_max, nx_max, ny_max,
-                              int(bool(gemm_bf16)), stream)
+    def __init__(self, *, width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3,
+                 batch_max=16, nx_max=512, ny_max=128, gemm_bf16=True, stream=None):
+        self.cfg = fno_config(width, hidden, layers, modes_x, modes_y, outputs, batch_max, nx_max,
+                              ny_max, int(bool(gemm_bf16)), stream)
+        self.outputs = outputs
         self.h = fno_create(self.cfg)
         self.n_params = int(_lib().fno_param_count(self.h))
         self.t = 0
@@ -96,7 +98,7 @@ class Fno:
         return out
 
     def forward(self, params_dev, nx: int, ny: int, out) -> None:
-        """params_dev: device float [B][4] (U_w, A0, lambda, T_r); out: device [B][ny][nx]."""
+        """params_dev: device float [B][4] (U_w, A0, lambda, T_r); out: device [B][outputs][ny][nx]."""
         B = params_dev.shape[0] if hasattr(params_dev, "shape") else 1
         _check(_lib().fno_forward(self.h, B, nx, ny, _ptr(params_dev), _ptr(out)), self.h)
 

@@ -11,7 +11,7 @@ from oracle import fno as ref
 
 pytestmark = pytest.mark.gpu
 
-CFG = dict(width=8, hidden=16, layers=2, modes_x=8, modes_y=4)
+CFG = dict(width=8, hidden=16, layers=2, modes_x=8, modes_y=4, outputs=3)
 NX, NY = 64, 16
 PARAMS = np.array([[0.03, 6e-4, 32.0, 0.95], [0.0, 3e-4, 64.0, 0.93]])
 
@@ -45,7 +45,8 @@ def unpack(flat, p, layers):
 
 
 def _reference_params(seed):
-    p = ref.init_params(CFG["width"], CFG["hidden"], CFG["layers"], CFG["modes_x"], CFG["modes_y"], seed)
+    p = ref.init_params(CFG["width"], CFG["hidden"], CFG["layers"], CFG["modes_x"], CFG["modes_y"], seed,
+                        outputs=CFG["outputs"])
     rng = np.random.default_rng(seed + 1)
     for k in list(p):  # exercise the biases and scale the spectral weights up
         if k in ("p", "q1", "q2") or k.startswith("w"):
@@ -61,7 +62,7 @@ def _gpu_run(p, target, bf16):
     net = Fno(**CFG, batch_max=2, nx_max=NX, ny_max=NY, gemm_bf16=bf16)
     net.set_params(pack(p, CFG["layers"]).astype(np.float32))
     prm = torch.tensor(PARAMS, dtype=torch.float32, device="cuda")
-    out = torch.empty((2, NY, NX), dtype=torch.float32, device="cuda")
+    out = torch.empty((2, CFG["outputs"], NY, NX), dtype=torch.float32, device="cuda")
     net.forward(prm, NX, NY, out)
     loss = net.backward(torch.tensor(target, dtype=torch.float32, device="cuda"))
     grads = unpack(net.get_grads(), p, CFG["layers"])
@@ -94,7 +95,7 @@ def test_network_forward_and_gradients(bf16):
     p = _reference_params(3)
     x = ref.features(PARAMS, NX, NY)
     rng = np.random.default_rng(4)
-    target = rng.standard_normal((2, NY, NX)) * 0.5
+    target = rng.standard_normal((2, CFG["outputs"], NY, NX)) * 0.5
     out, loss, grads = _gpu_run(p, target, bf16)
     o_ref = ref.forward(p, x, CFG["layers"], CFG["modes_x"], CFG["modes_y"])
     l_ref = ref.loss(p, x, target, CFG["layers"], CFG["modes_x"], CFG["modes_y"])
@@ -122,9 +123,9 @@ def test_adam_step_matches_the_update_rule():
     flat = pack(p, CFG["layers"]).astype(np.float32)
     net.set_params(flat)
     prm = torch.tensor(PARAMS, dtype=torch.float32, device="cuda")
-    out = torch.empty((2, NY, NX), dtype=torch.float32, device="cuda")
+    out = torch.empty((2, CFG["outputs"], NY, NX), dtype=torch.float32, device="cuda")
     net.forward(prm, NX, NY, out)
-    net.backward(torch.zeros((2, NY, NX), dtype=torch.float32, device="cuda"))
+    net.backward(torch.zeros((2, CFG["outputs"], NY, NX), dtype=torch.float32, device="cuda"))
     g = net.get_grads().astype(np.float64)
     net.adam(1e-3, 0.9, 0.999, 1e-8)
     new = net.get_params().astype(np.float64)

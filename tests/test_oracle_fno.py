@@ -82,7 +82,7 @@ def test_features_definition():
 
 def test_forward_is_affine_in_the_last_layer():
     """out is affine in (Q2, q2): doubling Q2 and q2 doubles out."""
-    p = fno.init_params(4, 6, 2, 4, 4, seed=5)
+    p = fno.init_params(4, 6, 2, 4, 4, seed=5, outputs=3)
     x = fno.features(np.array([[0.02, 5e-4, 32.0, 0.95]]), 32, 8)
     o1 = fno.forward(p, x, 2, 4, 4)
     p["Q2"] *= 2.0
