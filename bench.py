@@ -476,6 +476,72 @@ def run_warmstart(args):
     return 0
 
 
+def _observables(n):
+    """Density profile <n>_x(y), and the dominant wavelength (sites) of the
+    density along x at quarter and three-quarter height."""
+    prof = n.mean(axis=1)
+    lam = []
+    for y in (n.shape[0] // 4, 3 * n.shape[0] // 4):
+        spec = np.abs(np.fft.rfft(n[y] - n[y].mean()))
+        k = int(np.argmax(spec[1:]) + 1)
+        lam.append(n.shape[1] / k)
+    return prof, lam
+
+
+def run_precision(args):
+    """Storage precisions against the FP64 path on the same lattice and
+    steps: error of the density profile <n>_x(y) and of the field, mass
+    drift, dominant wavelength along x."""
+    import torch
+    from paper_1307_6703_gb300 import LB_BF16DEV, LB_FP16DEV, LB_FP32, LB_FP64
+    from paper_1307_6703_gb300.workloads import C4, noise_field
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return 0
+    w = C4.with_(nx=args.precision_nx, ny=args.precision_ny)
+    n0 = noise_field(w)
+    rows = {}
+    ref = None
+    for name, prec in (("fp64", LB_FP64), ("fp32", LB_FP32), ("bf16dev", LB_BF16DEV), ("fp16dev", LB_FP16DEV)):
+        s = make_solver(w, None, {LB_FP32: "fp32", LB_BF16DEV: "bf16dev", LB_FP16DEV: "fp16dev"}.get(prec, "fp32")) \
+            if prec != LB_FP64 else None
+        if prec == LB_FP64:
+            from paper_1307_6703_gb300 import Solver
+            s = Solver(w.nx, w.ny, precision=LB_FP64, walls=w.walls, a=w.a, b=w.b, T=w.T, kappa=w.kappa,
+                       tau=w.tau, A0=w.A0, lam=w.lam, u_bot=w.u_bot, u_top=w.u_top, N=w.N, Q=w.Q)
+        s.init_fields(n0)
+        rc, (m0, _, _) = s.reduce()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(args.steps)
+        rc, (m1, _, _) = s.reduce()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        n = s.moments()[0]
+        s.close()
+        prof, lam = _observables(n)
+        row = {"mass_drift": abs(m1 - m0) / m0, "wavelength_x": lam, "reduce_rc": rc,
+               "mlups": round(w.nx * w.ny * args.steps / el / 1e6, 1)}
+        if ref is None:
+            ref = (n, prof, lam)
+        else:
+            row["profile_max_rel_err"] = float(np.abs(prof - ref[1]).max() / np.abs(ref[1]).max())
+            row["field_max_rel_err"] = float(np.abs(n - ref[0]).max() / np.abs(ref[0]).max())
+            row["field_rms_err"] = float(np.sqrt(np.mean((n - ref[0]) ** 2)))
+            row["wavelength_equal"] = lam == ref[2]
+        rows[name] = row
+    line = {"metric": "error_vs_fp64", "value": rows["bf16dev"]["profile_max_rel_err"],
+            "unit": "max rel error of <n>_x(y), bf16 storage", "n_gpus": 1, "steps": args.steps,
+            "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 reference)", "data": "synthetic",
+            "config": {"workload": f"{w.name} at {w.nx}x{w.ny}", "nx": w.nx, "ny": w.ny},
+            "precisions": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,10 +551,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=sorted(B_ALG), default="fp32")
-    ap.add_argument("--workload", choices=["single", "batch", "warmstart"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "warmstart", "precision"], default="single",
                     help="single: the 4096x1024 lattice; batch: the seeded ensemble of "
                          "independent lattices through the batched solver")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--precision-nx", type=int, default=4096)
+    ap.add_argument("--precision-ny", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -500,6 +568,8 @@ def main():
         return run_batch(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_ours(args)
 
 

@@ -208,3 +208,33 @@ def test_dev16_default_reference_is_critical_density():
     assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
     a.close()
     b.close()
+
+
+def test_storage_observables_against_fp64():
+    """The headline physics (sheared quench, A0 = 1e-4, lambda = 512 scaled
+    to 1024x256, lambda = 128) for 5000 steps in every storage, against the
+    GPU FP64 path (itself bit-identical to the oracle): density profile
+    <n>_x(y), dominant wavelength along x, mass drift."""
+    from paper_1307_6703_gb300 import LB_FP32, LB_FP64
+    from gpu_util import solver_for
+    w = C4.with_(nx=1024, ny=256, lam=128.0)
+    n0 = noise_field(w)
+    res = {}
+    for name, prec in (("fp64", LB_FP64), ("fp32", LB_FP32), ("bf16", LB_BF16DEV), ("fp16", LB_FP16DEV)):
+        s = solver_for(w, prec) if prec in (LB_FP64, LB_FP32) else dev16_solver(w, prec, RHO_REF)
+        s.init_fields(n0)
+        m0 = s.reduce()[1][0]
+        s.step(5000)
+        rc, (m1, _, _) = s.reduce()
+        n = s.moments()[0]
+        s.close()
+        spec = np.abs(np.fft.rfft(n[w.ny // 4] - n[w.ny // 4].mean()))
+        res[name] = (n.mean(axis=1), w.nx / (np.argmax(spec[1:]) + 1), abs(m1 - m0) / m0, rc)
+    prof64, lam64, drift64, _ = res["fp64"]
+    assert lam64 == 128.0 and drift64 < 1e-12
+    bounds = {"fp32": 1e-3, "fp16": 1e-2, "bf16": 5e-2}
+    for name, bound in bounds.items():
+        prof, lam, drift, rc = res[name]
+        err = np.abs(prof - prof64).max() / np.abs(prof64).max()
+        print(f"{name}: profile error {err:.2e}, wavelength {lam}, mass drift {drift:.2e}")
+        assert rc == 0 and lam == lam64 and drift < 1e-5 and err < bound
