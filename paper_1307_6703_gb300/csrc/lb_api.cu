@@ -280,6 +280,7 @@ lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   A.fout = fout;
   A.fdev = dev16(h) ? (void *)((char *)fout + (size_t)h->plane * sizeof(float)) : nullptr;
   A.partials = h->d_cta;
+  A.records = 1;
   A.err = h->d_err;
   return A;
 }
@@ -469,8 +470,11 @@ int lb_step(lb_handle *h, int64_t nsteps) {
       h->step++;
     }
   } else if (h->sweep) {
+    // Per-CTA mass/momentum records only on the last step: lb_reduce reads
+    // only the current state's.
     for (int64_t k = 0; k < nsteps; k++) {
-      const lbk::SweepArgs A = sweep_args(h, (float *)h->f[h->cur ^ 1]);
+      lbk::SweepArgs A = sweep_args(h, (float *)h->f[h->cur ^ 1]);
+      A.records = (k == nsteps - 1) ? 1 : 0;
       cudaError_t e = lbk::launch_sweep(h->store, h->tmap[h->cur][0], h->tmap[h->cur][1], A, h->sweep_smem, h->st);
       if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: sweep kernel");
       h->cur ^= 1;
@@ -818,8 +822,8 @@ int batch_graph(lb_batch *b) {
   if (b->graph) return LB_OK;
   cudaGraph_t g = nullptr;
   LB_BCUDA(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e1 = lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 0, b->smem, b->cap);
-  cudaError_t e2 = lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 1, b->smem, b->cap);
+  cudaError_t e1 = lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 0, 0, b->smem, b->cap);
+  cudaError_t e2 = lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 1, 1, b->smem, b->cap);
   cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -904,7 +908,7 @@ int lb_batch_step(lb_batch *b, int64_t nsteps) {
   }
   int64_t k = 0;
   if (b->kpar == 1) {  // one plain step to reach kpar 0
-    LB_BCUDA(b, lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 1, b->smem, b->st));
+    LB_BCUDA(b, lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 1, 1, b->smem, b->st));
     b->kpar = 0;
     k = 1;
   }
@@ -914,7 +918,7 @@ int lb_batch_step(lb_batch *b, int64_t nsteps) {
     for (; k + 2 <= nsteps; k += 2) LB_BCUDA(b, cudaGraphLaunch(b->graph, b->st));
   }
   if (k < nsteps) {
-    LB_BCUDA(b, lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 0, b->smem, b->st));
+    LB_BCUDA(b, lbk::launch_sweep_batch(b->store, b->d_items, b->nitems, b->d_args, b->d_maps, 0, 1, b->smem, b->st));
     b->kpar = 1;
     k++;
   }

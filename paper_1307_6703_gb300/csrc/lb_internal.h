@@ -30,6 +30,7 @@ struct SweepArgs {
   float *fout;
   void *fdev;
   double *partials;            // 4 doubles per CTA: mass, J_x, J_y, bad-site flag
+  int records;                 // write the per-CTA records (0: skip them)
   int *err;                    // set when a bounded wait gave up
 };
 
@@ -65,7 +66,7 @@ struct BatchItem {
 // maps: 4 per instance ([input buffer][map], map 1 = deviation planes of
 // 16-bit storage or a copy of map 0), 64-byte aligned device memory.
 cudaError_t launch_sweep_batch(int store, const BatchItem *items, int nitems, const SweepArgs *args,
-                               const CUtensorMap *maps, int kpar, size_t smem, cudaStream_t st);
+                               const CUtensorMap *maps, int kpar, int records, size_t smem, cudaStream_t st);
 // Copy the periodic images into the ghost band of `nplanes` planes of
 // `elem_bytes`-byte elements (4 or 2).
 cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,

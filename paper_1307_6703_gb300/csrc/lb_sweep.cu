@@ -138,10 +138,8 @@ struct __align__(128) SweepSmem {
   // four pairs: stage A of iteration k+1 writes pair k+1 while stage D of
   // iteration k (no barrier in between) may still read pairs k-2 and k-1
   float n[4][2][kCols];
-  float P[2][2][kCols];
-  float L[2][2][kCols];
-  float Jx[2][2][kCols];
-  float Jy[2][2][kCols];
+  float2 PL[2][2][kCols];  // (P, lap n): one 64-bit load per stencil tap
+  float2 J[2][2][kCols];   // (n u*_x, n u*_y)
   unsigned long long full[kPairs];
   static_assert(SlotBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
   static_assert(kPairs * SlotBytes >= (int)sizeof(double) * 4 * kThreads,
@@ -213,6 +211,18 @@ __device__ __forceinline__ float slap(const Sten &s, const float *r0, const floa
          s.R * ((r2[t + 1] + r2[t - 1]) + (r0[t + 1] + r0[t - 1])) - s.four_QR * r1[t];
 }
 
+// x- and y-derivative stencils applied to both components of float2 rows.
+__device__ __forceinline__ float2 sdx2(const Sten &s, const float2 *r0, const float2 *r1, const float2 *r2, int t) {
+  const float2 a = r1[t + 1], b = r1[t - 1], c = r2[t + 1], d = r2[t - 1], e = r0[t + 1], f = r0[t - 1];
+  return make_float2(s.N * (a.x - b.x) + s.M * ((c.x - d.x) + (e.x - f.x)),
+                     s.N * (a.y - b.y) + s.M * ((c.y - d.y) + (e.y - f.y)));
+}
+__device__ __forceinline__ float2 sdy2(const Sten &s, const float2 *r0, const float2 *r2, int t) {
+  const float2 g = r2[t], h = r0[t], c = r2[t + 1], e = r0[t + 1], d = r2[t - 1], f = r0[t - 1];
+  return make_float2(s.N * (g.x - h.x) + s.M * ((c.x - e.x) + (d.x - f.x)),
+                     s.N * (g.y - h.y) + s.M * ((c.y - e.y) + (d.y - f.y)));
+}
+
 // Propagated populations of the site in column t of row r1 (pull).
 template <class St>
 __device__ __forceinline__ void pull(const typename St::Row &r0, const typename St::Row &r1,
@@ -263,7 +273,7 @@ __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, floa
 // of 16-bit storage) describe; the CTA's mass/momentum record goes to rec.
 template <class St>
 __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
-                                           const int strip, const int seg, double *rec) {
+                                           const int strip, const int seg, double *rec, const bool records) {
   using Row = typename St::Row;
   using Smem = SweepSmem<St::kSlotBytes>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -373,8 +383,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             const float c = r1[t];
             const float nT = c * A.T;
             const float pw = nT * __fdividef(1.0f, 1.0f - A.b * c) - A.a * c * c;
-            S.P[s2][j][t] = nT - pw;
-            S.L[s2][j][t] = slap(st, r0, r1, r2, t);
+            S.PL[s2][j][t] = make_float2(nT - pw, slap(st, r0, r1, r2, t));
           }
         }
       }
@@ -383,20 +392,19 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       // -------------------------------------- C: rows a-2, a-1 -- F, n u*
       float Fx_cur[2] = {0.f, 0.f}, Fy_cur[2] = {0.f, 0.f};
       {
-        const float *P0 = S.P[s2m1][0], *P1 = S.P[s2m1][1], *P2 = S.P[s2][0], *P3 = S.P[s2][1];
-        const float *L0 = S.L[s2m1][0], *L1 = S.L[s2m1][1], *L2 = S.L[s2][0], *L3 = S.L[s2][1];
+        const float2 *P0 = S.PL[s2m1][0], *P1 = S.PL[s2m1][1], *P2 = S.PL[s2][0], *P3 = S.PL[s2][1];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 2 + j;
           if (!(actC && (kSteady || (y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1)))))) continue;
-          const float *p0 = j ? P1 : P0, *p1 = j ? P2 : P1, *p2 = j ? P3 : P2;
-          const float *l0 = j ? L1 : L0, *l1 = j ? L2 : L1, *l2 = j ? L3 : L2;
-          if (!kSteady && walls && y == 0) { p0 = p2; l0 = l2; }
-          if (!kSteady && walls && y == ny - 1) { p2 = p0; l2 = l0; }
+          const float2 *p0 = j ? P1 : P0, *p1 = j ? P2 : P1, *p2 = j ? P3 : P2;
+          if (!kSteady && walls && y == 0) p0 = p2;
+          if (!kSteady && walls && y == ny - 1) p2 = p0;
           const float n = S.n[s3m1][j][t];
           const float kn = A.kappa * n;
-          const float Fx = (sdx(st, p0, p1, p2, t) + kn * sdx(st, l0, l1, l2, t)) + A.A0 * sinx;
-          const float Fy = sdy(st, p0, p2, t) + kn * sdy(st, l0, l2, t);
+          const float2 dx = sdx2(st, p0, p1, p2, t), dy = sdy2(st, p0, p2, t);
+          const float Fx = (dx.x + kn * dx.y) + A.A0 * sinx;
+          const float Fy = dy.x + kn * dy.y;
           float sx = sxa[j], sy = sya[j];
           if (!kSteady && walls && (y == 0 || y == ny - 1)) {
             // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
@@ -409,8 +417,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
             sy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
           }
-          S.Jx[s2][j][t] = sx + 0.5f * Fx;
-          S.Jy[s2][j][t] = sy + 0.5f * Fy;
+          S.J[s2][j][t] = make_float2(sx + 0.5f * Fx, sy + 0.5f * Fy);
           Fx_cur[j] = Fx;
           Fy_cur[j] = Fy;
         }
@@ -422,8 +429,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       // -------------------------------------- D: rows a-3, a-2 -- collide, store
       {
         const float *n0 = S.n[s3m2][0], *n1 = S.n[s3m2][1], *n2 = S.n[s3m1][0], *n3 = S.n[s3m1][1];
-        const float *X0 = S.Jx[s2m1][0], *X1 = S.Jx[s2m1][1], *X2 = S.Jx[s2][0], *X3 = S.Jx[s2][1];
-        const float *Y0 = S.Jy[s2m1][0], *Y1 = S.Jy[s2m1][1], *Y2 = S.Jy[s2][0], *Y3 = S.Jy[s2][1];
+        const float2 *J0 = S.J[s2m1][0], *J1 = S.J[s2m1][1], *J2 = S.J[s2][0], *J3 = S.J[s2][1];
         // population rows a-4 .. a-1: pair k-2 row 1, pair k-1 rows 0, 1, pair k row 0
         const Row q0p = St::row(S.pops[s5m2], 1), q1p = St::row(S.pops[s5m1], 0);
         const Row q2p = St::row(S.pops[s5m1], 1), q3p = St::row(S.pops[s5], 0);
@@ -432,25 +438,27 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           const int y = a - 3 + j;
           if (!(actD && (kSteady || (y >= ya && y < yb)))) continue;
           const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
-          const float *x0p = j ? X1 : X0, *x1p = j ? X2 : X1, *x2p = j ? X3 : X2;
-          const float *y0p = j ? Y1 : Y0, *y1p = j ? Y2 : Y1, *y2p = j ? Y3 : Y2;
+          const float2 *j0p = j ? J1 : J0, *j1p = j ? J2 : J1, *j2p = j ? J3 : J2;
           const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
           const bool bot = !kSteady && walls && y == 0, top = !kSteady && walls && y == ny - 1;
-          float dJy;
+          float dJy, dJx;
           if (bot || top) {
             // mirror rows across the wall: n and J_x even, J_y odd
             float sgm = 1.f, sgp = 1.f;
-            if (bot) { m0 = m2; x0p = x2p; y0p = y2p; sgm = -1.f; }
-            if (top) { m2 = m0; x2p = x0p; y2p = y0p; sgp = -1.f; }
-            dJy = st.N * (sgp * y2p[t] - sgm * y0p[t]) +
-                  st.M * ((sgp * y2p[t + 1] - sgm * y0p[t + 1]) + (sgp * y2p[t - 1] - sgm * y0p[t - 1]));
+            if (bot) { m0 = m2; j0p = j2p; sgm = -1.f; }
+            if (top) { m2 = m0; j2p = j0p; sgp = -1.f; }
+            const float2 g = j2p[t], h = j0p[t], c = j2p[t + 1], e = j0p[t + 1], d = j2p[t - 1], f = j0p[t - 1];
+            dJy = st.N * (sgp * g.y - sgm * h.y) + st.M * ((sgp * c.y - sgm * e.y) + (sgp * d.y - sgm * f.y));
+            dJx = sdx2(st, j0p, j1p, j2p, t).x;
           } else {
-            dJy = sdy(st, y0p, y2p, t);
+            dJx = sdx2(st, j0p, j1p, j2p, t).x;
+            dJy = sdy2(st, j0p, j2p, t).y;
           }
           const float n = m1[t];
           const float dnx = sdx(st, m0, m1, m2, t), dny = sdy(st, m0, m2, t);
-          const float divJ = sdx(st, x0p, x1p, x2p, t) + dJy;
-          const float Jx = x1p[t], Jy = y1p[t];
+          const float divJ = dJx + dJy;
+          const float2 Jc = j1p[t];
+          const float Jx = Jc.x, Jy = Jc.y;
           float f[9], fs[9];
           pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f, A);
           if (bot || top) wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
@@ -512,14 +520,16 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           }
           // Mass and momentum of the stored site: sum f* = n (by
           // construction), sum f* c = n u* + F/2 (identity of the collision).
-          if (!(n > 0.f && n < A.nmax && fabsf(Jx) + fabsf(Jy) < 3.0e38f)) bad = 1;
-          acc_m += n;
-          if constexpr (!St::kDev) {
-            acc_x += Jx + 0.5f * Fx;
-            acc_y += Jy + 0.5f * Fy;
-          } else {  // momentum of the stored (rounded) populations
-            acc_x += ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
-            acc_y += ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
+          if (records) {
+            if (!(n > 0.f && n < A.nmax && fabsf(Jx) + fabsf(Jy) < 3.0e38f)) bad = 1;
+            acc_m += n;
+            if constexpr (!St::kDev) {
+              acc_x += Jx + 0.5f * Fx;
+              acc_y += Jy + 0.5f * Fy;
+            } else {  // momentum of the stored (rounded) populations
+              acc_x += ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
+              acc_y += ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
+            }
           }
         }
       }
@@ -540,8 +550,10 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       iteration(k, std::false_type{});
   }
 
-  // CTA partial sums of the stored state (FP64, fixed order).  Every TMA
-  // copy has been waited for, so the population ring is free for them.
+  // CTA partial sums of the stored state (FP64, fixed order), when asked
+  // for.  Every TMA copy has been waited for, so the population ring is
+  // free for them.
+  if (!records) return;
   double *red = reinterpret_cast<double *>(&S.pops[0][0]);
   __syncthreads();
   red[0 * kThreads + t] = (double)acc_m;
@@ -577,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, St::kMinBlocks)
 sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tdev,
                   const SweepArgs A) {
   sweep_body<St>(&tin, &tdev, A, blockIdx.x, blockIdx.y,
-                 A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x));
+                 A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), A.records != 0);
 }
 
 // Batched step: CTA b works on items[b] (instance, strip, segment) of a
@@ -587,7 +599,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant
 template <class St>
 __global__ void __launch_bounds__(kThreads, St::kMinBlocks)
 sweep_batch_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restrict__ args,
-                   const CUtensorMap *__restrict__ maps, int kpar) {
+                   const CUtensorMap *__restrict__ maps, int kpar, int records) {
   __shared__ SweepArgs A;
   const BatchItem it = items[blockIdx.x];
   const int par = it.par0 ^ kpar;
@@ -599,7 +611,7 @@ sweep_batch_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restr
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m + 1) : "memory");
   }
   __syncthreads();
-  sweep_body<St>(m, m + 1, A, it.strip, it.seg, A.partials + 4 * (size_t)it.rec);
+  sweep_body<St>(m, m + 1, A, it.strip, it.seg, A.partials + 4 * (size_t)it.rec, records != 0);
 }
 
 // Copy the periodic images into the ghost band of nplanes padded planes.
@@ -708,8 +720,8 @@ cudaError_t prepare_one(size_t *smem_bytes) {
 
 template <class St>
 cudaError_t launch_batch_one(const BatchItem *items, int nitems, const SweepArgs *args, const CUtensorMap *maps,
-                             int kpar, size_t smem, cudaStream_t st) {
-  sweep_batch_kernel<St><<<nitems, kThreads, smem, st>>>(items, args, maps, kpar);
+                             int kpar, int records, size_t smem, cudaStream_t st) {
+  sweep_batch_kernel<St><<<nitems, kThreads, smem, st>>>(items, args, maps, kpar, records);
   return cudaGetLastError();
 }
 
@@ -782,12 +794,12 @@ cudaError_t launch_sweep(int store, const CUtensorMap &m0, const CUtensorMap &m1
 }
 
 cudaError_t launch_sweep_batch(int store, const BatchItem *items, int nitems, const SweepArgs *args,
-                               const CUtensorMap *maps, int kpar, size_t smem, cudaStream_t st) {
+                               const CUtensorMap *maps, int kpar, int records, size_t smem, cudaStream_t st) {
   if (nitems < 1) return cudaSuccess;
   switch (store) {
-    case kStoreF32: return launch_batch_one<StoreF32>(items, nitems, args, maps, kpar, smem, st);
-    case kStoreBF16: return launch_batch_one<StoreBF16>(items, nitems, args, maps, kpar, smem, st);
-    case kStoreFP16: return launch_batch_one<StoreFP16>(items, nitems, args, maps, kpar, smem, st);
+    case kStoreF32: return launch_batch_one<StoreF32>(items, nitems, args, maps, kpar, records, smem, st);
+    case kStoreBF16: return launch_batch_one<StoreBF16>(items, nitems, args, maps, kpar, records, smem, st);
+    case kStoreFP16: return launch_batch_one<StoreFP16>(items, nitems, args, maps, kpar, records, smem, st);
   }
   return cudaErrorInvalidValue;
 }
