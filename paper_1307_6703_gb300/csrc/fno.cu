@@ -78,6 +78,13 @@ __device__ double block_sum(double v, double *sm) {
 
 unsigned blocks_for(long long n) { return (unsigned)std::min<long long>((n + kThreads - 1) / kThreads, 8192); }
 
+// 2D grid: y = rows (one per field and channel), x = enough blocks for S sites
+// with a total of about 8192 blocks.
+dim3 grid2(long long S, int rows) {
+  const long long per_row = std::max<long long>(1, 8192 / std::max(rows, 1));
+  return dim3((unsigned)std::min<long long>((S + kThreads - 1) / kThreads, per_row), (unsigned)rows);
+}
+
 // ------------------------------------------------------------------ kernels
 
 // Input features of each field from its parameters (U_w, A0, lambda, T_r).
@@ -100,34 +107,36 @@ __global__ void features_kernel(const float *__restrict__ prm, int B, int nx, in
   }
 }
 
+// Elementwise kernels run on 2D grids: y = one (field, channel) row of S
+// sites, x = sites, so no per-element index division is needed.
 // v0[b, o, s] = sum_c P[o, c] x0[b, c, s] + p[o]
 __global__ void lift_kernel(const float *__restrict__ x0, const float *__restrict__ P, const float *__restrict__ pb,
-                            int B, int C, long long S, float *__restrict__ v, __nv_bfloat16 *__restrict__ vb) {
-  const long long total = (long long)B * C * S;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long s = i % S;
-    const int o = (int)((i / S) % C), b = (int)(i / (S * C));
-    const float *xb = x0 + (long long)b * kFeatures * S + s;
+                            int C, long long S, float *__restrict__ v, __nv_bfloat16 *__restrict__ vb) {
+  const int row = blockIdx.y, b = row / C, o = row - b * C;
+  const float *xb = x0 + (long long)b * kFeatures * S;
+  float *vr = v + (long long)row * S;
+  __nv_bfloat16 *vbr = vb + (long long)row * S;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x) {
     float acc = pb[o];
 #pragma unroll
-    for (int c = 0; c < kFeatures; c++) acc += P[o * kFeatures + c] * xb[c * S];
-    v[i] = acc;
-    vb[i] = __float2bfloat16_rn(acc);
+    for (int c = 0; c < kFeatures; c++) acc += P[o * kFeatures + c] * xb[c * S + s];
+    vr[s] = acc;
+    vbr[s] = __float2bfloat16_rn(acc);
   }
 }
 
 // y-transform of the x-transformed lines: A[bc][y][j] (j < mx real part,
 // j >= mx imaginary part of mode j - mx) -> Sh[bc][ky][kx][2].
-__global__ void ydft_kernel(const float *__restrict__ A, int ny, int mx, int my, float *__restrict__ Sh) {
+__global__ void ydft_kernel(const float *__restrict__ A, const float2 *__restrict__ Ty, int ny, int mx, int my,
+                            float *__restrict__ Sh) {
   const int bc = blockIdx.x;
   const float *a = A + (long long)bc * ny * 2 * mx;
   for (int t = threadIdx.x; t < my * mx; t += blockDim.x) {
     const int k = t / mx, kx = t - k * mx;
-    const int ky = ymode(k, my);
     float sr = 0.f, si = 0.f;
     for (int y = 0; y < ny; y++) {
-      float sn, cs;
-      sincospif(2.0f * (float)(ky * y) / (float)ny, &sn, &cs);
+      const float2 tw = Ty[k * ny + y];
+      const float cs = tw.x, sn = tw.y;
       const float ar = a[y * 2 * mx + kx], ai = a[y * 2 * mx + mx + kx];
       sr += ar * cs + ai * sn;
       si += ai * cs - ar * sn;
@@ -142,7 +151,8 @@ __global__ void ydft_kernel(const float *__restrict__ A, int ny, int mx, int my,
 // Y[o, ky] = sum_c S[c, ky] R[ky, kx, c, o];  G[o][y][kx] = sum_ky Y e^{+i theta}.
 // One block per (kx, b); shared memory: Y[C][my][2].
 __global__ void mix_iy_kernel(const float *__restrict__ Sh, const float *__restrict__ Rr, const float *__restrict__ Ri,
-                              int C, int ny, int mx, int my, float *__restrict__ G, __nv_bfloat16 *__restrict__ Gb) {
+                              const float2 *__restrict__ Ty, int C, int ny, int mx, int my, float *__restrict__ G,
+                              __nv_bfloat16 *__restrict__ Gb) {
   extern __shared__ float ysm[];
   const int kx = blockIdx.x, b = blockIdx.y;
   for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
@@ -163,8 +173,8 @@ __global__ void mix_iy_kernel(const float *__restrict__ Sh, const float *__restr
     const int o = t / ny, y = t - o * ny;
     float gr = 0.f, gi = 0.f;
     for (int k = 0; k < my; k++) {
-      float sn, cs;
-      sincospif(2.0f * (float)(ymode(k, my) * y) / (float)ny, &sn, &cs);
+      const float2 tw = Ty[k * ny + y];
+      const float cs = tw.x, sn = tw.y;
       const float yr = ysm[(o * my + k) * 2], yi = ysm[(o * my + k) * 2 + 1];
       gr += yr * cs - yi * sn;
       gi += yr * sn + yi * cs;
@@ -178,11 +188,13 @@ __global__ void mix_iy_kernel(const float *__restrict__ Sh, const float *__restr
 }
 
 // z += w (per channel); v' = gelu(z) (or z for the last layer).
-__global__ void bias_act_kernel(float *__restrict__ z, const float *__restrict__ w, int C, long long S, long long total,
-                                int act, float *__restrict__ v, __nv_bfloat16 *__restrict__ vb) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const int o = (int)((i / S) % C);
-    const float zz = z[i] + w[o];
+__global__ void bias_act_kernel(float *__restrict__ z, const float *__restrict__ w, int C, long long S, int act,
+                                float *__restrict__ v, __nv_bfloat16 *__restrict__ vb) {
+  const int row = blockIdx.y, o = row % C;
+  const float wo = w[o];
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x) {
+    const long long i = (long long)row * S + s;
+    const float zz = z[i] + wo;
     z[i] = zz;
     const float vv = act ? gelu(zz) : zz;
     v[i] = vv;
@@ -194,12 +206,10 @@ constexpr int kMaxOutputs = 4;
 
 // hp += q1 (kept); out[b, j, s] = sum_h Q2[j, h] gelu(hp[b, h, s]) + q2[j].
 __global__ void project_kernel(float *__restrict__ hp, const float *__restrict__ q1, const float *__restrict__ Q2,
-                               const float *__restrict__ q2, int B, int H, int O, long long S, float *__restrict__ out,
+                               const float *__restrict__ q2, int H, int O, long long S, float *__restrict__ out,
                                float *__restrict__ out_user) {
-  const long long total = (long long)B * S;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(i / S);
-    const long long s = i - (long long)b * S;
+  const int b = blockIdx.y;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x) {
     float *h = hp + (long long)b * H * S + s;
     float acc[kMaxOutputs];
 #pragma unroll
@@ -245,11 +255,11 @@ __global__ void finish_loss_kernel(const double *__restrict__ partial, int n, lo
 
 // dhp[b, h, s] = sum_j Q2[j, h] dout[b, j, s] gelu'(hp[b, h, s])
 __global__ void project_back_kernel(const float *__restrict__ hp, const float *__restrict__ Q2,
-                                    const float *__restrict__ dout, int H, int O, long long S, long long total,
+                                    const float *__restrict__ dout, int H, int O, long long S,
                                     float *__restrict__ dhp, __nv_bfloat16 *__restrict__ dhpb) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long s = i % S;
-    const int k = (int)((i / S) % H), b = (int)(i / (S * H));
+  const int row = blockIdx.y, b = row / H, k = row - b * H;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < S; s += (long long)gridDim.x * blockDim.x) {
+    const long long i = (long long)row * S + s;
     float acc = 0.f;
     for (int j = 0; j < O; j++) acc += Q2[j * H + k] * dout[((long long)b * O + j) * S + s];
     const float d = acc * gelu_grad(hp[i]);
@@ -258,43 +268,54 @@ __global__ void project_back_kernel(const float *__restrict__ hp, const float *_
   }
 }
 
-// Per-channel sums over (b, s): out[ch] = sum a[b, ch, s] (* f(other)),
-// one block per channel.  mode 0: plain sum; 1: a * gelu(other[b, ch, s]);
-// 2: a[b, ch, s] * other[b, ch2, s] for the lift weights (ch = o * 5 + c2).
-__global__ void chan_sum_kernel(const float *__restrict__ a, const float *__restrict__ other, int mode, int B, int C,
-                                int C2, long long S, float *__restrict__ out) {
+// Two-pass per-channel sums over (b, s), deterministic: pass 1 gives each
+// of nb blocks per channel a contiguous share (FP32 per thread, FP64 block
+// tree), pass 2 adds the nb partials of a channel in order.
+//   kind 0: sum a[b, ch, s]                        (a has C channels)
+//   kind 1: sum a[b, j, s] gelu(o2[b, k, s])       (ch = j*C2 + k; a has C, o2 has C2 channels)
+//   kind 2: sum a[b, o, s] o2[b, c, s]             (ch = o*C2 + c; a has C, o2 has C2 channels)
+constexpr int kReduceBlocks = 32;
+__global__ void reduce_pass1_kernel(int kind, const float *__restrict__ a, const float *__restrict__ o2, int B, int C,
+                                    int C2, long long S, double *__restrict__ part) {
   __shared__ double sm[kThreads];
-  const int ch = blockIdx.x;
-  const int o = mode == 2 ? ch / C2 : ch, c2 = mode == 2 ? ch % C2 : 0;
-  double acc = 0.0;
-  const long long n = (long long)B * S;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const int b = (int)(i / S);
-    const long long s = i - (long long)b * S;
-    const float av = a[((long long)b * C + o) * S + s];
-    float v = av;
-    if (mode == 1) v = av * gelu(other[((long long)b * C + o) * S + s]);
-    if (mode == 2) v = av * other[((long long)b * C2 + c2) * S + s];
-    acc += (double)v;
+  const int ch = blockIdx.x, blk = blockIdx.y;
+  const int ca = kind == 0 ? ch : ch / C2, cb = kind == 0 ? 0 : ch % C2;
+  const long long n = (long long)B * S, per = (n + gridDim.y - 1) / gridDim.y;
+  const long long lo = blk * per, hi = min(n, lo + per);
+  float acc = 0.f;
+  long long i = lo + threadIdx.x;
+  int b = (int)(i / S);
+  long long s = i - (long long)b * S;
+  for (; i < hi; i += blockDim.x) {
+    while (s >= S) {  // advance (b, s) without dividing
+      s -= S;
+      b++;
+    }
+    const float av = a[((long long)b * C + ca) * S + s];
+    if (kind == 0) acc += av;
+    else if (kind == 1) acc += av * gelu(o2[((long long)b * C2 + cb) * S + s]);
+    else acc += av * o2[((long long)b * C2 + cb) * S + s];
+    s += blockDim.x;
   }
-  const double r = block_sum(acc, sm);
-  if (threadIdx.x == 0) out[ch] = (float)r;
+  const double r = block_sum((double)acc, sm);
+  if (threadIdx.x == 0) part[(long long)ch * gridDim.y + blk] = r;
 }
 
-// dQ2[j, k] = sum_{b, s} dout[b, j, s] gelu(hp[b, k, s]); one block per (j, k).
-__global__ void dQ2_kernel(const float *__restrict__ dout, const float *__restrict__ hp, int B, int H, int O,
-                           long long S, float *__restrict__ out) {
-  __shared__ double sm[kThreads];
-  const int j = blockIdx.x / H, k = blockIdx.x - j * H;
+__global__ void reduce_pass2_kernel(const double *__restrict__ part, int nch, int nb, float *__restrict__ out) {
+  const int ch = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ch >= nch) return;
   double acc = 0.0;
-  const long long n = (long long)B * S;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const int b = (int)(i / S);
-    const long long s = i - (long long)b * S;
-    acc += (double)(dout[((long long)b * O + j) * S + s] * gelu(hp[((long long)b * H + k) * S + s]));
+  for (int i = 0; i < nb; i++) acc += part[(long long)ch * nb + i];
+  out[ch] = (float)acc;
+}
+
+// out[i] = sum_b part[b][i], in order (weight gradients of the per-field GEMMs).
+__global__ void sum_fields_kernel(const float *__restrict__ part, int B, int n, float *__restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < B; b++) acc += part[(long long)b * n + i];
+    out[i] = acc;
   }
-  const double r = block_sum(acc, sm);
-  if (threadIdx.x == 0) out[blockIdx.x] = (float)r;
 }
 
 // dz = dv * gelu'(z) (or dv for the last layer), with a BF16 copy.
@@ -311,17 +332,17 @@ __global__ void act_back_kernel(const float *__restrict__ dv, const float *__res
 // inputs): dY[o, ky] = sum_y dG e^{-i theta} (adjoint form), dS[c, ky] =
 // sum_o (R^H-like products).  One block per (kx, b); dY kept for dR.
 __global__ void mix_iy_back_kernel(const float *__restrict__ dG, const float *__restrict__ Rr, const float *__restrict__ Ri,
-                                   int C, int ny, int mx, int my, float *__restrict__ dY, float *__restrict__ dS) {
+                                   const float2 *__restrict__ Ty, int C, int ny, int mx, int my, float *__restrict__ dY,
+                                   float *__restrict__ dS) {
   extern __shared__ float ysm[];
   const int kx = blockIdx.x, b = blockIdx.y;
   for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
     const int o = t / my, k = t - o * my;
-    const int ky = ymode(k, my);
     const float *g = dG + (((long long)b * C + o) * ny) * 2 * mx;
     float yr = 0.f, yi = 0.f;
     for (int y = 0; y < ny; y++) {
-      float sn, cs;
-      sincospif(2.0f * (float)(ky * y) / (float)ny, &sn, &cs);
+      const float2 tw = Ty[k * ny + y];
+      const float cs = tw.x, sn = tw.y;
       const float gr = g[y * 2 * mx + kx], gi = g[y * 2 * mx + mx + kx];
       yr += gr * cs + gi * sn;
       yi += -gr * sn + gi * cs;
@@ -369,16 +390,16 @@ __global__ void dR_kernel(const float *__restrict__ Sh, const float *__restrict_
 }
 
 // Adjoint of the y-transform: dA[bc][y][kx] (re / im parts) from dS.
-__global__ void ydft_back_kernel(const float *__restrict__ dS, int ny, int mx, int my, float *__restrict__ dA,
-                                 __nv_bfloat16 *__restrict__ dAb) {
+__global__ void ydft_back_kernel(const float *__restrict__ dS, const float2 *__restrict__ Ty, int ny, int mx, int my,
+                                 float *__restrict__ dA, __nv_bfloat16 *__restrict__ dAb) {
   const int bc = blockIdx.x;
   const float *d = dS + (long long)bc * my * mx * 2;
   for (int t = threadIdx.x; t < ny * mx; t += blockDim.x) {
     const int y = t / mx, kx = t - y * mx;
     float ar = 0.f, ai = 0.f;
     for (int k = 0; k < my; k++) {
-      float sn, cs;
-      sincospif(2.0f * (float)(ymode(k, my) * y) / (float)ny, &sn, &cs);
+      const float2 tw = Ty[k * ny + y];
+      const float cs = tw.x, sn = tw.y;
       const float sr = d[(k * mx + kx) * 2], si = d[(k * mx + kx) * 2 + 1];
       ar += sr * cs - si * sn;
       ai += sr * sn + si * cs;
@@ -393,8 +414,16 @@ __global__ void ydft_back_kernel(const float *__restrict__ dS, int ny, int mx, i
 
 // Truncated DFT matrices for nx: Fx[x][j] (forward, e^{-i phi}) and
 // Fxi[j][x] (real inverse with c_kx and 1/(nx ny)).
-__global__ void dft_tables_kernel(int nx, int ny, int mx, float *Fx, float *Fxi, __nv_bfloat16 *Fxb,
-                                  __nv_bfloat16 *Fxib) {
+__global__ void dft_tables_kernel(int nx, int ny, int mx, int my, float *Fx, float *Fxi, __nv_bfloat16 *Fxb,
+                                  __nv_bfloat16 *Fxib, float2 *Ty) {
+  // y twiddles: Ty[k][y] = (cos, sin)(2 pi ky y / ny), argument reduced mod ny
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < my * ny; i += gridDim.x * blockDim.x) {
+    const int k = i / ny, y = i - k * ny;
+    const int r = ((ymode(k, my) * y) % ny + ny) % ny;
+    float sn, cs;
+    sincospif(2.0f * (float)r / (float)ny, &sn, &cs);
+    Ty[i] = make_float2(cs, sn);
+  }
   const int n = nx * mx;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int x = i / mx, k = i - x * mx;
@@ -451,9 +480,11 @@ struct fno_handle {
   float *dout = nullptr, *dhp = nullptr, *dV = nullptr, *dZ = nullptr, *dG = nullptr, *dA = nullptr, *dY = nullptr,
         *dS = nullptr;
   __nv_bfloat16 *dhpb = nullptr, *dZb = nullptr, *dAb = nullptr;
-  double *partial = nullptr, *loss = nullptr;
+  double *partial = nullptr, *loss = nullptr, *rpart = nullptr;
+  float *wpart = nullptr;  // per-field weight gradients [B][max(C, H) * C]
   float *Fx = nullptr, *Fxi = nullptr;
   __nv_bfloat16 *Fxb = nullptr, *Fxib = nullptr;
+  float2 *Ty = nullptr;
   int tab_nx = 0, tab_ny = 0;
   int B = 0, nx = 0, ny = 0;  // shape of the last forward pass
   bool have_forward = false;
@@ -499,6 +530,13 @@ cublasStatus_t gemm(fno_handle *h, bool tA, bool tB, int m, int n, int k, const 
                                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
 }
 
+// out[ch] for nch channels of a per-channel sum (kinds: reduce_pass1_kernel).
+void chan_reduce(fno_handle *h, int kind, const float *a, const float *o2, int B, int C, int C2, long long S, int nch,
+                 float *out) {
+  reduce_pass1_kernel<<<dim3(nch, kReduceBlocks), kThreads, 0, h->st>>>(kind, a, o2, B, C, C2, S, h->rpart);
+  reduce_pass2_kernel<<<(nch + kThreads - 1) / kThreads, kThreads, 0, h->st>>>(h->rpart, nch, kReduceBlocks, out);
+}
+
 template <typename T>
 cudaError_t alloc(T **p, long long n) {
   return cudaMalloc((void **)p, (size_t)std::max<long long>(n, 1) * sizeof(T));
@@ -506,7 +544,7 @@ cudaError_t alloc(T **p, long long n) {
 
 void free_workspace(fno_handle *h) {
   void *ps[] = {h->x0, h->A, h->G, h->Gb, h->hp, h->out, h->dout, h->dhp, h->dhpb, h->dV, h->dZ, h->dZb, h->dG,
-                h->dA, h->dAb, h->dY, h->dS, h->partial, h->loss, h->Fx, h->Fxi, h->Fxb, h->Fxib};
+                h->dA, h->dAb, h->dY, h->dS, h->partial, h->loss, h->Fx, h->Fxi, h->Fxb, h->Fxib, h->rpart, h->wpart, h->Ty};
   for (void *p : ps) cudaFree(p);
   for (int l = 0; l <= kMaxLayers; l++) {
     cudaFree(h->V[l]);
@@ -556,11 +594,16 @@ cudaError_t alloc_workspace(fno_handle *h) {
   if (e == cudaSuccess) e = alloc(&h->dY, h->cap_modes);
   if (e == cudaSuccess) e = alloc(&h->dS, h->cap_modes);
   if (e == cudaSuccess) e = alloc(&h->partial, 8192);
+  if (e == cudaSuccess)
+    e = alloc(&h->rpart, (long long)std::max(c.width * kFeatures, std::max(c.hidden * c.outputs, c.hidden)) * kReduceBlocks +
+                             (long long)c.width * kReduceBlocks);
+  if (e == cudaSuccess) e = alloc(&h->wpart, B * (long long)std::max(c.width, c.hidden) * c.width);
   if (e == cudaSuccess) e = alloc(&h->loss, 1);
   if (e == cudaSuccess) e = alloc(&h->Fx, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Fxi, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Fxb, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Fxib, (long long)c.nx_max * 2 * c.modes_x);
+  if (e == cudaSuccess) e = alloc(&h->Ty, (long long)c.ny_max * c.modes_y);
   return e;
 }
 
@@ -639,25 +682,26 @@ int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *p
   if (B < 1 || B > c.batch_max || nx > c.nx_max || ny > c.ny_max || nx < 2 * c.modes_x || ny < c.modes_y)
     return ffail(h, LB_ERR_ARG, "fno_forward: batch or lattice outside the workspace bounds");
   const int C = c.width, H = c.hidden, L = c.layers, mx = c.modes_x, my = c.modes_y;
-  const long long S = (long long)nx * ny, BCS = (long long)B * C * S;
+  const long long S = (long long)nx * ny;
   const int R = B * C * ny;
   cudaStream_t st = h->st;
   if (h->tab_nx != nx || h->tab_ny != ny) {
-    dft_tables_kernel<<<blocks_for((long long)nx * mx), kThreads, 0, st>>>(nx, ny, mx, h->Fx, h->Fxi, h->Fxb, h->Fxib);
+    dft_tables_kernel<<<blocks_for((long long)std::max(nx * mx, ny * my)), kThreads, 0, st>>>(
+        nx, ny, mx, my, h->Fx, h->Fxi, h->Fxb, h->Fxib, h->Ty);
     FNO_CUDA(h, cudaGetLastError());
     h->tab_nx = nx;
     h->tab_ny = ny;
   }
   const float *P = h->prm;
   features_kernel<<<blocks_for((long long)B * S), kThreads, 0, st>>>(params_dev, B, nx, ny, h->x0);
-  lift_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->x0, P + h->o.P, P + h->o.p, B, C, S, h->V[0], h->Vb[0]);
+  lift_kernel<<<grid2(S, B * C), kThreads, 0, st>>>(h->x0, P + h->o.P, P + h->o.p, C, S, h->V[0], h->Vb[0]);
   FNO_CUDA(h, cudaGetLastError());
   for (int l = 0; l < L; l++) {
     // x-transform of every line: A[R, 2mx] = V[R, nx] Fx[nx, 2mx]
     FNO_BLAS(h, gemm(h, false, false, R, 2 * mx, nx, h->V[l], h->Vb[l], nx, 0, h->Fx, h->Fxb, 2 * mx, 0, h->A, 2 * mx,
                      0, 1, 0.f));
-    ydft_kernel<<<B * C, kThreads, 0, st>>>(h->A, ny, mx, my, h->Sh[l]);
-    mix_iy_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->Sh[l], P + h->o.Rr[l], P + h->o.Ri[l],
+    ydft_kernel<<<B * C, kThreads, 0, st>>>(h->A, h->Ty, ny, mx, my, h->Sh[l]);
+    mix_iy_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->Sh[l], P + h->o.Rr[l], P + h->o.Ri[l], h->Ty,
                                                                           C, ny, mx, my, h->G, h->Gb);
     FNO_CUDA(h, cudaGetLastError());
     // inverse x-transform into z: Z[R, nx] = G[R, 2mx] Fxi[2mx, nx]
@@ -666,14 +710,14 @@ int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *p
     // z[b] += W v[b]  (one GEMM per field, strided)
     FNO_BLAS(h, gemm(h, false, false, C, (int)S, C, P + h->o.W[l], h->prmb + h->o.W[l], C, 0, h->V[l], h->Vb[l], (int)S,
                      (long long)C * S, h->Z[l], (int)S, (long long)C * S, B, 1.f));
-    bias_act_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->Z[l], P + h->o.w[l], C, S, BCS, l < L - 1 ? 1 : 0,
+    bias_act_kernel<<<grid2(S, B * C), kThreads, 0, st>>>(h->Z[l], P + h->o.w[l], C, S, l < L - 1 ? 1 : 0,
                                                            h->V[l + 1], h->Vb[l + 1]);
     FNO_CUDA(h, cudaGetLastError());
   }
   // projection: hp[b] = Q1 v_L[b]; out = Q2 gelu(hp + q1) + q2
   FNO_BLAS(h, gemm(h, false, false, H, (int)S, C, P + h->o.Q1, h->prmb + h->o.Q1, C, 0, h->V[L], h->Vb[L], (int)S,
                    (long long)C * S, h->hp, (int)S, (long long)H * S, B, 0.f));
-  project_kernel<<<blocks_for((long long)B * S), kThreads, 0, st>>>(h->hp, P + h->o.q1, P + h->o.Q2, P + h->o.q2, B, H,
+  project_kernel<<<grid2(S, B), kThreads, 0, st>>>(h->hp, P + h->o.q1, P + h->o.Q2, P + h->o.q2, H,
                                                                      c.outputs, S, h->out, out);
   FNO_CUDA(h, cudaGetLastError());
   h->B = B;
@@ -699,34 +743,32 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
   loss_kernel<<<lb, kThreads, 0, st>>>(h->out, target, BS, h->dout, h->partial);
   finish_loss_kernel<<<1, kThreads, 0, st>>>(h->partial, (int)lb, BS, h->loss);
   // projection: dq2, dQ2, dhp, dq1, dQ1, dV = Q1^T dhp
-  chan_sum_kernel<<<O, kThreads, 0, st>>>(h->dout, nullptr, 0, B, O, 1, S, g + o.q2);
-  dQ2_kernel<<<O * H, kThreads, 0, st>>>(h->dout, h->hp, B, H, O, S, g + o.Q2);
-  project_back_kernel<<<blocks_for((long long)B * H * S), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, O, S,
-                                                                             (long long)B * H * S, h->dhp, h->dhpb);
-  chan_sum_kernel<<<H, kThreads, 0, st>>>(h->dhp, nullptr, 0, B, H, 1, S, g + o.q1);
+  chan_reduce(h, 0, h->dout, nullptr, B, O, 1, S, O, g + o.q2);
+  chan_reduce(h, 1, h->dout, h->hp, B, O, H, S, O * H, g + o.Q2);
+  project_back_kernel<<<grid2(S, B * H), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, O, S, h->dhp, h->dhpb);
+  chan_reduce(h, 0, h->dhp, nullptr, B, H, 1, S, H, g + o.q1);
   FNO_CUDA(h, cudaGetLastError());
-  for (int b = 0; b < B; b++)
-    FNO_BLAS(h, gemm(h, false, true, H, C, (int)S, h->dhp + (long long)b * H * S, h->dhpb + (long long)b * H * S,
-                     (int)S, 0, h->V[L] + (long long)b * C * S, h->Vb[L] + (long long)b * C * S, (int)S, 0, g + o.Q1, C,
-                     0, 1, b ? 1.f : 0.f));
+  // dQ1 = sum_b dhp[b] v_L[b]^T: one batched GEMM into per-field parts, then their sum
+  FNO_BLAS(h, gemm(h, false, true, H, C, (int)S, h->dhp, h->dhpb, (int)S, (long long)H * S, h->V[L], h->Vb[L], (int)S,
+                   (long long)C * S, h->wpart, C, (long long)H * C, B, 0.f));
+  sum_fields_kernel<<<blocks_for((long long)H * C), kThreads, 0, st>>>(h->wpart, B, H * C, g + o.Q1);
   FNO_BLAS(h, gemm(h, true, false, C, (int)S, H, P + o.Q1, h->prmb + o.Q1, C, 0, h->dhp, h->dhpb, (int)S,
                    (long long)H * S, h->dV, (int)S, (long long)C * S, B, 0.f));
   for (int l = L - 1; l >= 0; l--) {
     act_back_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->dV, h->Z[l], BCS, l < L - 1 ? 1 : 0, h->dZ, h->dZb);
-    chan_sum_kernel<<<C, kThreads, 0, st>>>(h->dZ, nullptr, 0, B, C, 1, S, g + o.w[l]);
+    chan_reduce(h, 0, h->dZ, nullptr, B, C, 1, S, C, g + o.w[l]);
     FNO_CUDA(h, cudaGetLastError());
     // dW = sum_b dz[b] v[b]^T
-    for (int b = 0; b < B; b++)
-      FNO_BLAS(h, gemm(h, false, true, C, C, (int)S, h->dZ + (long long)b * C * S, h->dZb + (long long)b * C * S,
-                       (int)S, 0, h->V[l] + (long long)b * C * S, h->Vb[l] + (long long)b * C * S, (int)S, 0,
-                       g + o.W[l], C, 0, 1, b ? 1.f : 0.f));
+    FNO_BLAS(h, gemm(h, false, true, C, C, (int)S, h->dZ, h->dZb, (int)S, (long long)C * S, h->V[l], h->Vb[l], (int)S,
+                     (long long)C * S, h->wpart, C, (long long)C * C, B, 0.f));
+    sum_fields_kernel<<<blocks_for((long long)C * C), kThreads, 0, st>>>(h->wpart, B, C * C, g + o.W[l]);
     // spectral path: dG = dz Fxi^T, then the adjoints of the mixing and of the y-transform
     FNO_BLAS(h, gemm(h, false, true, R, 2 * mx, nx, h->dZ, h->dZb, nx, 0, h->Fxi, h->Fxib, nx, 0, h->dG, 2 * mx, 0, 1,
                      0.f));
-    mix_iy_back_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->dG, P + o.Rr[l], P + o.Ri[l], C, ny,
+    mix_iy_back_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->dG, P + o.Rr[l], P + o.Ri[l], h->Ty, C, ny,
                                                                                mx, my, h->dY, h->dS);
     dR_kernel<<<my * mx, kThreads, 0, st>>>(h->Sh[l], h->dY, B, C, mx, my, g + o.Rr[l], g + o.Ri[l]);
-    ydft_back_kernel<<<B * C, kThreads, 0, st>>>(h->dS, ny, mx, my, h->dA, h->dAb);
+    ydft_back_kernel<<<B * C, kThreads, 0, st>>>(h->dS, h->Ty, ny, mx, my, h->dA, h->dAb);
     FNO_CUDA(h, cudaGetLastError());
     // dv = W^T dz (pointwise path) + dA Fx^T (spectral path)
     FNO_BLAS(h, gemm(h, true, false, C, (int)S, C, P + o.W[l], h->prmb + o.W[l], C, 0, h->dZ, h->dZb, (int)S,
@@ -735,8 +777,8 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
                      1.f));
   }
   // lift: dp = sum dv0, dP[o, c] = sum dv0[b, o, s] x0[b, c, s]
-  chan_sum_kernel<<<C, kThreads, 0, st>>>(h->dV, nullptr, 0, B, C, 1, S, g + o.p);
-  chan_sum_kernel<<<C * kFeatures, kThreads, 0, st>>>(h->dV, h->x0, 2, B, C, kFeatures, S, g + o.P);
+  chan_reduce(h, 0, h->dV, nullptr, B, C, 1, S, C, g + o.p);
+  chan_reduce(h, 2, h->dV, h->x0, B, C, kFeatures, S, C * kFeatures, g + o.P);
   FNO_CUDA(h, cudaGetLastError());
   if (loss) {
     FNO_CUDA(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
