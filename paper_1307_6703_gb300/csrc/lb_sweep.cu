@@ -466,11 +466,13 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
+            // The new state is streamed out (evict-first stores): it is
+            // read again only by the next step.
             // Collision conserves the site's mass exactly (A = 0, sum f^eq =
             // n); the remainder form keeps rounded weights from biasing it.
             fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
 #pragma unroll
-            for (int q = 0; q < 9; ++q) o[q * plane] = fs[q];
+            for (int q = 0; q < 9; ++q) __stcs(o + q * plane, fs[q]);
             if (gx != 0) {
 #pragma unroll
               for (int q = 0; q < 9; ++q) o[q * plane + gx] = fs[q];
