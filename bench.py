@@ -316,6 +316,17 @@ def run_batch(args):
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # Each rank runs its own seeded ensemble (independent lattices: weak
+    # scaling, no data-path collective).
     ws = batch_workloads(args.batch_count, seed=7 + rank)
     sites = sum(w.nx * w.ny for w in ws)
     stream = torch.cuda.Stream()
@@ -332,12 +343,14 @@ def run_batch(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
+        barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
         lb_batch_step(batch.b, args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-    t_ms = ev0.elapsed_time(ev1)
+        barrier()
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
     unstable = [i for i, v in enumerate(batch) if v.reduce()[0] != 0]
     # The same lattices one by one: each stepped k_seq times alone (its own
     # lb_step launches), device times summed.
@@ -351,7 +364,12 @@ def run_batch(args):
         torch.cuda.synchronize()
         seq_ms += ev0.elapsed_time(ev1)
     batch.close()
-    value = sites * args.steps / (t_ms * 1e-3) / 1e6
+    total_sites = sites
+    if dist is not None:  # the ranks' ensembles differ in size
+        tsum = torch.tensor([float(sites)], device="cuda")
+        dist.all_reduce(tsum)
+        total_sites = int(tsum.item())
+    value = job_mlups(total_sites, args.steps, 1, t_ms)
     seq = sites * k_seq / (seq_ms * 1e-3) / 1e6
     peak, peak_kind = measured_peaks()
     achieved = b_alg * sites / (t_ms * 1e-3 / args.steps) / 1e9
@@ -370,11 +388,13 @@ def run_batch(args):
                          "peak_kind": peak_kind, "kernel": "lbk::sweep_batch_kernel",
                          "bytes_per_site": b_alg},
             "one_by_one": {"value": round(seq, 1), "unit": "MLUPS", "steps": k_seq,
-                           "launches_per_step": len(ws)},
+                           "launches_per_step": len(ws), "rank": 0},
             "clocks": clk.summary(),
             "gpu_launches": args.steps,
         }
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
