@@ -284,3 +284,53 @@ def test_autotune_keeps_the_trajectory(prec):
     assert ra[0] == rb[0] == 0 and abs(ra[1][0] - rb[1][0]) <= 1e-7 * ra[1][0]
     a.close()
     b.close()
+
+
+def test_zero_steps_is_a_no_op():
+    w = C2(0.05).with_(nx=96, ny=40)
+    s = solver_for(w, LB_FP32).init_noise(3, w.rho_mean, w.noise)
+    before = s.get_state()
+    s.step(0)
+    assert s.t == 0 and np.array_equal(before, s.get_state())
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [LB_FP64, LB_FP32])
+def test_uniform_rest_state_is_a_fixed_point(prec):
+    """Degenerate case: a uniform fluid at rest between walls at rest with no
+    potential stays uniform and at rest (gradients, forces and the wall rule
+    all vanish)."""
+    w = C2(0.0).with_(nx=128, ny=48, A0=0.0, lam=0.0)
+    s = solver_for(w, prec).init_fields(np.full((w.ny, w.nx), 0.8))
+    s.step(200)
+    n, ux, uy = s.moments()
+    tol = 1e-14 if prec == LB_FP64 else 2e-6
+    assert np.abs(n - 0.8).max() <= tol and np.abs(ux).max() <= tol and np.abs(uy).max() <= tol
+    s.close()
+
+
+def test_largest_sweep_lattice_matches_fp64():
+    """The largest lattice whose padded planes the sweep kernel indexes in
+    32 bits (9 * pitch * (ny + 8) < 2^31: 16384 x 13000, 213 M sites): three
+    FP32 sweep steps against the FP64 path (bit-identical to the oracle) on
+    every site, compared on the device."""
+    import torch
+    from paper_1307_6703_gb300 import LB_DTYPE_F32, LB_DTYPE_F64, lb_moments
+    w = C4.with_(nx=16384, ny=13000)
+    pitch = ((w.nx + 8 + 31) // 32) * 32
+    assert 9 * pitch * (w.ny + 8) < 2 ** 31
+    out = {}
+    for prec, dt, code in ((LB_FP64, torch.float64, LB_DTYPE_F64), (LB_FP32, torch.float32, LB_DTYPE_F32)):
+        s = solver_for(w, prec).init_noise(9, w.rho_mean, w.noise).step(3)
+        n = torch.empty((w.ny, w.nx), dtype=dt, device="cuda")
+        lb_moments(s.h, n, None, None, code, 1)
+        torch.cuda.synchronize()
+        rc, (m, _, _) = s.reduce()
+        assert rc == 0
+        out[prec] = (n, m)
+        s.close()
+    n64, m64 = out[LB_FP64]
+    n32, m32 = out[LB_FP32]
+    err = float(((n32.double() - n64).abs().max() / n64.abs().max()).item())
+    assert err <= 1e-6, err
+    assert abs(m32 - m64) / m64 <= 1e-6
