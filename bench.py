@@ -8,9 +8,10 @@ arithmetic).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|bf16dev|fp16dev]
+                  [--workload single|batch|warmstart|precision|network]
 
---impl reference times the FP64 CPU oracle (the reference arm of this build)
-on the host cores, each step a bounded row band of the same workload.
+--impl reference times the FP64 CPU oracle (the reference arm) on the host
+cores, each step a bounded row band of the same workload.
 Multi-GPU runs are independent replicas (the lattice is not sharded).
 """
 from __future__ import annotations
@@ -407,7 +408,7 @@ def run_warmstart(args):
     import torch
     from paper_1307_6703_gb300 import warmstart as ws
     from paper_1307_6703_gb300.fno import Fno
-    from oracle import fno as ref  # seeded initial weights only (the tests use the same)
+    from paper_1307_6703_gb300.workloads import network_pack, network_weights
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
@@ -422,9 +423,7 @@ def run_warmstart(args):
     gen_s = time.perf_counter() - t0
     net = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=16,
               nx_max=512, ny_max=128, gemm_bf16=True)
-    p = ref.init_params(32, 64, 4, 16, 8, seed=0, outputs=3)
-    names = ["P", "p"] + sum([[f"W{l}", f"w{l}", f"Rr{l}", f"Ri{l}"] for l in range(4)], []) + ["Q1", "q1", "Q2", "q2"]
-    net.set_params(np.concatenate([np.asarray(p[k]).ravel() for k in names]).astype(np.float32))
+    net.set_params(network_pack(network_weights(32, 64, 4, 16, 8, seed=0, outputs=3), 4))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hist = ws.train(net, [(ptr[:768][k1], n1[k1]), (ptr[768:][k2], n2[k2])], steps=6000, lr=2e-3)
@@ -494,6 +493,56 @@ def run_warmstart(args):
                      "kernel": "network training step (forward + backward, ~3x forward FLOPs)"},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_network(args):
+    """The warm-start network alone: K training steps (forward, loss and
+    backward, Adam) on 16 fields of 256x64, device-timed."""
+    import torch
+    from paper_1307_6703_gb300.fno import Fno
+    from paper_1307_6703_gb300.warmstart import sample_params
+    from paper_1307_6703_gb300.workloads import network_pack, network_weights
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return 0
+    net = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=16,
+              nx_max=256, ny_max=64, gemm_bf16=True)
+    net.set_params(network_pack(network_weights(32, 64, 4, 16, 8, seed=0, outputs=3), 4))
+    prm = torch.tensor(sample_params(16, seed=5), dtype=torch.float32, device="cuda")
+    out = torch.empty((16, 3, 64, 256), dtype=torch.float32, device="cuda")
+    tgt = torch.zeros_like(out)
+
+    def step():
+        net.forward(prm, 256, 64, out)
+        net.backward(tgt, want_loss=False)
+        net.adam(1e-3)
+
+    for _ in range(args.warmup):
+        step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    net.close()
+    S = 256 * 64
+    flop = 3 * 16 * S * (4 * (2 * 32 * 32 * 2 + 2 * 32 * 32) + 2 * 64 * 32 + 2 * 3 * 64)
+    peak, peak_kind = measured_peaks("bf16_tflops")
+    achieved = flop / (ms * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "train_step_ms", "value": round(ms, 4), "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (GEMMs bf16)", "data": "synthetic",
+        "config": {"workload": "network_train_step_16x256x64", "width": 32, "layers": 4, "modes": [16, 8]},
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 5), "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "training step (forward + backward, ~3x forward FLOPs)"}}), flush=True)
     return 0
 
 
@@ -572,7 +621,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=sorted(B_ALG), default="fp32")
-    ap.add_argument("--workload", choices=["single", "batch", "warmstart", "precision"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "warmstart", "precision", "network"],
+                    default="single",
                     help="single: the 4096x1024 lattice; batch: the seeded ensemble of "
                          "independent lattices through the batched solver")
     ap.add_argument("--batch-count", type=int, default=64)
@@ -591,6 +641,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "network":
+        return run_network(args)
     return run_ours(args)
 
 

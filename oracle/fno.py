@@ -20,6 +20,10 @@ The network (definitions written out plainly, no blocking or fusion):
             Q2: outputs x hidden)
   loss      mean over b, output channel, y, x of (out - target)^2
 gelu(z) = z Phi(z) with Phi the standard normal distribution function.
+
+Parameters are a dict of float64 arrays keyed P, p, W{l}, w{l}, Rr{l}, Ri{l}
+(Rr, Ri: [ky][kx][c_in][c_out]), Q1, q1, Q2, q2; the tests draw them with
+the shared seeded generator and give the CUDA network the same values.
 """
 from __future__ import annotations
 
@@ -80,25 +84,6 @@ def idft_modes(V: np.ndarray, ny: int, nx: int) -> np.ndarray:
     c = np.where(kx == 0, 1.0, 2.0)
     out = np.einsum("yk,...km,m,mx->...yx", ey, V, c, ex)
     return out.real / (nx * ny)
-
-
-def init_params(width: int, hidden: int, layers: int, mx: int, my: int, seed: int,
-                outputs: int = 1) -> dict:
-    """Seeded initial parameters (the CUDA network is given the same values)."""
-    rng = np.random.default_rng(seed)
-    p = {"P": rng.standard_normal((width, N_FEATURES)) / math.sqrt(N_FEATURES),
-         "p": np.zeros(width)}
-    for l in range(layers):
-        p[f"W{l}"] = rng.standard_normal((width, width)) / math.sqrt(width)
-        p[f"w{l}"] = np.zeros(width)
-        s = 1.0 / (width * width)
-        p[f"Rr{l}"] = s * rng.uniform(0, 1, (my, mx, width, width))  # [ky, kx, c_in, c_out]
-        p[f"Ri{l}"] = s * rng.uniform(0, 1, (my, mx, width, width))
-    p["Q1"] = rng.standard_normal((hidden, width)) / math.sqrt(width)
-    p["q1"] = np.zeros(hidden)
-    p["Q2"] = rng.standard_normal((outputs, hidden)) / math.sqrt(hidden)
-    p["q2"] = np.zeros(outputs)
-    return p
 
 
 def forward(p: dict, x: np.ndarray, layers: int, mx: int, my: int) -> np.ndarray:

@@ -120,3 +120,42 @@ def batch_workloads(count: int = 64, seed: int = 7) -> list[Workload]:
         out.append(Workload(f"batch{i}_{nx}x{ny}", nx, ny, True, tr * TC, 1.0, a0, lam, -uw, uw,
                             nq[0], nq[1], 1000, seed=seed * 1000 + i))
     return out
+
+
+# Warm-start network: seeded initial weights (random draws only; the network
+# itself is defined in include/fno.h).  Both the CUDA network and its CPU
+# reference are given these values.
+N_FEATURES = 5
+
+
+def network_groups(layers: int) -> list[str]:
+    """Parameter groups in the order of the flat vector of include/fno.h."""
+    return ["P", "p"] + sum([[f"W{l}", f"w{l}", f"Rr{l}", f"Ri{l}"] for l in range(layers)], []) + \
+        ["Q1", "q1", "Q2", "q2"]
+
+
+def network_weights(width: int, hidden: int, layers: int, mx: int, my: int, seed: int,
+                    outputs: int = 1) -> dict:
+    """Seeded initial weights: P, W_l, Q1, Q2 standard normal / sqrt(fan-in),
+    biases zero, spectral weights Rr, Ri ~ U[0, 1] / width^2 with shape
+    [modes_y][modes_x][width(in)][width(out)]."""
+    rng = np.random.default_rng(seed)
+    p = {"P": rng.standard_normal((width, N_FEATURES)) / np.sqrt(N_FEATURES),
+         "p": np.zeros(width)}
+    for l in range(layers):
+        p[f"W{l}"] = rng.standard_normal((width, width)) / np.sqrt(width)
+        p[f"w{l}"] = np.zeros(width)
+        s = 1.0 / (width * width)
+        p[f"Rr{l}"] = s * rng.uniform(0, 1, (my, mx, width, width))
+        p[f"Ri{l}"] = s * rng.uniform(0, 1, (my, mx, width, width))
+    p["Q1"] = rng.standard_normal((hidden, width)) / np.sqrt(width)
+    p["q1"] = np.zeros(hidden)
+    p["Q2"] = rng.standard_normal((outputs, hidden)) / np.sqrt(hidden)
+    p["q2"] = np.zeros(outputs)
+    return p
+
+
+def network_pack(p: dict, layers: int) -> np.ndarray:
+    """Flat FP32 parameter vector in the order of include/fno.h."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).ravel()
+                           for k in network_groups(layers)]).astype(np.float32)

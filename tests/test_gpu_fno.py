@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import fno as ref
+from paper_1307_6703_gb300.workloads import network_weights
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +46,7 @@ def unpack(flat, p, layers):
 
 
 def _reference_params(seed):
-    p = ref.init_params(CFG["width"], CFG["hidden"], CFG["layers"], CFG["modes_x"], CFG["modes_y"], seed,
+    p = network_weights(CFG["width"], CFG["hidden"], CFG["layers"], CFG["modes_x"], CFG["modes_y"], seed,
                         outputs=CFG["outputs"])
     rng = np.random.default_rng(seed + 1)
     for k in list(p):  # exercise the biases and scale the spectral weights up

@@ -22,10 +22,8 @@ def _cuda():
 
 
 def _initial_params():
-    from oracle import fno as ref
-    p = ref.init_params(32, 64, 4, 16, 8, seed=0, outputs=3)
-    names = ["P", "p"] + sum([[f"W{l}", f"w{l}", f"Rr{l}", f"Ri{l}"] for l in range(4)], []) + ["Q1", "q1", "Q2", "q2"]
-    return np.concatenate([np.asarray(p[k]).ravel() for k in names]).astype(np.float32)
+    from paper_1307_6703_gb300.workloads import network_pack, network_weights
+    return network_pack(network_weights(32, 64, 4, 16, 8, seed=0, outputs=3), 4)
 
 
 def test_warm_start_shortens_the_run_to_steady_state():

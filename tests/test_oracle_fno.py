@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import fno
+from paper_1307_6703_gb300.workloads import network_weights
 
 
 def _band_limited(rng, ny, nx, mx, my):
@@ -59,7 +60,7 @@ def test_spectral_layer_with_identity_weights_projects():
     band-limited field (in every channel) to itself."""
     rng = np.random.default_rng(3)
     ny, nx, mx, my, width = 16, 32, 6, 6, 3
-    p = fno.init_params(width, 4, 1, mx, my, seed=0)
+    p = network_weights(width, 4, 1, mx, my, seed=0)
     p["W0"][:] = 0.0
     p["Rr0"][:] = np.eye(width)[None, None]
     p["Ri0"][:] = 0.0
@@ -82,7 +83,7 @@ def test_features_definition():
 
 def test_forward_is_affine_in_the_last_layer():
     """out is affine in (Q2, q2): doubling Q2 and q2 doubles out."""
-    p = fno.init_params(4, 6, 2, 4, 4, seed=5, outputs=3)
+    p = network_weights(4, 6, 2, 4, 4, seed=5, outputs=3)
     x = fno.features(np.array([[0.02, 5e-4, 32.0, 0.95]]), 32, 8)
     o1 = fno.forward(p, x, 2, 4, 4)
     p["Q2"] *= 2.0
