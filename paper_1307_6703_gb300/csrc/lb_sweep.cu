@@ -44,7 +44,10 @@
 // diagonal links, rounded to FP32) is stored rounded to nearest even; the
 // rest population stays a float and takes the remainder n - sum_{i>=1} f_i
 // of the ROUNDED values, so each site keeps its density to FP32 round-off.
-// Arithmetic is FP32 in both formats.
+// Arithmetic is FP32 in both formats; with 16-bit storage it runs on the
+// deviations themselves: the references cancel in the momentum, add one
+// constant to the density, and enter the collision as one constant per link
+// class, so decoding and encoding are a conversion each.
 //
 // Every CTA also writes FP64 partial sums of mass and momentum of the state
 // it stored, and a flag for non-finite or out-of-range sites, so that the
@@ -84,6 +87,7 @@ struct StoreF32 {
     return reinterpret_cast<const float *>(slot) + r * kCols;
   }
   __device__ static float get(Row p, int q, int c, const SweepArgs &) { return p[q * 2 * kCols + c]; }
+  __device__ static float getd(Row p, int q, int c, const SweepArgs &) { return p[q * 2 * kCols + c]; }
 };
 
 // 16-bit deviation storage: a float box {kCols, 2, 1} of the rest plane and a
@@ -113,6 +117,12 @@ struct StoreDev {
   __device__ static float get(const Row &p, int q, int c, const SweepArgs &A) {
     if (q == 0) return p.f0[c];
     return (q <= 4 ? A.ref_ax : A.ref_dg) + dec(p.d[(q - 1) * 2 * kDevCols + c]);
+  }
+  // Deviation d_q = f_q - r_q of a moving population (q >= 1); the rest
+  // population (q = 0) is stored in full and returned as it is.
+  __device__ static float getd(const Row &p, int q, int c, const SweepArgs &) {
+    if (q == 0) return p.f0[c];
+    return dec(p.d[(q - 1) * 2 * kDevCols + c]);
   }
 };
 template <>
@@ -223,22 +233,35 @@ __device__ __forceinline__ float2 sdy2(const Sten &s, const float2 *r0, const fl
                      s.N * (g.y - h.y) + s.M * ((c.y - e.y) + (d.y - f.y)));
 }
 
-// Propagated populations of the site in column t of row r1 (pull).
+// Propagated populations of the site in column t of row r1 (pull).  With
+// 16-bit storage f[1..8] are the deviations d_i = f_i - r_i and f[0] is the
+// rest population; with FP32 storage they are the populations.
 template <class St>
 __device__ __forceinline__ void pull(const typename St::Row &r0, const typename St::Row &r1,
                                      const typename St::Row &r2, int t, float *f, const SweepArgs &A) {
-  f[0] = St::get(r1, 0, t, A); f[1] = St::get(r1, 1, t - 1, A); f[3] = St::get(r1, 3, t + 1, A);
-  f[2] = St::get(r0, 2, t, A); f[5] = St::get(r0, 5, t - 1, A); f[6] = St::get(r0, 6, t + 1, A);
-  f[4] = St::get(r2, 4, t, A); f[7] = St::get(r2, 7, t + 1, A); f[8] = St::get(r2, 8, t - 1, A);
+  f[0] = St::getd(r1, 0, t, A); f[1] = St::getd(r1, 1, t - 1, A); f[3] = St::getd(r1, 3, t + 1, A);
+  f[2] = St::getd(r0, 2, t, A); f[5] = St::getd(r0, 5, t - 1, A); f[6] = St::getd(r0, 6, t + 1, A);
+  f[4] = St::getd(r2, 4, t, A); f[7] = St::getd(r2, 7, t + 1, A); f[8] = St::getd(r2, 8, t - 1, A);
+}
+
+// Deviations <-> populations of the moving links (16-bit storage only).
+__device__ __forceinline__ void add_refs(float *f, float r_ax, float r_dg) {
+#pragma unroll
+  for (int q = 1; q < 9; ++q) f[q] += q <= 4 ? r_ax : r_dg;
 }
 
 // One collision (Eqs. evoleq, eqfunc, forceterm, coeff) in the moment form
 //   f*_i = (1 - omega) f_i + w_i E_i,
 //   E_i = omega n [A_i + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2] + 3 c.B + 9/2 C:cc - 3/2 tr C,
 // for the eight moving populations (the rest population is the remainder,
-// taken by the caller after any storage rounding).
+// taken by the caller after any storage rounding).  kDev: f holds the
+// deviations d_i = f_i - r_i and fs receives d*_i = f*_i - r_i, which is
+//   d*_i = (1 - omega) d_i + w_i (E_i - omega r_i / w_i);
+// k_ax = 9 omega r_ax and k_dg = 36 omega r_dg enter the isotropic part of E.
+template <bool kDev>
 __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, float n, float Jx, float Jy,
-                                        float Fx, float Fy, float dnx, float dny, float divJ, float *fs) {
+                                        float Fx, float Fy, float dnx, float dny, float divJ, float *fs,
+                                        float k_ax = 0.f, float k_dg = 0.f) {
   const float rn = __fdividef(1.0f, n);
   const float ux = Jx * rn, uy = Jy * rn;
   const float Bx = A.g * Fx, By = A.g * Fy;
@@ -247,8 +270,16 @@ __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, floa
   const float Cxy = A.g * ((ux * Fy + Fx * uy) + A.th * (ux * dny + uy * dnx));
   const float trC = Cxx + Cyy;
   const float on = A.omega * n;
-  const float base = -1.5f * (on * (ux * ux + uy * uy) + trC);
-  const float e_ax = on * A.A_ax + base, e_dg = on * A.A_diag + base;
+  const float iso = on * (ux * ux + uy * uy) + trC;
+  float e_ax, e_dg;
+  if constexpr (kDev) {
+    e_ax = on * A.A_ax + fmaf(-1.5f, iso, -k_ax);
+    e_dg = on * A.A_diag + fmaf(-1.5f, iso, -k_dg);
+  } else {
+    const float base = -1.5f * iso;
+    e_ax = on * A.A_ax + base;
+    e_dg = on * A.A_diag + base;
+  }
   const float symx = 4.5f * (on * ux * ux + Cxx), antx = 3.f * (on * ux + Bx);
   const float symy = 4.5f * (on * uy * uy + Cyy), anty = 3.f * (on * uy + By);
   const float vp = ux + uy, vm = uy - ux;
@@ -299,6 +330,11 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   float *col = A.fout + A.off + x;  // f* (rest plane for 16-bit storage) of this column at interior row 0
   const int pitch = A.pitch, plane = (int)A.plane;
   const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);  // periodic image column
+  // 16-bit storage: sum of the moving links' reference populations, and the
+  // collision's isotropic offsets 9 omega r_ax, 36 omega r_dg.
+  const float r_sum = St::kDev ? 4.f * (A.ref_ax + A.ref_dg) : 0.f;
+  const float k_ax = St::kDev ? 9.f * A.omega * A.ref_ax : 0.f;
+  const float k_dg = St::kDev ? 36.f * A.omega * A.ref_dg : 0.f;
 
   // TMA writes need 128-byte aligned destinations: refuse to run otherwise.
   if (smem_u32(&S.pops[0][0]) & 127u) {
@@ -347,6 +383,9 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           float f[9];
           pull<St>(r0, r1, r2, t, f, A);
           float n;
+          if constexpr (St::kDev) {
+            if (!kSteady && walls && (y == 0 || y == ny - 1)) add_refs(f, A.ref_ax, A.ref_dg);
+          }
           if (!kSteady && walls && y == 0) {
             n = St::get(r1, 0, t, A) + St::get(r1, 4, t, A) + St::get(r1, 7, t, A) + St::get(r1, 8, t, A) + f[1] +
                 f[3] + f[4] + f[7] + f[8];
@@ -355,6 +394,8 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
                 f[3] + f[2] + f[6] + f[5];
           } else {
             n = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+            if constexpr (St::kDev) n += r_sum;
+            // the reference populations cancel in the momentum
             sx_new[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
             sy_new[j] = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
           }
@@ -412,6 +453,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             const Row w2 = St::row(S.pops[s5], 0), w3 = St::row(S.pops[s5], 1);
             float f[9];
             pull<St>(j ? w1 : w0, j ? w2 : w1, j ? w3 : w2, t, f, A);
+            if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
             const bool top = y != 0;
             wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
             sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
@@ -461,8 +503,12 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           const float Jx = Jc.x, Jy = Jc.y;
           float f[9], fs[9];
           pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f, A);
-          if (bot || top) wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
-          collide(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs);
+          if (bot || top) {
+            if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
+            wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
+            if constexpr (St::kDev) add_refs(f, -A.ref_ax, -A.ref_dg);
+          }
+          collide<St::kDev>(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs, k_ax, k_dg);
           const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
@@ -487,17 +533,17 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
               }
             }
           } else {
-            // Round the deviations, then let the rest population carry the
-            // remainder of the rounded values (site density kept).
+            // Round the deviations (fs[1..8] hold d*_i), then let the rest
+            // population carry the remainder of the rounded values (site
+            // density kept): f*_0 = (n - sum r_i) - sum rounded d*_i.
             using H = decltype(St::enc(0.f));
             H code[8];
 #pragma unroll
             for (int q = 1; q < 9; ++q) {
-              const float r = q <= 4 ? A.ref_ax : A.ref_dg;
-              code[q - 1] = St::enc(fs[q] - r);
-              fs[q] = r + St::dec(code[q - 1]);
+              code[q - 1] = St::enc(fs[q]);
+              fs[q] = St::dec(code[q - 1]);
             }
-            fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
+            fs[0] = (n - r_sum) - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
             H *od = reinterpret_cast<H *>(A.fdev) + (A.off + x + (long long)y * pitch);
             o[0] = fs[0];
 #pragma unroll
@@ -528,7 +574,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             if constexpr (!St::kDev) {
               acc_x += Jx + 0.5f * Fx;
               acc_y += Jy + 0.5f * Fy;
-            } else {  // momentum of the stored (rounded) populations
+            } else {  // momentum of the stored (rounded) populations; refs cancel
               acc_x += ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
               acc_y += ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
             }
