@@ -322,6 +322,12 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   const bool actB = t >= 2 && t <= W + 5;
   const bool actC = t >= 3 && t <= W + 4;
   const bool actD = t >= 4 && t <= W + 3;
+  // Steady iterations run every stage on every thread, at column tcl (the
+  // thread's own column for every active thread; clamped so that the
+  // neighbours stay inside the window) and store ring values at column t:
+  // the columns an inactive thread writes are never read by the next
+  // stage's active threads, so only the global stores need a guard.
+  const int tcl = min(max(t, 1), kCols - 2);
   const int kmax = (yb - ya + 5) >> 1;  // last iteration
   const int npairs = kmax + 2;          // rows ya-4 .. ya+2*kmax+3
   const Sten st{A.N, A.M, A.Q, A.R, A.four_QR};
@@ -375,13 +381,14 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       const Row q0 = St::row(S.pops[s5], 0), q1 = St::row(S.pops[s5], 1);      // rows a-1, a
       const Row q2 = St::row(S.pops[s5p1], 0), q3 = St::row(S.pops[s5p1], 1);  // rows a+1, a+2
       float sx_new[2] = {0.f, 0.f}, sy_new[2] = {0.f, 0.f};
+      const int tc = kSteady ? tcl : t;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int y = a + j;
         const Row r0 = j ? q1 : q0, r1 = j ? q2 : q1, r2 = j ? q3 : q2;
-        if (actA && (kSteady || !walls || (y >= 0 && y <= ny - 1))) {
+        if (kSteady || (actA && (!walls || (y >= 0 && y <= ny - 1)))) {
           float f[9];
-          pull<St>(r0, r1, r2, t, f, A);
+          pull<St>(r0, r1, r2, tc, f, A);
           float n;
           if constexpr (St::kDev) {
             if (!kSteady && walls && (y == 0 || y == ny - 1)) add_refs(f, A.ref_ax, A.ref_dg);
@@ -418,13 +425,13 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
         for (int j = 0; j < 2; ++j) {
           const int y = a - 1 + j;
           const float *r0 = j ? n1 : n0, *r1 = j ? n2 : n1, *r2 = j ? n3 : n2;
-          if (actB && (kSteady || (y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1))))) {
+          if (kSteady || (actB && y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1)))) {
             if (!kSteady && walls && y == 0) r0 = r2;
             if (!kSteady && walls && y == ny - 1) r2 = r0;
-            const float c = r1[t];
+            const float c = r1[tc];
             const float nT = c * A.T;
             const float pw = nT * __fdividef(1.0f, 1.0f - A.b * c) - A.a * c * c;
-            S.PL[s2][j][t] = make_float2(nT - pw, slap(st, r0, r1, r2, t));
+            S.PL[s2][j][t] = make_float2(nT - pw, slap(st, r0, r1, r2, tc));
           }
         }
       }
@@ -437,13 +444,13 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 2 + j;
-          if (!(actC && (kSteady || (y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1)))))) continue;
+          if (!(kSteady || (actC && y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1))))) continue;
           const float2 *p0 = j ? P1 : P0, *p1 = j ? P2 : P1, *p2 = j ? P3 : P2;
           if (!kSteady && walls && y == 0) p0 = p2;
           if (!kSteady && walls && y == ny - 1) p2 = p0;
-          const float n = S.n[s3m1][j][t];
+          const float n = S.n[s3m1][j][tc];
           const float kn = A.kappa * n;
-          const float2 dx = sdx2(st, p0, p1, p2, t), dy = sdy2(st, p0, p2, t);
+          const float2 dx = sdx2(st, p0, p1, p2, tc), dy = sdy2(st, p0, p2, tc);
           const float Fx = (dx.x + kn * dx.y) + A.A0 * sinx;
           const float Fy = dy.x + kn * dy.y;
           float sx = sxa[j], sy = sya[j];
@@ -478,7 +485,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 3 + j;
-          if (!(actD && (kSteady || (y >= ya && y < yb)))) continue;
+          if (!(kSteady || (actD && y >= ya && y < yb))) continue;
           const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
           const float2 *j0p = j ? J1 : J0, *j1p = j ? J2 : J1, *j2p = j ? J3 : J2;
           const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
@@ -493,22 +500,23 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             dJy = st.N * (sgp * g.y - sgm * h.y) + st.M * ((sgp * c.y - sgm * e.y) + (sgp * d.y - sgm * f.y));
             dJx = sdx2(st, j0p, j1p, j2p, t).x;
           } else {
-            dJx = sdx2(st, j0p, j1p, j2p, t).x;
-            dJy = sdy2(st, j0p, j2p, t).y;
+            dJx = sdx2(st, j0p, j1p, j2p, tc).x;
+            dJy = sdy2(st, j0p, j2p, tc).y;
           }
-          const float n = m1[t];
-          const float dnx = sdx(st, m0, m1, m2, t), dny = sdy(st, m0, m2, t);
+          const float n = m1[tc];
+          const float dnx = sdx(st, m0, m1, m2, tc), dny = sdy(st, m0, m2, tc);
           const float divJ = dJx + dJy;
-          const float2 Jc = j1p[t];
+          const float2 Jc = j1p[tc];
           const float Jx = Jc.x, Jy = Jc.y;
           float f[9], fs[9];
-          pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, t, f, A);
+          pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, tc, f, A);
           if (bot || top) {
             if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
             wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
             if constexpr (St::kDev) add_refs(f, -A.ref_ax, -A.ref_dg);
           }
           collide<St::kDev>(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs, k_ax, k_dg);
+          if (kSteady && !actD) continue;  // computed, not stored (see tcl)
           const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
