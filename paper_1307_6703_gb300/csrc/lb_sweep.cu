@@ -203,6 +203,14 @@ __device__ __forceinline__ void tma_pair(const CUtensorMap *m0, const CUtensorMa
 }
 
 __device__ __forceinline__ int dec(int s, int n) { return s == 0 ? n - 1 : s - 1; }
+
+// 1/v by the PTX approximate reciprocal (v > 0 and finite here: densities
+// and 1 - b n on the liquid-vapour branch).
+__device__ __forceinline__ float rcp(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 __device__ __forceinline__ int inc(int s, int n) { return s == n - 1 ? 0 : s + 1; }
 
 // x-derivative, y-derivative and Laplacian stencils of Eqs. (xstencil,
@@ -254,47 +262,57 @@ __device__ __forceinline__ void add_refs(float *f, float r_ax, float r_dg) {
 //   f*_i = (1 - omega) f_i + w_i E_i,
 //   E_i = omega n [A_i + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2] + 3 c.B + 9/2 C:cc - 3/2 tr C,
 // for the eight moving populations (the rest population is the remainder,
-// taken by the caller after any storage rounding).  kDev: f holds the
-// deviations d_i = f_i - r_i and fs receives d*_i = f*_i - r_i, which is
-//   d*_i = (1 - omega) d_i + w_i (E_i - omega r_i / w_i);
-// k_ax = 9 omega r_ax and k_dg = 36 omega r_dg enter the isotropic part of E.
+// taken by the caller after any storage rounding).  With on = omega n,
+// S_i = on (c.u)^2 + C:cc and T_i = on c.u + c.B, w_i E_i splits into a part
+// even in c, h_i = w_i (on A_i - 3/2 (on u^2 + tr C)) + 9/2 w_i S_i, and an
+// odd part t_i = 3 w_i T_i.  On the axes (w = 1/9) h_x = e_a + S_x / 2 and
+// t_x = T_x / 3; on the diagonals (w = 1/36) S_(+-) = S_x + S_y +- 2 X with
+// X = on u_x u_y + C_xy and T_(+-) = T_y +- T_x, so
+//   h_(+-) = (e_d - e_a / 2) + (h_x + h_y +- X) / 4,  t_(+-) = (t_y +- t_x) / 4,
+// where e_a, e_d are w_i (on A_i - 3/2 (on u^2 + tr C)) on the axes and
+// diagonals.  kDev: f holds the deviations d_i = f_i - r_i and fs receives
+// d*_i = f*_i - r_i = (1 - omega) d_i + w_i E_i - omega r_i; wr_ax and wr_dg
+// are omega r_i on the axes and diagonals and join e_a and e_d.
 template <bool kDev>
 __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, float n, float Jx, float Jy,
                                         float Fx, float Fy, float dnx, float dny, float divJ, float *fs,
-                                        float k_ax = 0.f, float k_dg = 0.f) {
-  const float rn = __fdividef(1.0f, n);
+                                        float wr_ax = 0.f, float wr_dg = 0.f) {
+  const float rn = rcp(n);
   const float ux = Jx * rn, uy = Jy * rn;
-  const float Bx = A.g * Fx, By = A.g * Fy;
-  const float Cxx = A.g * (2.f * ux * Fx + A.th * (2.f * ux * dnx + divJ));
-  const float Cyy = A.g * (2.f * uy * Fy + A.th * (2.f * uy * dny + divJ));
-  const float Cxy = A.g * ((ux * Fy + Fx * uy) + A.th * (ux * dny + uy * dnx));
-  const float trC = Cxx + Cyy;
   const float on = A.omega * n;
-  const float iso = on * (ux * ux + uy * uy) + trC;
-  float e_ax, e_dg;
+  const float onux = on * ux, onuy = on * uy;
+  const float ux2 = ux + ux, uy2 = uy + uy;
+  // C / g (Eq. coeff)
+  const float cxx = fmaf(A.th, fmaf(ux2, dnx, divJ), ux2 * Fx);
+  const float cyy = fmaf(A.th, fmaf(uy2, dny, divJ), uy2 * Fy);
+  const float cxy = fmaf(A.th, fmaf(ux, dny, uy * dnx), fmaf(ux, Fy, Fx * uy));
+  const float iso = fmaf(on, fmaf(ux, ux, uy * uy), A.g * (cxx + cyy));  // on u^2 + tr C
+  float ea, ed;
   if constexpr (kDev) {
-    e_ax = on * A.A_ax + fmaf(-1.5f, iso, -k_ax);
-    e_dg = on * A.A_diag + fmaf(-1.5f, iso, -k_dg);
+    ea = fmaf(on, A.A_ax * (1.f / 9.f), fmaf(-1.f / 6.f, iso, -wr_ax));
+    ed = fmaf(on, A.A_diag * (1.f / 36.f), fmaf(-1.f / 24.f, iso, -wr_dg));
   } else {
-    const float base = -1.5f * iso;
-    e_ax = on * A.A_ax + base;
-    e_dg = on * A.A_diag + base;
+    ea = fmaf(on, A.A_ax * (1.f / 9.f), iso * (-1.f / 6.f));
+    ed = fmaf(on, A.A_diag * (1.f / 36.f), iso * (-1.f / 24.f));
   }
-  const float symx = 4.5f * (on * ux * ux + Cxx), antx = 3.f * (on * ux + Bx);
-  const float symy = 4.5f * (on * uy * uy + Cyy), anty = 3.f * (on * uy + By);
-  const float vp = ux + uy, vm = uy - ux;
-  const float sym5 = 4.5f * (on * vp * vp + trC + 2.f * Cxy), ant5 = 3.f * (on * vp + (Bx + By));
-  const float sym6 = 4.5f * (on * vm * vm + trC - 2.f * Cxy), ant6 = 3.f * (on * vm + (By - Bx));
+  const float g2 = 0.5f * A.g;
+  const float hx = fmaf(0.5f * onux, ux, fmaf(g2, cxx, ea));
+  const float hy = fmaf(0.5f * onuy, uy, fmaf(g2, cyy, ea));
+  const float X = fmaf(onux, uy, A.g * cxy);
+  const float tx = fmaf(A.g, Fx, onux) * (1.f / 3.f);
+  const float ty = fmaf(A.g, Fy, onuy) * (1.f / 3.f);
+  const float hd = fmaf(-0.5f, ea, ed), hxy = hx + hy;
+  const float h5 = fmaf(0.25f, hxy + X, hd), h6 = fmaf(0.25f, hxy - X, hd);
+  const float t5 = 0.25f * (tx + ty), t6 = 0.25f * (ty - tx);
   const float om1 = A.one_minus_omega;
-  constexpr float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-  fs[1] = om1 * f[1] + w1 * (e_ax + symx + antx);
-  fs[3] = om1 * f[3] + w1 * (e_ax + symx - antx);
-  fs[2] = om1 * f[2] + w1 * (e_ax + symy + anty);
-  fs[4] = om1 * f[4] + w1 * (e_ax + symy - anty);
-  fs[5] = om1 * f[5] + w5 * (e_dg + sym5 + ant5);
-  fs[7] = om1 * f[7] + w5 * (e_dg + sym5 - ant5);
-  fs[6] = om1 * f[6] + w5 * (e_dg + sym6 + ant6);
-  fs[8] = om1 * f[8] + w5 * (e_dg + sym6 - ant6);
+  fs[1] = fmaf(om1, f[1], hx + tx);
+  fs[3] = fmaf(om1, f[3], hx - tx);
+  fs[2] = fmaf(om1, f[2], hy + ty);
+  fs[4] = fmaf(om1, f[4], hy - ty);
+  fs[5] = fmaf(om1, f[5], h5 + t5);
+  fs[7] = fmaf(om1, f[7], h5 - t5);
+  fs[6] = fmaf(om1, f[6], h6 + t6);
+  fs[8] = fmaf(om1, f[8], h6 - t6);
 }
 
 }  // namespace
@@ -337,10 +355,10 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   const int pitch = A.pitch, plane = (int)A.plane;
   const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);  // periodic image column
   // 16-bit storage: sum of the moving links' reference populations, and the
-  // collision's isotropic offsets 9 omega r_ax, 36 omega r_dg.
+  // collision's offsets omega r_ax, omega r_dg.
   const float r_sum = St::kDev ? 4.f * (A.ref_ax + A.ref_dg) : 0.f;
-  const float k_ax = St::kDev ? 9.f * A.omega * A.ref_ax : 0.f;
-  const float k_dg = St::kDev ? 36.f * A.omega * A.ref_dg : 0.f;
+  const float wr_ax = St::kDev ? A.omega * A.ref_ax : 0.f;
+  const float wr_dg = St::kDev ? A.omega * A.ref_dg : 0.f;
 
   // TMA writes need 128-byte aligned destinations: refuse to run otherwise.
   if (smem_u32(&S.pops[0][0]) & 127u) {
@@ -382,6 +400,10 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       const Row q2 = St::row(S.pops[s5p1], 0), q3 = St::row(S.pops[s5p1], 1);  // rows a+1, a+2
       float sx_new[2] = {0.f, 0.f}, sy_new[2] = {0.f, 0.f};
       const int tc = kSteady ? tcl : t;
+      // Each stage computes both rows before it stores either, so that the
+      // two rows' independent arithmetic can interleave.
+      float nv[2] = {0.f, 0.f};
+      bool nw[2] = {false, false};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int y = a + j;
@@ -406,9 +428,13 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             sx_new[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
             sy_new[j] = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
           }
-          S.n[s3][j][t] = n;
+          nv[j] = n;
+          nw[j] = true;
         }
       }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (nw[j]) S.n[s3][j][t] = nv[j];
       __syncthreads();
       // The slot of pair k-3 is free (last used by iteration k-1): refill it
       // with pair k+2.
@@ -421,6 +447,8 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       {
         const float *n0 = S.n[s3m1][0], *n1 = S.n[s3m1][1];  // rows a-2, a-1
         const float *n2 = S.n[s3][0], *n3 = S.n[s3][1];      // rows a, a+1
+        float2 plv[2];
+        bool plw[2] = {false, false};
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 1 + j;
@@ -430,10 +458,14 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             if (!kSteady && walls && y == ny - 1) r2 = r0;
             const float c = r1[tc];
             const float nT = c * A.T;
-            const float pw = nT * __fdividef(1.0f, 1.0f - A.b * c) - A.a * c * c;
-            S.PL[s2][j][t] = make_float2(nT - pw, slap(st, r0, r1, r2, tc));
+            const float pw = nT * rcp(1.0f - A.b * c) - A.a * c * c;
+            plv[j] = make_float2(nT - pw, slap(st, r0, r1, r2, tc));
+            plw[j] = true;
           }
         }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          if (plw[j]) S.PL[s2][j][t] = plv[j];
       }
       __syncthreads();
 
@@ -441,6 +473,8 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       float Fx_cur[2] = {0.f, 0.f}, Fy_cur[2] = {0.f, 0.f};
       {
         const float2 *P0 = S.PL[s2m1][0], *P1 = S.PL[s2m1][1], *P2 = S.PL[s2][0], *P3 = S.PL[s2][1];
+        float2 jv[2];
+        bool jw[2] = {false, false};
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 2 + j;
@@ -466,10 +500,14 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
             sy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
           }
-          S.J[s2][j][t] = make_float2(sx + 0.5f * Fx, sy + 0.5f * Fy);
+          jv[j] = make_float2(sx + 0.5f * Fx, sy + 0.5f * Fy);
+          jw[j] = true;
           Fx_cur[j] = Fx;
           Fy_cur[j] = Fy;
         }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          if (jw[j]) S.J[s2][j][t] = jv[j];
       }
       sxa[0] = sx_new[0]; sxa[1] = sx_new[1];
       sya[0] = sy_new[0]; sya[1] = sy_new[1];
@@ -515,7 +553,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
             if constexpr (St::kDev) add_refs(f, -A.ref_ax, -A.ref_dg);
           }
-          collide<St::kDev>(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs, k_ax, k_dg);
+          collide<St::kDev>(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs, wr_ax, wr_dg);
           if (kSteady && !actD) continue;  // computed, not stored (see tcl)
           const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
@@ -595,16 +633,18 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
     s5 = s5p1;
     s3 = (s3 + 1) & 3;
   };
-  for (int k = 0; k <= kmax; ++k) {
-    const int a = ya - 3 + 2 * k;
-    // every row of the four stages is interior (see the lambda's note)
-    const bool steady = k >= 3 && a - 2 < yb &&
-                        (walls ? (a - 3 >= 1 && a + 1 <= ny - 2) : (a - 3 >= 4 && a + 1 < ny - 4));
-    if (steady)
-      iteration(k, std::true_type{});
-    else
-      iteration(k, std::false_type{});
-  }
+  // Iteration k (a = ya - 3 + 2k) is steady -- every row of its four stages
+  // interior, see the lambda's note -- when k >= 3, a - 2 < yb and, with
+  // walls, 1 <= a - 3 and a + 1 <= ny - 2 (periodic: 4 <= a - 3 and
+  // a + 1 < ny - 4).  These are lower and upper bounds on k, so the steady
+  // iterations are the range [klo, khi).
+  auto ceil2 = [](int v) { return (v + 1) >> 1; };  // ceil(v / 2), any sign
+  const int klo = max(3, ceil2((walls ? 7 : 10) - ya));
+  const int khi = min(min(kmax + 1, ceil2(yb - ya + 5)), walls ? ((ny - ya) >> 1) + 1 : ceil2(ny - ya - 2));
+  int k = 0;
+  for (; k < min(klo, kmax + 1); ++k) iteration(k, std::false_type{});
+  for (; k < khi; ++k) iteration(k, std::true_type{});
+  for (; k <= kmax; ++k) iteration(k, std::false_type{});
 
   // CTA partial sums of the stored state (FP64, fixed order), when asked
   // for.  Every TMA copy has been waited for, so the population ring is
