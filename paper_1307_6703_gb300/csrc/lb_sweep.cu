@@ -484,9 +484,14 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           if (!kSteady && walls && y == ny - 1) p2 = p0;
           const float n = S.n[s3m1][j][tc];
           const float kn = A.kappa * n;
-          const float2 dx = sdx2(st, p0, p1, p2, tc), dy = sdy2(st, p0, p2, tc);
-          const float Fx = (dx.x + kn * dx.y) + A.A0 * sinx;
-          const float Fy = dy.x + kn * dy.y;
+          // D P + kappa n D L = D G with G = P + kappa n L at the neighbours
+          // (n is the site's own density, a constant of the stencil)
+          auto G = [kn](const float2 v) { return fmaf(kn, v.y, v.x); };
+          const float g0m = G(p0[tc - 1]), g0c = G(p0[tc]), g0p = G(p0[tc + 1]);
+          const float g1m = G(p1[tc - 1]), g1p = G(p1[tc + 1]);
+          const float g2m = G(p2[tc - 1]), g2c = G(p2[tc]), g2p = G(p2[tc + 1]);
+          const float Fx = (st.N * (g1p - g1m) + st.M * ((g2p - g2m) + (g0p - g0m))) + A.A0 * sinx;
+          const float Fy = st.N * (g2c - g0c) + st.M * ((g2p - g0p) + (g2m - g0m));
           float sx = sxa[j], sy = sya[j];
           if (!kSteady && walls && (y == 0 || y == ny - 1)) {
             // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
