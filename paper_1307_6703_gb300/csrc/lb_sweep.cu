@@ -525,10 +525,9 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
         // population rows a-4 .. a-1: pair k-2 row 1, pair k-1 rows 0, 1, pair k row 0
         const Row q0p = St::row(S.pops[s5m2], 1), q1p = St::row(S.pops[s5m1], 0);
         const Row q2p = St::row(S.pops[s5m1], 1), q3p = St::row(S.pops[s5], 0);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int y = a - 3 + j;
-          if (!(kSteady || (actD && y >= ya && y < yb))) continue;
+        // collision of row a-3+j (its inputs from the rings); fs, n, J, F out
+        auto site = [&](const int j, const int y, float *fs, float &n_o, float &Jx_o, float &Jy_o, float &Fx_o,
+                        float &Fy_o) {
           const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
           const float2 *j0p = j ? J1 : J0, *j1p = j ? J2 : J1, *j2p = j ? J3 : J2;
           const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
@@ -551,7 +550,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
           const float divJ = dJx + dJy;
           const float2 Jc = j1p[tc];
           const float Jx = Jc.x, Jy = Jc.y;
-          float f[9], fs[9];
+          float f[9];
           pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, tc, f, A);
           if (bot || top) {
             if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
@@ -559,7 +558,15 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
             if constexpr (St::kDev) add_refs(f, -A.ref_ax, -A.ref_dg);
           }
           collide<St::kDev>(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs, wr_ax, wr_dg);
-          if (kSteady && !actD) continue;  // computed, not stored (see tcl)
+          n_o = n;
+          Jx_o = Jx;
+          Jy_o = Jy;
+          Fx_o = Fx;
+          Fy_o = Fy;
+        };
+        // store row y and add it to the CTA's records
+        auto emit = [&](const int y, float *fs, const float n, const float Jx, const float Jy, const float Fx,
+                      const float Fy) {
           const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
@@ -629,6 +636,25 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
               acc_x += ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
               acc_y += ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
             }
+          }
+        };
+        if constexpr (kSteady) {
+          // both rows first, then their stores (inactive columns store nothing)
+          float fs[2][9], nv_[2], jx[2], jy[2], fx[2], fy[2];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) site(j, a - 3 + j, fs[j], nv_[j], jx[j], jy[j], fx[j], fy[j]);
+          if (actD) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) emit(a - 3 + j, fs[j], nv_[j], jx[j], jy[j], fx[j], fy[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int y = a - 3 + j;
+            if (!(actD && y >= ya && y < yb)) continue;
+            float fs[9], nn, jxx, jyy, fxx, fyy;
+            site(j, y, fs, nn, jxx, jyy, fxx, fyy);
+            emit(y, fs, nn, jxx, jyy, fxx, fyy);
           }
         }
       }
