@@ -226,9 +226,14 @@ def run_ours(args):
     b_alg = B_ALG[args.precision]
     s.init_noise(w.seed + rank, w.rho_mean, w.noise)
 
-    # Tiling chosen by the library's autotuner (state restored afterwards).
-    from paper_1307_6703_gb300 import lb_autotune
-    seg_h = lb_autotune(s.h, 20)
+    # Tiling chosen by the library's autotuner (state restored afterwards),
+    # or fixed with --seg-h (no trial launches: profiler captures).
+    from paper_1307_6703_gb300 import lb_autotune, lb_set_seg_h
+    if args.seg_h:
+        seg_h = int(args.seg_h.split(",")[0])
+        lb_set_seg_h(s.h, seg_h)
+    else:
+        seg_h = lb_autotune(s.h, 20)
 
     # ------------------------------------------------ device-resident timing
     lb_step(s.h, args.warmup)
@@ -340,7 +345,17 @@ def run_batch(args):
                   stream=stream.cuda_stream)
     for v, w in zip(batch, ws):
         v.init_fields(noise_field(w))
-    segs = batch.autotune(10)
+    if args.seg_h:  # segment heights per height class (ny <= 96, <= 160, > 160)
+        from paper_1307_6703_gb300 import lb_set_seg_h
+        cls = [int(v) for v in args.seg_h.split(",")]
+        cls += [cls[-1]] * (3 - len(cls))
+        segs = []
+        for v, w in zip(batch, ws):
+            c = cls[0 if w.ny <= 96 else (1 if w.ny <= 160 else 2)]
+            lb_set_seg_h(v.h, c)
+            segs.append(min(c, w.ny))
+    else:
+        segs = batch.autotune(10)
     lb_batch_step(batch.b, args.warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -626,6 +641,9 @@ def main():
                     help="single: the 4096x1024 lattice; batch: the seeded ensemble of "
                          "independent lattices through the batched solver")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--seg-h", default="",
+                    help="fixed segment height instead of the autotuner (batch: one per height class "
+                         "ny <= 96, <= 160, > 160, comma-separated)")
     ap.add_argument("--precision-nx", type=int, default=4096)
     ap.add_argument("--precision-ny", type=int, default=1024)
     args = ap.parse_args()

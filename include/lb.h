@@ -179,6 +179,14 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step);
  * LB_ERR_OOM.                                                              */
 int lb_autotune(lb_handle *h, int steps, int32_t *seg_h);
 
+/* Set the strip-sweep kernel's segment height (rows per CTA) without
+ * tuning, e.g. to a value an earlier lb_autotune chose; clamped to
+ * [1, ny].  The trajectory does not depend on it beyond FP32 rounding
+ * order.  No-op (LB_OK) for a handle on the tile kernel.  Host-side only
+ * (may grow the per-CTA record array).  Errors: LB_ERR_ARG (seg_h < 1),
+ * LB_ERR_CUDA, LB_ERR_OOM.                                                 */
+int lb_set_seg_h(lb_handle *h, int32_t seg_h);
+
 /* ------------------------------------------------------------------------
  * Batched solver: many independent lattices (different sizes and physical
  * parameters) advanced together, one kernel launch per step over a work

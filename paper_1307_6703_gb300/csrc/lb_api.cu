@@ -694,6 +694,16 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   return LB_OK;
 }
 
+int lb_set_seg_h(lb_handle *h, int32_t seg_h) {
+  if (!h) return LB_ERR_ARG;
+  if (seg_h < 1) return fail(h, LB_ERR_ARG, "lb_set_seg_h: seg_h must be >= 1");
+  if (!h->sweep) return LB_OK;
+  const int sh = std::min((int)seg_h, h->p.ny);
+  LB_CUDA(h, ensure_records(h, (h->p.ny + sh - 1) / sh));
+  set_segments(h, sh);
+  return LB_OK;
+}
+
 int lb_get_step(const lb_handle *h, int64_t *step) {
   if (!h || !step) return LB_ERR_ARG;
   *step = h->step;

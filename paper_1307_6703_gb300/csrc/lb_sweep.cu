@@ -390,6 +390,15 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
     const int s5m1 = dec(s5, kPairs), s5m2 = dec(s5m1, kPairs), s5p1 = inc(s5, kPairs);
     const int s3m1 = (s3 + 3) & 3, s3m2 = (s3 + 2) & 3;  // density ring: 4 pairs
     const int s2 = k & 1, s2m1 = s2 ^ 1;
+    // Every thread is past iteration k-1 (whose stage D last read pair
+    // k-3): refill that slot with pair k+2 now, one stage earlier.
+    if (k >= 3) {
+      __syncthreads();
+      if (t == 0 && k + 2 < npairs) {
+        const int slot = dec(s5m2, kPairs);
+        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
+      }
+    }
     mbar_wait(smem_u32(&S.full[s5p1]), par, A.err);  // newest pair needed: k+1
     if (s5p1 == kPairs - 1) par ^= 1u;
     const int a = ya - 3 + 2 * k;
@@ -438,10 +447,6 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       __syncthreads();
       // The slot of pair k-3 is free (last used by iteration k-1): refill it
       // with pair k+2.
-      if (t == 0 && k >= 3 && k + 2 < npairs) {
-        const int slot = dec(s5m2, kPairs);
-        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
-      }
 
       // -------------------------------------- B: rows a-1, a -- P, lap n
       {

@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_last_error.restype = C.c_char_p
         lib.lb_reduce_noalloc.argtypes = [P, C.c_int, C.c_int32, C.c_int32, C.c_double, P, P, P]
         lib.lb_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+        lib.lb_set_seg_h.argtypes = [P, C.c_int32]
         lib.lb_batch_create.argtypes = [C.POINTER(lb_params), C.c_int32, C.POINTER(P)]
         lib.lb_batch_handle.argtypes = [P, C.c_int32]
         lib.lb_batch_handle.restype = P
@@ -190,6 +191,11 @@ def lb_autotune(h, steps: int = 20) -> int:
     return seg.value
 
 
+def lb_set_seg_h(h, seg_h: int) -> None:
+    """Fix the sweep kernel's segment height (rows per CTA) without tuning."""
+    _check(load_library().lb_set_seg_h(h, seg_h), h)
+
+
 def _bcheck(rc: int, b) -> int:
     if rc != LB_OK:
         s = load_library().lb_batch_last_error(b)
@@ -276,6 +282,10 @@ class Solver:
 
     def autotune(self, steps: int = 20) -> int:
         return lb_autotune(self.h, steps)
+
+    def set_seg_h(self, seg_h: int):
+        lb_set_seg_h(self.h, seg_h)
+        return self
 
     def get_state(self):
         """[9][ny][nx] populations; for 16-bit storage the pair (rest plane

@@ -72,6 +72,13 @@ def test_create_rejects_bad_parameters_without_gpu(lib):
         assert ei.value.code == LB_ERR_ARG
 
 
+def test_null_handles_are_refused_without_gpu(lib):
+    """Entry points given a NULL handle return LB_ERR_ARG before any CUDA call."""
+    from paper_1307_6703_gb300 import LB_ERR_ARG
+    assert lib.lb_set_seg_h(None, 64) == LB_ERR_ARG
+    assert lib.lb_step(None, 1) == LB_ERR_ARG
+
+
 def test_product_path_does_not_touch_oracle():
     """The package never imports the oracle (test infrastructure only)."""
     pkg = os.path.join(ROOT, "paper_1307_6703_gb300")

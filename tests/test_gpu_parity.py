@@ -286,6 +286,22 @@ def test_autotune_keeps_the_trajectory(prec):
     b.close()
 
 
+@pytest.mark.parametrize("seg", [8, 24, 64, 10 ** 6])
+def test_set_seg_h_keeps_the_trajectory(seg):
+    """lb_set_seg_h fixes the tiling without tuning (clamped to ny): the
+    same state, bitwise, as the default tiling; seg_h < 1 is refused."""
+    from paper_1307_6703_gb300 import LB_ERR_ARG, LBError
+    w = C2(0.05).with_(nx=256, ny=200)
+    a = solver_for(w, LB_FP32).init_noise(4, w.rho_mean, w.noise).step(20)
+    b = solver_for(w, LB_FP32).init_noise(4, w.rho_mean, w.noise).set_seg_h(seg).step(20)
+    assert np.array_equal(a.get_state(), b.get_state())
+    with pytest.raises(LBError) as e:
+        b.set_seg_h(0)
+    assert e.value.code == LB_ERR_ARG
+    a.close()
+    b.close()
+
+
 def test_zero_steps_is_a_no_op():
     w = C2(0.05).with_(nx=96, ny=40)
     s = solver_for(w, LB_FP32).init_noise(3, w.rho_mean, w.noise)
