@@ -264,15 +264,14 @@ __device__ __forceinline__ void add_refs(float *f, float r_ax, float r_dg) {
 // for the eight moving populations (the rest population is the remainder,
 // taken by the caller after any storage rounding).  With on = omega n,
 // S_i = on (c.u)^2 + C:cc and T_i = on c.u + c.B, w_i E_i splits into a part
-// even in c, h_i = w_i (on A_i - 3/2 (on u^2 + tr C)) + 9/2 w_i S_i, and an
-// odd part t_i = 3 w_i T_i.  On the axes (w = 1/9) h_x = e_a + S_x / 2 and
-// t_x = T_x / 3; on the diagonals (w = 1/36) S_(+-) = S_x + S_y +- 2 X with
-// X = on u_x u_y + C_xy and T_(+-) = T_y +- T_x, so
-//   h_(+-) = (e_d - e_a / 2) + (h_x + h_y +- X) / 4,  t_(+-) = (t_y +- t_x) / 4,
-// where e_a, e_d are w_i (on A_i - 3/2 (on u^2 + tr C)) on the axes and
-// diagonals.  kDev: f holds the deviations d_i = f_i - r_i and fs receives
-// d*_i = f*_i - r_i = (1 - omega) d_i + w_i E_i - omega r_i; wr_ax and wr_dg
-// are omega r_i on the axes and diagonals and join e_a and e_d.
+// even in c, h_i = e_i + 9/2 w_i S_i with e_i = w_i (on A_i - 3/2 (S_x + S_y))
+// (S_x + S_y = on u^2 + tr C), and an odd part t_i = 3 w_i T_i.  On the
+// axes (w = 1/9) h_x = e_a + S_x / 2, t_x = T_x / 3; on the diagonals
+// (w = 1/36) S_(+-) = S_x + S_y +- 2 X with X = on u_x u_y + C_xy and
+// T_(+-) = T_y +- T_x, so h_(+-) = e_d + (S_x + S_y) / 8 +- X / 4 and
+// t_(+-) = (t_y +- t_x) / 4.  kDev: f holds the deviations d_i = f_i - r_i
+// and fs receives d*_i = f*_i - r_i = (1 - omega) d_i + w_i E_i - omega r_i;
+// wr_ax and wr_dg are omega r_i on the axes and diagonals and join e_a, e_d.
 template <bool kDev>
 __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, float n, float Jx, float Jy,
                                         float Fx, float Fy, float dnx, float dny, float divJ, float *fs,
@@ -286,23 +285,21 @@ __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, floa
   const float cxx = fmaf(A.th, fmaf(ux2, dnx, divJ), ux2 * Fx);
   const float cyy = fmaf(A.th, fmaf(uy2, dny, divJ), uy2 * Fy);
   const float cxy = fmaf(A.th, fmaf(ux, dny, uy * dnx), fmaf(ux, Fy, Fx * uy));
-  const float iso = fmaf(on, fmaf(ux, ux, uy * uy), A.g * (cxx + cyy));  // on u^2 + tr C
+  const float Sx = fmaf(onux, ux, A.g * cxx), Sy = fmaf(onuy, uy, A.g * cyy);
+  const float X = fmaf(onux, uy, A.g * cxy);
+  const float Sxy = Sx + Sy;  // on u^2 + tr C
   float ea, ed;
   if constexpr (kDev) {
-    ea = fmaf(on, A.A_ax * (1.f / 9.f), fmaf(-1.f / 6.f, iso, -wr_ax));
-    ed = fmaf(on, A.A_diag * (1.f / 36.f), fmaf(-1.f / 24.f, iso, -wr_dg));
+    ea = fmaf(on, A.A_ax * (1.f / 9.f), fmaf(-1.f / 6.f, Sxy, -wr_ax));
+    ed = fmaf(on, A.A_diag * (1.f / 36.f), fmaf(-1.f / 24.f, Sxy, -wr_dg));
   } else {
-    ea = fmaf(on, A.A_ax * (1.f / 9.f), iso * (-1.f / 6.f));
-    ed = fmaf(on, A.A_diag * (1.f / 36.f), iso * (-1.f / 24.f));
+    ea = fmaf(on, A.A_ax * (1.f / 9.f), Sxy * (-1.f / 6.f));
+    ed = fmaf(on, A.A_diag * (1.f / 36.f), Sxy * (-1.f / 24.f));
   }
-  const float g2 = 0.5f * A.g;
-  const float hx = fmaf(0.5f * onux, ux, fmaf(g2, cxx, ea));
-  const float hy = fmaf(0.5f * onuy, uy, fmaf(g2, cyy, ea));
-  const float X = fmaf(onux, uy, A.g * cxy);
+  const float hx = fmaf(0.5f, Sx, ea), hy = fmaf(0.5f, Sy, ea);
+  const float h5 = fmaf(0.125f, Sxy, fmaf(0.25f, X, ed)), h6 = fmaf(0.125f, Sxy, fmaf(-0.25f, X, ed));
   const float tx = fmaf(A.g, Fx, onux) * (1.f / 3.f);
   const float ty = fmaf(A.g, Fy, onuy) * (1.f / 3.f);
-  const float hd = fmaf(-0.5f, ea, ed), hxy = hx + hy;
-  const float h5 = fmaf(0.25f, hxy + X, hd), h6 = fmaf(0.25f, hxy - X, hd);
   const float t5 = 0.25f * (tx + ty), t6 = 0.25f * (ty - tx);
   const float om1 = A.one_minus_omega;
   fs[1] = fmaf(om1, f[1], hx + tx);
