@@ -152,6 +152,19 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype,
  * non-finite or any site's post-collision mass lies outside (0, 1/b).     */
 int lb_reduce(lb_handle *h, double *out);
 
+/* Asynchronous form of lb_reduce for monitoring every step without
+ * stalling: enqueues the same sums on the handle's stream and a copy of
+ * five doubles to the HOST array out[5]: out[0..2] as lb_reduce, out[3] =
+ * 1.0 if a population is non-finite or a site's mass lies outside (0, 1/b)
+ * (the condition lb_reduce reports as LB_ERR_UNSTABLE), else 0.0, out[4] =
+ * 1.0 if a device-side wait gave up or a layout check failed (lb_reduce's
+ * LB_ERR_TIMEOUT), else 0.0.  The values are there once the stream has
+ * been synchronised; out must stay valid until then and should be pinned
+ * (page-locked) memory -- with pageable memory the copy, and so the call,
+ * synchronises.  Several calls may be in flight with different out arrays.
+ * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA.                          */
+int lb_reduce_async(lb_handle *h, double *out);
+
 /* Checkpoint: copy the stored populations to the HOST buffer buf:
  * [9][ny][nx] elements of the storage precision (double for LB_FP64, float
  * for LB_FP32); for 16-bit storage the float rest plane [ny][nx] followed by

@@ -36,6 +36,7 @@ struct lb_handle {
   size_t cta_bytes = 0;
   int plan_gen = 0;              // bumped when the tiling or the record array changes
   bool cta_valid = false;        // d_cta describes the current state
+  bool total_valid = false;      // d_out holds the current state's sums (fused)
   int *d_err = nullptr;          // bounded-wait failure flag
   void *f[2] = {nullptr, nullptr};
   int cur = 0;
@@ -44,7 +45,8 @@ struct lb_handle {
   void *d_mom = nullptr;        // 3*S doubles, staging for host moments
   double *d_partials = nullptr; // reduction scratch
   int *d_flag = nullptr;
-  double *d_out = nullptr;
+  double *d_out = nullptr;       // 5 doubles: mass, J_x, J_y, unstable, wait error
+  unsigned *d_arrive = nullptr;  // CTA arrival counter of the fused sums
   int red_blocks = 0;
   int64_t step = 0;
   bool initialised = false;
@@ -150,9 +152,12 @@ reduce_pass1(const real_t *__restrict__ f, int nx, size_t S, int pitch, long lon
   if (bad) atomicOr(flag, 1);
 }
 
-// Pass 2: one block adds the block partials in a fixed order.
+// Pass 2: one block adds the block partials in a fixed order; out[3] and
+// out[4] receive the instability flag pass 1 raised and the step kernels'
+// wait/layout error flag (1.0 or 0.0).
 __global__ void __launch_bounds__(RED_THREADS)
-reduce_pass2(const double *__restrict__ partials, int nblocks, double *__restrict__ out) {
+reduce_pass2(const double *__restrict__ partials, int nblocks, double *__restrict__ out,
+             const int *__restrict__ flag, const int *__restrict__ err) {
   __shared__ double sm[3][RED_THREADS];
   double acc[3] = {0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblocks; b += RED_THREADS)
@@ -172,12 +177,15 @@ reduce_pass2(const double *__restrict__ partials, int nblocks, double *__restric
     out[0] = sm[0][0];
     out[1] = sm[1][0];
     out[2] = sm[2][0];
+    out[3] = *flag != 0 ? 1.0 : 0.0;
+    out[4] = *err != 0 ? 1.0 : 0.0;
   }
 }
 
-// Pass 2 over the sweep kernel's per-CTA records (mass, J_x, J_y, flag).
+// Pass 2 over the sweep kernel's per-CTA records (mass, J_x, J_y, flag);
+// out[3], out[4] as in reduce_pass2.
 __global__ void __launch_bounds__(RED_THREADS)
-reduce_cta(const double *__restrict__ cta, int nblocks, double *__restrict__ out, int *__restrict__ flag) {
+reduce_cta(const double *__restrict__ cta, int nblocks, double *__restrict__ out, const int *__restrict__ err) {
   __shared__ double sm[3][RED_THREADS];
   double acc[3] = {0.0, 0.0, 0.0};
   int bad = 0;
@@ -196,11 +204,13 @@ reduce_cta(const double *__restrict__ cta, int nblocks, double *__restrict__ out
     }
     __syncthreads();
   }
-  if (bad) atomicOr(flag, 1);
+  const int any_bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     out[0] = sm[0][0];
     out[1] = sm[1][0];
     out[2] = sm[2][0];
+    out[3] = any_bad ? 1.0 : 0.0;
+    out[4] = *err != 0 ? 1.0 : 0.0;
   }
 }
 
@@ -282,6 +292,8 @@ lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   A.partials = h->d_cta;
   A.records = 1;
   A.err = h->d_err;
+  A.total = nullptr;
+  A.arrivals = nullptr;
   return A;
 }
 
@@ -291,6 +303,7 @@ void set_segments(lb_handle *h, int seg_h) {
   h->sweep_seg = std::max(1, std::min(seg_h, h->p.ny));
   h->sweep_nseg = (h->p.ny + h->sweep_seg - 1) / h->sweep_seg;
   h->cta_valid = false;
+  h->total_valid = false;
   h->plan_gen++;
 }
 
@@ -306,6 +319,7 @@ cudaError_t ensure_records(lb_handle *h, int nseg) {
   h->d_cta = p;
   h->cta_bytes = need;
   h->cta_valid = false;
+  h->total_valid = false;
   h->plan_gen++;
   return cudaSuccess;
 }
@@ -385,7 +399,9 @@ int lb_create(const lb_params *p, lb_handle **out) {
   h->red_blocks = (int)std::min<size_t>((h->S + RED_THREADS - 1) / RED_THREADS, 1024);
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_partials, 3 * (size_t)h->red_blocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_flag, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_out, 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_out, 5 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_arrive, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->d_arrive, 0, sizeof(unsigned));
   if (e == cudaSuccess) {
     // sin(2 pi x / lambda), evaluated in FP64 on the host.
     const size_t nb = (size_t)p->nx * h->elem;
@@ -451,6 +467,7 @@ int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean, double noise
     if (e != cudaSuccess) return cuda_fail(h, e, "lb_init: 16-bit store");
   }
   h->cta_valid = false;
+  h->total_valid = false;
   if (mode == 1) LB_CUDA(h, cudaStreamSynchronize(h->st));
   h->step = 0;
   h->initialised = true;
@@ -475,11 +492,16 @@ int lb_step(lb_handle *h, int64_t nsteps) {
     for (int64_t k = 0; k < nsteps; k++) {
       lbk::SweepArgs A = sweep_args(h, (float *)h->f[h->cur ^ 1]);
       A.records = (k == nsteps - 1) ? 1 : 0;
+      if (A.records) {  // the last CTA also leaves the global sums in d_out
+        A.total = h->d_out;
+        A.arrivals = h->d_arrive;
+      }
       cudaError_t e = lbk::launch_sweep(h->store, h->tmap[h->cur][0], h->tmap[h->cur][1], A, h->sweep_smem, h->st);
       if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: sweep kernel");
       h->cur ^= 1;
       h->step++;
       h->cta_valid = true;
+      h->total_valid = A.records != 0;
     }
   } else {
     const StepArgs<float> A = make_args<float>(h);
@@ -525,16 +547,17 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_de
   return LB_OK;
 }
 
-int lb_reduce(lb_handle *h, double *out) {
-  if (!h || !out) return h ? fail(h, LB_ERR_ARG, "lb_reduce: null output") : LB_ERR_ARG;
-  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reduce: state not initialised");
+// Enqueue the global sums of the current state into d_out[0..4] (mass,
+// momentum x, y, instability flag, wait/layout error flag).
+static int enqueue_reduce(lb_handle *h) {
   const double nmax = h->p.b > 0.0 ? 1.0 / h->p.b : INFINITY;
-  LB_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
+  if (h->sweep && h->total_valid) return LB_OK;  // the last step's kernel left them there
   if (h->sweep && h->cta_valid) {
     // The last sweep step left one record per CTA (site sums in FP32,
     // totals in FP64): only the final pass remains.
-    reduce_cta<<<1, RED_THREADS, 0, h->st>>>(h->d_cta, h->sweep_nstrips * h->sweep_nseg, h->d_out, h->d_flag);
+    reduce_cta<<<1, RED_THREADS, 0, h->st>>>(h->d_cta, h->sweep_nstrips * h->sweep_nseg, h->d_out, h->d_err);
   } else {
+    LB_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
     if (fp64(h))
       reduce_pass1<double><<<h->red_blocks, RED_THREADS, 0, h->st>>>(
           (const double *)h->f[h->cur], h->p.nx, h->S, h->pitch, h->plane, h->off, nmax,
@@ -546,20 +569,38 @@ int lb_reduce(lb_handle *h, double *out) {
           f32, h->p.nx, h->S, h->pitch, h->plane, h->off, nmax, h->d_partials, h->d_flag);
     }
     LB_CUDA(h, cudaGetLastError());
-    reduce_pass2<<<1, RED_THREADS, 0, h->st>>>(h->d_partials, h->red_blocks, h->d_out);
+    reduce_pass2<<<1, RED_THREADS, 0, h->st>>>(h->d_partials, h->red_blocks, h->d_out, h->d_flag, h->d_err);
   }
   LB_CUDA(h, cudaGetLastError());
-  int flag = 0, werr = 0;
-  LB_CUDA(h, cudaMemcpyAsync(out, h->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  LB_CUDA(h, cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-  LB_CUDA(h, cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  return LB_OK;
+}
+
+int lb_reduce(lb_handle *h, double *out) {
+  if (!h || !out) return h ? fail(h, LB_ERR_ARG, "lb_reduce: null output") : LB_ERR_ARG;
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reduce: state not initialised");
+  const int rc = enqueue_reduce(h);
+  if (rc != LB_OK) return rc;
+  double r[5];
+  LB_CUDA(h, cudaMemcpyAsync(r, h->d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   LB_CUDA(h, cudaStreamSynchronize(h->st));
-  if (werr) return fail(h, LB_ERR_TIMEOUT, "lb_reduce: a device-side wait gave up or a layout check failed during a step");
-  if (flag) {
+  out[0] = r[0];
+  out[1] = r[1];
+  out[2] = r[2];
+  if (r[4] != 0.0) return fail(h, LB_ERR_TIMEOUT, "lb_reduce: a device-side wait gave up or a layout check failed during a step");
+  if (r[3] != 0.0) {
     char m[128];
     snprintf(m, sizeof m, "lb_reduce: non-finite or out-of-range density at step %lld", (long long)h->step);
     return fail(h, LB_ERR_UNSTABLE, m);
   }
+  return LB_OK;
+}
+
+int lb_reduce_async(lb_handle *h, double *out) {
+  if (!h || !out) return h ? fail(h, LB_ERR_ARG, "lb_reduce_async: null output") : LB_ERR_ARG;
+  if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_reduce_async: state not initialised");
+  const int rc = enqueue_reduce(h);
+  if (rc != LB_OK) return rc;
+  LB_CUDA(h, cudaMemcpyAsync(out, h->d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   return LB_OK;
 }
 
@@ -623,6 +664,7 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step) {
   }
   LB_CUDA(h, cudaStreamSynchronize(h->st));
   h->cta_valid = false;
+  h->total_valid = false;
   h->step = step;
   h->initialised = true;
   return LB_OK;
@@ -646,6 +688,7 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   // Per-CTA records sized for the smallest segments (kept afterwards).
   LB_CUDA(h, ensure_records(h, max_nseg));
   h->cta_valid = false;
+  h->total_valid = false;
 
   const size_t buf_bytes = lbk::sweep_buffer_bytes(h->store, h->plane);
   const int cur0 = h->cur;
@@ -721,6 +764,7 @@ int lb_destroy(lb_handle *h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_flag);
   cudaFree(h->d_out);
+  cudaFree(h->d_arrive);
   cudaFree(h->d_cta);
   cudaFree(h->d_err);
   cudaFree(h->wide);
@@ -936,6 +980,7 @@ int lb_batch_step(lb_batch *b, int64_t nsteps) {
     h->cur ^= (int)(nsteps & 1);
     h->step += nsteps;
     h->cta_valid = true;
+    h->total_valid = false;
   }
   return LB_OK;
 }

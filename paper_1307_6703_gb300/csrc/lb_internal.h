@@ -32,6 +32,12 @@ struct SweepArgs {
   double *partials;            // 4 doubles per CTA: mass, J_x, J_y, bad-site flag
   int records;                 // write the per-CTA records (0: skip them)
   int *err;                    // set when a bounded wait gave up
+  // Non-null (single-lattice launches with records only): the last CTA to
+  // finish sums every CTA's record in a fixed order into total[0..4] --
+  // mass, J_x, J_y, 1.0 if any record flags a bad site, 1.0 if *err is set
+  // -- and resets *arrivals (a counter that is zero between launches).
+  double *total;
+  unsigned *arrivals;
 };
 
 // Storage formats of the sweep kernel (values of lb_precision).

@@ -152,7 +152,7 @@ struct __align__(128) SweepSmem {
   float2 J[2][2][kCols];   // (n u*_x, n u*_y)
   unsigned long long full[kPairs];
   static_assert(SlotBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
-  static_assert(kPairs * SlotBytes >= (int)sizeof(double) * 4 * kThreads,
+  static_assert(kPairs * SlotBytes >= (int)(sizeof(double) * 4 * kThreads + sizeof(unsigned)),
                 "the end-of-kernel reduction reuses the population ring");
 };
 static_assert(offsetof(SweepSmem<StoreF32::kSlotBytes>, pops) == 0, "the ring starts the (128-byte aligned) block");
@@ -709,6 +709,50 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
     if (t == 0) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) rec[q] = v[q];
+    }
+  }
+  if (A.total == nullptr) return;
+
+  // The last CTA to finish sums every CTA's record (FP64, fixed order:
+  // thread t takes records t, t + 124, ..., then warp 0's tree), so the
+  // global sums of the new state need no further kernel.
+  const unsigned nrec = gridDim.x * gridDim.y;
+  unsigned *last = reinterpret_cast<unsigned *>(red + 4 * kThreads);
+  if (t == 0) {
+    __threadfence();  // this CTA's record before its arrival
+    *last = (atomicAdd(A.arrivals, 1u) == nrec - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (*last == 0u) return;
+  __threadfence();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (unsigned b = t; b < nrec; b += kThreads) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += __ldcg(A.partials + 4 * (size_t)b + q);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q * kThreads + t] = acc[q];
+  __syncthreads();
+  if (t < 32) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double sum = 0.0;
+      for (int i = t; i < kThreads; i += 32) sum += red[q * kThreads + i];
+      v[q] = sum;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    }
+    if (t == 0) {
+      A.total[0] = v[0];
+      A.total[1] = v[1];
+      A.total[2] = v[2];
+      A.total[3] = v[3] != 0.0 ? 1.0 : 0.0;
+      A.total[4] = __ldcg(A.err) != 0 ? 1.0 : 0.0;
+      *A.arrivals = 0u;
     }
   }
 }

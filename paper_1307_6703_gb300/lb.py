@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_step.argtypes = [P, C.c_int64]
         lib.lb_moments.argtypes = [P, P, P, P, C.c_int, C.c_int]
         lib.lb_reduce.argtypes = [P, C.POINTER(C.c_double)]
+        lib.lb_reduce_async.argtypes = [P, P]
         lib.lb_get_state.argtypes = [P, P, C.POINTER(C.c_size_t)]
         lib.lb_set_state.argtypes = [P, P, C.c_size_t, C.c_int64]
         lib.lb_get_step.argtypes = [P, C.POINTER(C.c_int64)]
@@ -151,6 +152,13 @@ def lb_reduce(h, out=None):
     if out is not None:
         out[:] = vals
     return rc, vals
+
+
+def lb_reduce_async(h, out) -> None:
+    """Enqueue the sums of lb_reduce and their copy into `out`, five HOST
+    doubles (mass, momx, momy, unstable flag, wait/layout error flag) --
+    a pinned torch tensor or a numpy array; valid after a stream sync."""
+    _check(load_library().lb_reduce_async(h, _addr(out)), h)
 
 
 def lb_get_state(h, buf=None) -> int:

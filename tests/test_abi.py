@@ -76,6 +76,7 @@ def test_null_handles_are_refused_without_gpu(lib):
     """Entry points given a NULL handle return LB_ERR_ARG before any CUDA call."""
     from paper_1307_6703_gb300 import LB_ERR_ARG
     assert lib.lb_set_seg_h(None, 64) == LB_ERR_ARG
+    assert lib.lb_reduce_async(None, None) == LB_ERR_ARG
     assert lib.lb_step(None, 1) == LB_ERR_ARG
 
 

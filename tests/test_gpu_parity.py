@@ -237,6 +237,38 @@ def test_instability_is_reported():
         x.close()
 
 
+def test_reduce_async_matches_reduce():
+    """lb_reduce_async: one record per step into a pinned ring, read after
+    one synchronisation -- the same sums as lb_reduce (same kernels, so bit
+    for bit on the same state), mass conserved step by step, flags clear;
+    a poisoned state raises its instability flag without stalling."""
+    import torch
+    from paper_1307_6703_gb300 import lb_reduce_async
+    w = C2(0.05).with_(nx=256, ny=128)
+    s = solver_for(w, LB_FP32).init_noise(2, w.rho_mean, w.noise)
+    ring = torch.zeros((6, 5), dtype=torch.float64).pin_memory()
+    lb_reduce_async(s.h, ring[0])
+    for k in range(1, 6):
+        s.step(7)
+        lb_reduce_async(s.h, ring[k])
+    torch.cuda.synchronize()
+    r = ring.numpy().copy()
+    rc, vals = s.reduce()
+    assert rc == 0 and list(r[5, :3]) == vals
+    assert np.all(np.abs(r[:, 0] - r[0, 0]) <= 1e-6 * r[0, 0])
+    assert np.all(r[:, 3:] == 0.0)
+    s.close()
+    n0 = noise_field(C1.with_(nx=32, ny=16))
+    n0[3, 5] = np.nan
+    bad = solver_for(C1.with_(nx=32, ny=16), LB_FP32).init_fields(n0).step(3)
+    out = torch.zeros(5, dtype=torch.float64).pin_memory()
+    lb_reduce_async(bad.h, out)
+    torch.cuda.synchronize()
+    assert out[3].item() == 1.0 and out[4].item() == 0.0
+    assert bad.reduce()[0] == LB_ERR_UNSTABLE
+    bad.close()
+
+
 def test_moments_to_device_and_stream():
     """lb_moments writes device pointers (torch tensors) on a torch stream
     and agrees with the host path."""
