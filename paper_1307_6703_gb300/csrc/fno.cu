@@ -270,16 +270,13 @@ __global__ void project_back_kernel(const float *__restrict__ hp, const float *_
 
 // Two-pass per-channel sums over (b, s), deterministic: pass 1 gives each
 // of nb blocks per channel a contiguous share (FP32 per thread, FP64 block
-// tree), pass 2 adds the nb partials of a channel in order.
-//   kind 0: sum a[b, ch, s]                        (a has C channels)
-//   kind 1: sum a[b, j, s] gelu(o2[b, k, s])       (ch = j*C2 + k; a has C, o2 has C2 channels)
-//   kind 2: sum a[b, o, s] o2[b, c, s]             (ch = o*C2 + c; a has C, o2 has C2 channels)
+// tree) of sum a[b, ch, s] (a has C channels), pass 2 adds the nb partials
+// of a channel in order.
 constexpr int kReduceBlocks = 32;
-__global__ void reduce_pass1_kernel(int kind, const float *__restrict__ a, const float *__restrict__ o2, int B, int C,
-                                    int C2, long long S, double *__restrict__ part) {
+constexpr int kOuterBlocks = 64;  // site shares of outer_pass1_kernel
+__global__ void reduce_pass1_kernel(const float *__restrict__ a, int B, int C, long long S, double *__restrict__ part) {
   __shared__ double sm[kThreads];
   const int ch = blockIdx.x, blk = blockIdx.y;
-  const int ca = kind == 0 ? ch : ch / C2, cb = kind == 0 ? 0 : ch % C2;
   const long long n = (long long)B * S, per = (n + gridDim.y - 1) / gridDim.y;
   const long long lo = blk * per, hi = min(n, lo + per);
   float acc = 0.f;
@@ -291,14 +288,73 @@ __global__ void reduce_pass1_kernel(int kind, const float *__restrict__ a, const
       s -= S;
       b++;
     }
-    const float av = a[((long long)b * C + ca) * S + s];
-    if (kind == 0) acc += av;
-    else if (kind == 1) acc += av * gelu(o2[((long long)b * C2 + cb) * S + s]);
-    else acc += av * o2[((long long)b * C2 + cb) * S + s];
+    acc += a[((long long)b * C + ch) * S + s];
     s += blockDim.x;
   }
   const double r = block_sum((double)acc, sm);
   if (threadIdx.x == 0) part[(long long)ch * gridDim.y + blk] = r;
+}
+
+// Weight gradients that are per-site outer products, pass 1 without
+// re-reading the operands per channel pair: block (x, y) takes x's contiguous share of the
+// (b, s) sites and tile y of NA x NB channel pairs (ca, cb); each thread
+// keeps the tile's NA*NB sums of a[b, ca, s] f(o2[b, cb, s]) in FP32 (f =
+// gelu or identity, evaluated once per (cb, site) of the tile), then the
+// block adds them in a fixed order -- FP32 warp trees (FP64 throughput is
+// low on this part), the warps' sums in FP64 -- into
+// part[(ca * Cb + cb) * gridDim.x + x], the layout of pass 2.
+template <int NA, int NB, bool kGelu>
+__global__ void __launch_bounds__(kThreads)
+outer_pass1_kernel(const float *__restrict__ a, const float *__restrict__ o2, int B, int Ca, int Cb, long long S,
+                   double *__restrict__ part) {
+  __shared__ double sm[kThreads / 32][NA * NB];
+  const int ntb = (Cb + NB - 1) / NB;
+  const int ca0 = (blockIdx.y / ntb) * NA, cb0 = (blockIdx.y % ntb) * NB;
+  float acc[NA][NB];
+#pragma unroll
+  for (int i = 0; i < NA; i++)
+#pragma unroll
+    for (int j = 0; j < NB; j++) acc[i][j] = 0.f;
+  const long long n = (long long)B * S, per = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * per, hi = min(n, lo + per);
+  long long e = lo + threadIdx.x;
+  long long b = e / S, s = e - b * S;  // then advanced without dividing
+  for (; e < hi; e += blockDim.x, s += blockDim.x) {
+    while (s >= S) {
+      s -= S;
+      b++;
+    }
+    float av[NA], bv[NB];
+#pragma unroll
+    for (int i = 0; i < NA; i++) av[i] = ca0 + i < Ca ? a[(b * Ca + ca0 + i) * S + s] : 0.f;
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+      const float v = cb0 + j < Cb ? o2[(b * Cb + cb0 + j) * S + s] : 0.f;
+      bv[j] = kGelu ? gelu(v) : v;
+    }
+#pragma unroll
+    for (int i = 0; i < NA; i++)
+#pragma unroll
+      for (int j = 0; j < NB; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NA; i++)
+#pragma unroll
+    for (int j = 0; j < NB; j++) {
+      float v = acc[i][j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sm[w][i * NB + j] = (double)v;
+    }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NA * NB; p += blockDim.x) {
+    const int i = p / NB, j = p % NB;
+    if (ca0 + i >= Ca || cb0 + j >= Cb) continue;
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; k++) t += sm[k][p];
+    part[((long long)(ca0 + i) * Cb + cb0 + j) * gridDim.x + blockIdx.x] = t;
+  }
 }
 
 __global__ void reduce_pass2_kernel(const double *__restrict__ part, int nch, int nb, float *__restrict__ out) {
@@ -530,11 +586,21 @@ cublasStatus_t gemm(fno_handle *h, bool tA, bool tB, int m, int n, int k, const 
                                     CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
 }
 
-// out[ch] for nch channels of a per-channel sum (kinds: reduce_pass1_kernel).
-void chan_reduce(fno_handle *h, int kind, const float *a, const float *o2, int B, int C, int C2, long long S, int nch,
-                 float *out) {
-  reduce_pass1_kernel<<<dim3(nch, kReduceBlocks), kThreads, 0, h->st>>>(kind, a, o2, B, C, C2, S, h->rpart);
-  reduce_pass2_kernel<<<(nch + kThreads - 1) / kThreads, kThreads, 0, h->st>>>(h->rpart, nch, kReduceBlocks, out);
+// out[ch] = sum over (b, s) of a[b, ch, s] for the C channels of a.
+void chan_reduce(fno_handle *h, const float *a, int B, int C, long long S, float *out) {
+  reduce_pass1_kernel<<<dim3(C, kReduceBlocks), kThreads, 0, h->st>>>(a, B, C, S, h->rpart);
+  reduce_pass2_kernel<<<(C + kThreads - 1) / kThreads, kThreads, 0, h->st>>>(h->rpart, C, kReduceBlocks, out);
+}
+
+// out[ca * Cb + cb] = sum over (b, s) of a[b, ca, s] f(o2[b, cb, s]) (f = gelu
+// for the projection's Q2, identity for the lift's P), in the order of
+// outer_pass1_kernel and reduce_pass2_kernel.
+template <int NA, int NB, bool kGelu>
+void outer_reduce(fno_handle *h, const float *a, const float *o2, int B, int Ca, int Cb, long long S, float *out) {
+  const int tiles = ((Ca + NA - 1) / NA) * ((Cb + NB - 1) / NB);
+  outer_pass1_kernel<NA, NB, kGelu><<<dim3(kOuterBlocks, tiles), kThreads, 0, h->st>>>(a, o2, B, Ca, Cb, S, h->rpart);
+  reduce_pass2_kernel<<<(Ca * Cb + kThreads - 1) / kThreads, kThreads, 0, h->st>>>(h->rpart, Ca * Cb, kOuterBlocks,
+                                                                                   out);
 }
 
 template <typename T>
@@ -595,8 +661,8 @@ cudaError_t alloc_workspace(fno_handle *h) {
   if (e == cudaSuccess) e = alloc(&h->dS, h->cap_modes);
   if (e == cudaSuccess) e = alloc(&h->partial, 8192);
   if (e == cudaSuccess)
-    e = alloc(&h->rpart, (long long)std::max(c.width * kFeatures, std::max(c.hidden * c.outputs, c.hidden)) * kReduceBlocks +
-                             (long long)c.width * kReduceBlocks);
+    e = alloc(&h->rpart, std::max((long long)std::max(c.width * kFeatures, c.hidden * c.outputs) * kOuterBlocks,
+                                  (long long)std::max(std::max(c.width, c.hidden), c.outputs) * kReduceBlocks));
   if (e == cudaSuccess) e = alloc(&h->wpart, B * (long long)std::max(c.width, c.hidden) * c.width);
   if (e == cudaSuccess) e = alloc(&h->loss, 1);
   if (e == cudaSuccess) e = alloc(&h->Fx, (long long)c.nx_max * 2 * c.modes_x);
@@ -743,10 +809,10 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
   loss_kernel<<<lb, kThreads, 0, st>>>(h->out, target, BS, h->dout, h->partial);
   finish_loss_kernel<<<1, kThreads, 0, st>>>(h->partial, (int)lb, BS, h->loss);
   // projection: dq2, dQ2, dhp, dq1, dQ1, dV = Q1^T dhp
-  chan_reduce(h, 0, h->dout, nullptr, B, O, 1, S, O, g + o.q2);
-  chan_reduce(h, 1, h->dout, h->hp, B, O, H, S, O * H, g + o.Q2);
+  chan_reduce(h, h->dout, B, O, S, g + o.q2);
+  outer_reduce<kMaxOutputs, 8, true>(h, h->dout, h->hp, B, O, H, S, g + o.Q2);
   project_back_kernel<<<grid2(S, B * H), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, O, S, h->dhp, h->dhpb);
-  chan_reduce(h, 0, h->dhp, nullptr, B, H, 1, S, H, g + o.q1);
+  chan_reduce(h, h->dhp, B, H, S, g + o.q1);
   FNO_CUDA(h, cudaGetLastError());
   // dQ1 = sum_b dhp[b] v_L[b]^T: one batched GEMM into per-field parts, then their sum
   FNO_BLAS(h, gemm(h, false, true, H, C, (int)S, h->dhp, h->dhpb, (int)S, (long long)H * S, h->V[L], h->Vb[L], (int)S,
@@ -756,7 +822,7 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
                    (long long)H * S, h->dV, (int)S, (long long)C * S, B, 0.f));
   for (int l = L - 1; l >= 0; l--) {
     act_back_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->dV, h->Z[l], BCS, l < L - 1 ? 1 : 0, h->dZ, h->dZb);
-    chan_reduce(h, 0, h->dZ, nullptr, B, C, 1, S, C, g + o.w[l]);
+    chan_reduce(h, h->dZ, B, C, S, g + o.w[l]);
     FNO_CUDA(h, cudaGetLastError());
     // dW = sum_b dz[b] v[b]^T
     FNO_BLAS(h, gemm(h, false, true, C, C, (int)S, h->dZ, h->dZb, (int)S, (long long)C * S, h->V[l], h->Vb[l], (int)S,
@@ -777,8 +843,8 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
                      1.f));
   }
   // lift: dp = sum dv0, dP[o, c] = sum dv0[b, o, s] x0[b, c, s]
-  chan_reduce(h, 0, h->dV, nullptr, B, C, 1, S, C, g + o.p);
-  chan_reduce(h, 2, h->dV, h->x0, B, C, kFeatures, S, C * kFeatures, g + o.P);
+  chan_reduce(h, h->dV, B, C, S, g + o.p);
+  outer_reduce<8, kFeatures, false>(h, h->dV, h->x0, B, C, kFeatures, S, g + o.P);
   FNO_CUDA(h, cudaGetLastError());
   if (loss) {
     FNO_CUDA(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
