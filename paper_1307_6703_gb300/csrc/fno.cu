@@ -269,13 +269,13 @@ __global__ void project_back_kernel(const float *__restrict__ hp, const float *_
 }
 
 // Two-pass per-channel sums over (b, s), deterministic: pass 1 gives each
-// of nb blocks per channel a contiguous share (FP32 per thread, FP64 block
-// tree) of sum a[b, ch, s] (a has C channels), pass 2 adds the nb partials
-// of a channel in order.
+// of nb blocks per channel a contiguous share of sum a[b, ch, s] (a has C
+// channels; FP32 per thread and in the warp trees, the warps' sums added in
+// FP64 in order), pass 2 adds the nb partials of a channel in order.
 constexpr int kReduceBlocks = 32;
 constexpr int kOuterBlocks = 64;  // site shares of outer_pass1_kernel
 __global__ void reduce_pass1_kernel(const float *__restrict__ a, int B, int C, long long S, double *__restrict__ part) {
-  __shared__ double sm[kThreads];
+  __shared__ double ws[kThreads / 32];
   const int ch = blockIdx.x, blk = blockIdx.y;
   const long long n = (long long)B * S, per = (n + gridDim.y - 1) / gridDim.y;
   const long long lo = blk * per, hi = min(n, lo + per);
@@ -291,8 +291,15 @@ __global__ void reduce_pass1_kernel(const float *__restrict__ a, int B, int C, l
     acc += a[((long long)b * C + ch) * S + s];
     s += blockDim.x;
   }
-  const double r = block_sum((double)acc, sm);
-  if (threadIdx.x == 0) part[(long long)ch * gridDim.y + blk] = r;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < kThreads / 32; w++) r += ws[w];
+    part[(long long)ch * gridDim.y + blk] = r;
+  }
 }
 
 // Weight gradients that are per-site outer products, pass 1 without
