@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -39,9 +40,16 @@ PROFILE = {"fp32": os.path.join(ROOT, "profiles", "lb_step_sweep_fp32_4096x1024.
 
 
 def kernel_source_digest() -> str:
+    """Digest of the step kernel's code: the source with comments and
+    whitespace removed, so that a profile stays attached to the code it
+    measured across comment edits."""
     import hashlib
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    with open(KERNEL_SRC, encoding="utf-8") as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = re.sub(r"\s+", " ", src).strip()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def profiled_traffic(precision: str):
@@ -56,7 +64,8 @@ def profiled_traffic(precision: str):
     digest, traffic = None, None
     for line in text.splitlines():
         if line.startswith("kernel source digest:"):
-            digest = line.split(":", 1)[1].strip().strip("`")
+            m = re.search(r"`([0-9a-f]+)`", line)
+            digest = m.group(1) if m else None
         if line.startswith("dram bytes per launch:"):
             traffic = float(line.split(":", 1)[1].split()[0])
     return traffic if digest == kernel_source_digest() else None

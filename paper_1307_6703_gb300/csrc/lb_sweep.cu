@@ -10,10 +10,11 @@
 // per iteration.  Every row of the previous state is read from HBM once by
 // the TMA engine: tensor copies bring a pair of rows of all nine population
 // planes into a 5-slot ring in shared memory (one mbarrier per slot, waits
-// bounded), two pairs ahead of use.
+// bounded): pair k+2 is requested as iteration k starts, into the slot that
+// iteration k-1 freed, and first read in iteration k+1.
 //
-// Iteration k (a = ya - 3 + 2k) runs four stages, separated by CTA barriers,
-// each on two rows:
+// Iteration k (a = ya - 3 + 2k) runs four stages, separated by CTA barriers
+// (and preceded by one that frees the oldest ring slot), each on two rows:
 //   A  rows a, a+1     : propagated populations (pull), density n (n-hat on
 //                        walls), raw momentum sum_i f_i c_i      -> n ring
 //   B  rows a-1, a     : P = p^i - p^w (Eq. eqstate), L = lap n  -> P/L ring
@@ -145,8 +146,8 @@ using StoreFP16 = StoreDev<__half>;
 template <int SlotBytes>
 struct __align__(128) SweepSmem {
   unsigned char pops[kPairs][SlotBytes];  // one row pair of every plane per slot
-  // four pairs: stage A of iteration k+1 writes pair k+1 while stage D of
-  // iteration k (no barrier in between) may still read pairs k-2 and k-1
+  // four pairs: stage A of iteration k+1 writes pair k+1 into a slot that
+  // stage D of iteration k (pairs k-2 and k-1) does not read
   float n[4][2][kCols];
   float2 PL[2][2][kCols];  // (P, lap n): one 64-bit load per stencil tap
   float2 J[2][2][kCols];   // (n u*_x, n u*_y)
@@ -442,8 +443,6 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       for (int j = 0; j < 2; ++j)
         if (nw[j]) S.n[s3][j][t] = nv[j];
       __syncthreads();
-      // The slot of pair k-3 is free (last used by iteration k-1): refill it
-      // with pair k+2.
 
       // -------------------------------------- B: rows a-1, a -- P, lap n
       {

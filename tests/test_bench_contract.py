@@ -40,3 +40,18 @@ def test_reference_arm_other_ranks_print_nothing():
 def test_warmup_below_three_is_refused():
     r = _bench("--impl", "reference", "--steps", "1", "--warmup", "2")
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_kernel_digest_ignores_comments_only(tmp_path, monkeypatch):
+    """The digest that ties a committed profile to the kernel source changes
+    with the code, not with its comments or layout."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(bench.KERNEL_SRC, encoding="utf-8").read()
+    base = bench.kernel_source_digest()
+    p = tmp_path / "k.cu"
+    p.write_text("// a new comment\n" + src.replace("\n", "\n\n", 3) + "\n/* trailing\n block */\n")
+    monkeypatch.setattr(bench, "KERNEL_SRC", str(p))
+    assert bench.kernel_source_digest() == base
+    p.write_text(src.replace("kWaitLimit = 1u << 22", "kWaitLimit = 1u << 21"))
+    assert bench.kernel_source_digest() != base
