@@ -319,7 +319,7 @@ def run_ours(args):
                     "steps": k_e2e, "per_step_records_ok": e2e_ok},
             "gpu_launches": args.steps,
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # the host baseline is an N = 1 figure
             mlups, nth, sample = cpu_oracle_mlups(w, args.cpu_seconds, 64)
             line["cpu_baseline"] = {"value": round(mlups, 3), "unit": "MLUPS", "cores": nth,
                                     "kind": "oracle", "sample": sample}
