@@ -13,7 +13,7 @@ from gpu_util import dev16_solver, oracle_for, rel_err, solver_for
 
 pytestmark = pytest.mark.gpu
 
-from paper_1307_6703_gb300 import LB_BF16DEV, LB_FP32, Batch  # noqa: E402
+from paper_1307_6703_gb300 import LB_BF16DEV, LB_FP16DEV, LB_FP32, Batch  # noqa: E402
 from paper_1307_6703_gb300.workloads import batch_workloads, noise_field  # noqa: E402
 
 
@@ -58,7 +58,7 @@ def _same(a, b, steps=10):
     return rel_err(sa, sb.astype(np.float64)) <= 2e-6 * max(1.0, steps / 10)
 
 
-@pytest.mark.parametrize("prec", [LB_FP32, LB_BF16DEV], ids=["fp32", "bf16dev"])
+@pytest.mark.parametrize("prec", [LB_FP32, LB_BF16DEV, LB_FP16DEV], ids=["fp32", "bf16dev", "fp16dev"])
 def test_batch_matches_instances_alone(prec):
     ws = _ensemble(7, prec)
     alone, batch = _make(ws, prec)

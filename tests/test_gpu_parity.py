@@ -237,15 +237,18 @@ def test_instability_is_reported():
         x.close()
 
 
-def test_reduce_async_matches_reduce():
+@pytest.mark.parametrize("storage", ["fp32", "bf16dev"])
+def test_reduce_async_matches_reduce(storage):
     """lb_reduce_async: one record per step into a pinned ring, read after
     one synchronisation -- the same sums as lb_reduce (same kernels, so bit
     for bit on the same state), mass conserved step by step, flags clear;
     a poisoned state raises its instability flag without stalling."""
     import torch
-    from paper_1307_6703_gb300 import lb_reduce_async
+    from gpu_util import dev16_solver
+    from paper_1307_6703_gb300 import LB_BF16DEV, lb_reduce_async
     w = C2(0.05).with_(nx=256, ny=128)
-    s = solver_for(w, LB_FP32).init_noise(2, w.rho_mean, w.noise)
+    s = (solver_for(w, LB_FP32) if storage == "fp32" else dev16_solver(w, LB_BF16DEV, 1.0))
+    s.init_noise(2, w.rho_mean, w.noise)
     ring = torch.zeros((6, 5), dtype=torch.float64).pin_memory()
     lb_reduce_async(s.h, ring[0])
     for k in range(1, 6):
