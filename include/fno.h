@@ -5,8 +5,8 @@
  * lattice Boltzmann solver (include/lb.h) -- density and velocity,
  * `outputs` channels -- used as its initial condition.  The paper has no
  * counterpart: its steady states come from running the scheme of Sec. II;
- * the network only shortens that run, and the solver remains the judge of
- * the result.
+ * the network only shortens that run, and the solver's own run still
+ * decides the result.
  *
  * Network (all sizes from fno_config; FP32 parameters and activations,
  * GEMMs in BF16 with FP32 accumulation unless gemm_bf16 = 0):

@@ -5,8 +5,8 @@ steady state that decides whether the network helps.
 Every step of the physics runs in the lattice Boltzmann library and every
 step of the network in its CUDA kernels; this module only moves buffers and
 loops.  The plain solver from a noisy uniform state is both the fallback and
-the judge: a predicted field is only an initial condition, and the state it
-leads to is the solver's.
+the arbiter: a predicted field is only an initial condition, and the state
+it leads to is the solver's.
 
 Steady state (the criterion used throughout): the maximum change of the
 density and of the velocity over 1000 steps is below STEADY_TOL, measured

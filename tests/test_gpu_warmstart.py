@@ -1,7 +1,7 @@
 """Learned warm start, end to end on the GPU: training data from the solver
 (noisy quenches run to their steady striped states at 256x64 and 512x128),
 the network trained by its own CUDA forward/backward/Adam kernels, and the
-plain solver as judge -- steps until the density and velocity stop changing
+plain solver as arbiter -- steps until the density and velocity stop changing
 (max change < 1e-4 per 1000 steps), from the predicted fields against from a
 noisy uniform state, on held-out parameter draws at 512x128.  The network
 must shorten the run on average; the state reached is the solver's own
