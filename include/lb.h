@@ -165,6 +165,20 @@ int lb_reduce(lb_handle *h, double *out);
  * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA.                          */
 int lb_reduce_async(lb_handle *h, double *out);
 
+/* Step-by-step monitoring with no call per step: register a HOST ring of
+ * `capacity` records of six doubles in page-locked memory the device can
+ * address (cudaHostAlloc, or a pinned torch tensor); host_ring = NULL or
+ * capacity = 0 switches it off.  While it is set, every sweep step computes
+ * the sums of lb_reduce and its kernel writes record (s mod capacity) =
+ * {mass, momentum x, momentum y, unstable flag, wait/layout error flag, s}
+ * straight into host memory, s being the step number after that step.  The
+ * records of the steps enqueued so far are complete once the stream has
+ * been synchronised; the ring must stay allocated while monitoring is on.
+ * Strip-sweep handles only (FP32 and 16-bit storage, not inside a batch).
+ * Errors: LB_ERR_ARG (other handles, capacity < 0, memory the device cannot
+ * address).                                                               */
+int lb_monitor(lb_handle *h, double *host_ring, int32_t capacity);
+
 /* Checkpoint: copy the stored populations to the HOST buffer buf:
  * [9][ny][nx] elements of the storage precision (double for LB_FP64, float
  * for LB_FP32); for 16-bit storage the float rest plane [ny][nx] followed by

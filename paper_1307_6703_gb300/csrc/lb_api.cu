@@ -47,6 +47,9 @@ struct lb_handle {
   int *d_flag = nullptr;
   double *d_out = nullptr;       // 5 doubles: mass, J_x, J_y, unstable, wait error
   unsigned *d_arrive = nullptr;  // CTA arrival counter of the fused sums
+  double *mon_ring = nullptr;    // device address of the monitoring ring (lb_monitor)
+  int mon_cap = 0;
+  bool in_batch = false;         // instance of an lb_batch
   int red_blocks = 0;
   int64_t step = 0;
   bool initialised = false;
@@ -294,6 +297,8 @@ lbk::SweepArgs sweep_args(const lb_handle *h, float *fout) {
   A.err = h->d_err;
   A.total = nullptr;
   A.arrivals = nullptr;
+  A.monitor = nullptr;
+  A.mon_step = 0.0;
   return A;
 }
 
@@ -491,10 +496,16 @@ int lb_step(lb_handle *h, int64_t nsteps) {
     // only the current state's.
     for (int64_t k = 0; k < nsteps; k++) {
       lbk::SweepArgs A = sweep_args(h, (float *)h->f[h->cur ^ 1]);
-      A.records = (k == nsteps - 1) ? 1 : 0;
+      // records on the last step, or on every step while monitoring
+      A.records = (k == nsteps - 1 || h->mon_cap > 0) ? 1 : 0;
       if (A.records) {  // the last CTA also leaves the global sums in d_out
         A.total = h->d_out;
         A.arrivals = h->d_arrive;
+      }
+      if (h->mon_cap > 0) {
+        const int64_t s = h->step + 1;
+        A.monitor = h->mon_ring + 6 * (s % h->mon_cap);
+        A.mon_step = (double)s;
       }
       cudaError_t e = lbk::launch_sweep(h->store, h->tmap[h->cur][0], h->tmap[h->cur][1], A, h->sweep_smem, h->st);
       if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: sweep kernel");
@@ -601,6 +612,27 @@ int lb_reduce_async(lb_handle *h, double *out) {
   const int rc = enqueue_reduce(h);
   if (rc != LB_OK) return rc;
   LB_CUDA(h, cudaMemcpyAsync(out, h->d_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  return LB_OK;
+}
+
+int lb_monitor(lb_handle *h, double *host_ring, int32_t capacity) {
+  if (!h) return LB_ERR_ARG;
+  if (capacity < 0) return fail(h, LB_ERR_ARG, "lb_monitor: capacity < 0");
+  if (!host_ring || capacity == 0) {
+    h->mon_ring = nullptr;
+    h->mon_cap = 0;
+    return LB_OK;
+  }
+  if (!h->sweep || h->in_batch)
+    return fail(h, LB_ERR_ARG, "lb_monitor: only for strip-sweep handles outside a batch");
+  void *dev = nullptr;
+  const cudaError_t e = cudaHostGetDevicePointer(&dev, host_ring, 0);
+  if (e != cudaSuccess || !dev) {
+    cudaGetLastError();  // clear the error state of the call
+    return fail(h, LB_ERR_ARG, "lb_monitor: the ring is not page-locked memory the device can address");
+  }
+  h->mon_ring = static_cast<double *>(dev);
+  h->mon_cap = capacity;
   return LB_OK;
 }
 
@@ -930,6 +962,7 @@ int lb_batch_create(const lb_params *ps, int32_t count, lb_batch **out) {
       lb_batch_destroy(b);
       return bfail(nullptr, rc, m);
     }
+    h->in_batch = true;
     b->hs.push_back(h);
   }
   cudaError_t e = lbk::sweep_prepare(b->store, &b->smem);

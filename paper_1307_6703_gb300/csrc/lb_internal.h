@@ -38,6 +38,10 @@ struct SweepArgs {
   // -- and resets *arrivals (a counter that is zero between launches).
   double *total;
   unsigned *arrivals;
+  // Non-null: the same last CTA also writes {total[0..4], mon_step} here
+  // (device address of a record in a mapped host ring).
+  double *monitor;
+  double mon_step;
 };
 
 // Storage formats of the sweep kernel (values of lb_precision).

@@ -746,11 +746,14 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
     }
     if (t == 0) {
-      A.total[0] = v[0];
-      A.total[1] = v[1];
-      A.total[2] = v[2];
-      A.total[3] = v[3] != 0.0 ? 1.0 : 0.0;
-      A.total[4] = __ldcg(A.err) != 0 ? 1.0 : 0.0;
+      const double r[5] = {v[0], v[1], v[2], v[3] != 0.0 ? 1.0 : 0.0, __ldcg(A.err) != 0 ? 1.0 : 0.0};
+#pragma unroll
+      for (int q = 0; q < 5; ++q) A.total[q] = r[q];
+      if (A.monitor) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) A.monitor[q] = r[q];
+        A.monitor[5] = A.mon_step;
+      }
       *A.arrivals = 0u;
     }
   }

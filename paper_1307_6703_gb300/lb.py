@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_moments.argtypes = [P, P, P, P, C.c_int, C.c_int]
         lib.lb_reduce.argtypes = [P, C.POINTER(C.c_double)]
         lib.lb_reduce_async.argtypes = [P, P]
+        lib.lb_monitor.argtypes = [P, P, C.c_int32]
         lib.lb_get_state.argtypes = [P, P, C.POINTER(C.c_size_t)]
         lib.lb_set_state.argtypes = [P, P, C.c_size_t, C.c_int64]
         lib.lb_get_step.argtypes = [P, C.POINTER(C.c_int64)]
@@ -159,6 +160,16 @@ def lb_reduce_async(h, out) -> None:
     doubles (mass, momx, momy, unstable flag, wait/layout error flag) --
     a pinned torch tensor or a numpy array; valid after a stream sync."""
     _check(load_library().lb_reduce_async(h, _addr(out)), h)
+
+
+def lb_monitor(h, ring=None, capacity: int = 0) -> None:
+    """Register `ring` (page-locked HOST memory of capacity x 6 doubles, e.g.
+    a pinned torch tensor) for per-step records written by the step kernel:
+    (mass, momx, momy, unstable flag, wait/layout error flag, step); None
+    switches monitoring off."""
+    if ring is not None and capacity == 0:
+        capacity = int(ring.numel() if hasattr(ring, "numel") else ring.size) // 6
+    _check(load_library().lb_monitor(h, _addr(ring), capacity if ring is not None else 0), h)
 
 
 def lb_get_state(h, buf=None) -> int:
@@ -293,6 +304,10 @@ class Solver:
 
     def set_seg_h(self, seg_h: int):
         lb_set_seg_h(self.h, seg_h)
+        return self
+
+    def monitor(self, ring=None, capacity: int = 0):
+        lb_monitor(self.h, ring, capacity)
         return self
 
     def get_state(self):

@@ -77,6 +77,7 @@ def test_null_handles_are_refused_without_gpu(lib):
     from paper_1307_6703_gb300 import LB_ERR_ARG
     assert lib.lb_set_seg_h(None, 64) == LB_ERR_ARG
     assert lib.lb_reduce_async(None, None) == LB_ERR_ARG
+    assert lib.lb_monitor(None, None, 0) == LB_ERR_ARG
     assert lib.lb_step(None, 1) == LB_ERR_ARG
 
 

@@ -272,6 +272,43 @@ def test_reduce_async_matches_reduce(storage):
     bad.close()
 
 
+@pytest.mark.parametrize("storage", ["fp32", "bf16dev"])
+def test_monitor_ring_records_every_step(storage):
+    """lb_monitor: with a pinned ring of 8 records, one lb_step(20) call
+    leaves the records of steps 13..20 in host memory, each written by its
+    step's kernel into slot (step mod 8): mass conserved, flags clear, the
+    last equal to lb_reduce bit for bit; switched off, steps write nothing;
+    a batch instance is refused."""
+    import torch
+    from gpu_util import dev16_solver
+    from paper_1307_6703_gb300 import LB_BF16DEV, LB_ERR_ARG, Batch, LBError, lb_monitor, lb_params
+    w = C2(0.05).with_(nx=256, ny=128)
+    s = (solver_for(w, LB_FP32) if storage == "fp32" else dev16_solver(w, LB_BF16DEV, 1.0))
+    s.init_noise(2, w.rho_mean, w.noise)
+    ring = torch.full((8, 6), -1.0, dtype=torch.float64).pin_memory()
+    s.monitor(ring)
+    s.step(20)
+    torch.cuda.synchronize()
+    r = ring.numpy().copy()
+    assert [int(r[i, 5]) for i in range(8)] == [16, 17, 18, 19, 20, 13, 14, 15]
+    rc, vals = s.reduce()
+    assert rc == 0 and list(r[20 % 8, :3]) == vals
+    assert np.all(np.abs(r[:, 0] - vals[0]) <= 1e-6 * vals[0])
+    assert np.all(r[:, 3:5] == 0.0)
+    s.monitor(None)
+    before = ring.clone()
+    s.step(5)
+    torch.cuda.synchronize()
+    assert torch.equal(ring, before)
+    s.close()
+    b = Batch([lb_params(64, 32, 1, LB_FP32, w.a, w.b, w.T, w.kappa, w.tau, w.A0, 32.0, -0.01, 0.01,
+                         w.N, w.Q, 0.0, None)])
+    with pytest.raises(LBError) as e:
+        lb_monitor(b.views[0].h, ring)
+    assert e.value.code == LB_ERR_ARG
+    b.close()
+
+
 def test_moments_to_device_and_stream():
     """lb_moments writes device pointers (torch tensors) on a torch stream
     and agrees with the host path."""
