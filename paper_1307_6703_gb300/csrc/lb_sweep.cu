@@ -50,9 +50,16 @@
 // constant to the density, and enter the collision as one constant per link
 // class, so decoding and encoding are a conversion each.
 //
-// Every CTA also writes FP64 partial sums of mass and momentum of the state
-// it stored, and a flag for non-finite or out-of-range sites, so that the
-// global reduction of the new state costs one tiny kernel.
+// On the last step of a call (or every step while a monitoring ring is set)
+// every CTA also writes FP64 partial sums of mass and momentum of the state
+// it stored, and a flag for non-finite or out-of-range sites; the CTA that
+// finishes last adds them up, so the global sums of the new state need no
+// further kernel.
+//
+// Consecutive steps are programmatic dependent launches: step k+1 may be
+// scheduled once every CTA of step k has left its main loop, and waits
+// (griddepcontrol.wait) for step k to complete before it touches global
+// memory, which hides the launch gap between the two grids.
 #include <cstddef>
 #include <type_traits>
 
@@ -348,7 +355,6 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   const int npairs = kmax + 2;          // rows ya-4 .. ya+2*kmax+3
   const Sten st{A.N, A.M, A.Q, A.R, A.four_QR};
   float sinx = 0.f;
-  if (actC) sinx = A.sinx[x < 0 ? x + nx : (x >= nx ? x - nx : x)];
   float *col = A.fout + A.off + x;  // f* (rest plane for 16-bit storage) of this column at interior row 0
   const int pitch = A.pitch, plane = (int)A.plane;
   const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);  // periodic image column
@@ -358,14 +364,22 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   const float wr_ax = St::kDev ? A.omega * A.ref_ax : 0.f;
   const float wr_dg = St::kDev ? A.omega * A.ref_dg : 0.f;
 
+  if (actC) sinx = A.sinx[x < 0 ? x + nx : (x >= nx ? x - nx : x)];  // a constant table
+  if (t == 0) {
+    for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // Launched as a programmatic dependent of the previous step: wait until
+  // that grid has finished and its writes are visible before any other
+  // global access (its output is this step's input, and this step's output
+  // buffer was its input).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // TMA writes need 128-byte aligned destinations: refuse to run otherwise.
   if (smem_u32(&S.pops[0][0]) & 127u) {
     if (t == 0) atomicOr(A.err, 2);
     return;
   }
   if (t == 0) {
-    for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int P = 0; P < min(kPairs, npairs); ++P)
       tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
@@ -677,6 +691,8 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   for (; k < min(klo, kmax + 1); ++k) iteration(k, std::false_type{});
   for (; k < khi; ++k) iteration(k, std::true_type{});
   for (; k <= kmax; ++k) iteration(k, std::false_type{});
+  // The next step may be scheduled now (it waits for this grid to finish).
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // CTA partial sums of the stored state (FP64, fixed order), when asked
   // for.  Every TMA copy has been waited for, so the population ring is
@@ -903,9 +919,20 @@ cudaError_t launch_batch_one(const BatchItem *items, int nitems, const SweepArgs
 template <class St>
 cudaError_t launch_one(const CUtensorMap &m0, const CUtensorMap &m1, const SweepArgs &A, size_t smem,
                        cudaStream_t st) {
-  dim3 grid((unsigned)A.nstrips, (unsigned)A.nseg);
-  sweep_step_kernel<St><<<grid, kThreads, smem, st>>>(m0, m1, A);
-  return cudaGetLastError();
+  // Programmatic dependent launch: the kernel may start while the previous
+  // step finishes; it waits for that grid (griddepcontrol.wait) before
+  // touching global memory.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)A.nstrips, (unsigned)A.nseg);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_step_kernel<St>, m0, m1, A);
 }
 
 unsigned elementwise_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
