@@ -262,22 +262,71 @@ def _flat_interface(oracle_mod, tau=1.0, ny=128, steps=20000, Tr=0.95, ux=None):
     return o
 
 
-def test_flat_interface_mechanical_equilibrium(oracle_mod):
-    """With F = d(p^i - p^w) + kappa n d(lap n) taken by the stencil on the
-    pressure field, a flat interface at rest balances p^w exactly:
-    p^w(n_L) = p^w(n_V), and the velocity vanishes."""
+def _discrete_balance_solve(n_init, T, Fext=None):
+    """Static 1D states of the scheme without running it.
+
+    At a steady state at rest (u* = 0, so C = 0 and n u* = 0) with variation
+    along one lattice axis only, the moments of propagation plus collision
+    (Eqs. evoleq, newvel, forceterm, coeff) reduce to two site-by-site
+    balances, whatever tau is:
+      momentum: D_c(n T) = F + (1/4) lap F,    mass: lap(n T) = D_c F,
+    with D_c the central difference, lap the 3-point Laplacian and F the
+    force of Eq. (force2) plus F_ext (the stencils of Eqs. xstencil and
+    laplstencil reduce to D_c and lap on such fields for any N, Q).  The
+    (1/4) lap F term is the lattice's own trapezoidal treatment of the force
+    (F/2 in Eq. newvel): the scheme balances the force against the pressure
+    over a link, (F_y + F_(y+1))/2 = T (n_(y+1) - n_y).  These equations and
+    the mass fix n(y); they are solved here by least squares from the same
+    initial profile, with no lattice Boltzmann step."""
+    from scipy.optimize import least_squares
+    a, b, kappa = PAPER["a"], PAPER["b"], PAPER["kappa"]
+    n_init = np.asarray(n_init, dtype=np.float64)
+    Fext = np.zeros_like(n_init) if Fext is None else Fext
+    mass = n_init.sum()
+    dc = lambda f: 0.5 * (np.roll(f, -1) - np.roll(f, 1))
+    lap = lambda f: np.roll(f, -1) + np.roll(f, 1) - 2.0 * f
+
+    def resid(n):
+        pw = n * T / (1.0 - b * n) - a * n * n
+        F = dc(n * T - pw) + kappa * n * dc(lap(n)) + Fext
+        return np.concatenate([dc(n * T) - F - 0.25 * lap(F), lap(n * T) - dc(F), [n.sum() - mass]])
+
+    sol = least_squares(resid, n_init, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=4000)
+    assert np.abs(sol.fun).max() < 1e-13
+    return sol.x
+
+
+def test_flat_interface_is_the_schemes_discrete_balance(oracle_mod):
+    """The oracle's flat interface (20,000 steps, periodic 1 x 128) has the
+    bulk densities of the static state of the discrete moment balances,
+    solved without any lattice Boltzmann step, to 1e-12 relative; its
+    density and force fields satisfy the momentum balance to rounding.  A dropped F/2,
+    a wrong forcing coefficient or a wrong propagation would move the state
+    far beyond that."""
     from oracle import maxwell
     o = _flat_interface(oracle_mod)
-    n, ux, uy = o.moments()
-    n = n[:, 0]
+    n, ux, uy, Fx, Fy = o.moments(forces=True)
+    n, F = n[:, 0], Fy[:, 0]
     T = 0.95 * TC_PAPER
+    dc = lambda f: 0.5 * (np.roll(f, -1) - np.roll(f, 1))
+    lap = lambda f: np.roll(f, -1) + np.roll(f, 1) - 2.0 * f
+    assert np.abs(dc(n * T) - F - 0.25 * lap(F)).max() < 1e-14
+    assert np.abs(uy).max() < 1e-12
+    ny = len(n)
+    y = np.arange(ny)
+    nL, nV = maxwell.coexistence(PAPER["a"], PAPER["b"], T)
+    n_init = nV + (nL - nV) * 0.5 * (np.tanh((y - ny / 4) / 3) - np.tanh((y - 3 * ny / 4) / 3))
+    nb = _discrete_balance_solve(n_init, T)
+    # bulk densities (the interfaces may sit a few 1e-6 sites apart: the
+    # balances fix the profile up to a translation)
+    assert abs(n.max() - nb.max()) <= 1e-12 * nL and abs(n.min() - nb.min()) <= 1e-12 * nL
+    # Mechanical equilibrium holds exactly, p^w(n_L) = p^w(n_V); the bulk
+    # densities sit below Maxwell's (n_L -0.62 %, n_V -2.99 %) because of the
+    # (1/4) lap F term, which no reading of the printed equations removes
+    # (see the design notes' table of readings).
     dp = maxwell.pressure(n[64], PAPER["a"], PAPER["b"], T) - maxwell.pressure(n[0], PAPER["a"], PAPER["b"], T)
     assert abs(dp) < 1e-8
-    assert np.abs(uy).max() < 1e-12
-    nL, nV = maxwell.coexistence(PAPER["a"], PAPER["b"], T)
-    # Bulk densities sit within a few percent of the Maxwell values (the
-    # discrete force is not exactly thermodynamically consistent).
-    assert abs(n[64] / nL - 1) < 0.01 and abs(n[0] / nV - 1) < 0.035
+    assert abs(n[64] / nL - 1 + 0.00624) < 5e-4 and abs(n[0] / nV - 1 + 0.02989) < 5e-4
 
 
 def test_phase_diagram_independent_of_tau(oracle_mod):
@@ -346,7 +395,9 @@ def test_droplet_matches_paper(oracle_mod):
     assert abs(n[L // 2, L // 2] / d["n_L"] - 1) < 0.005
     assert abs(n[0, 0] / d["n_V"] - 1) < 0.005
     umax = np.hypot(ux, uy).max()
-    assert 0.5 * g["spurious_velocity_T095"]["u_max"] < umax < 1.5 * g["spurious_velocity_T095"]["u_max"]
+    # printed to one digit: 0.002 stands for [0.0015, 0.0025)
+    u_paper = g["spurious_velocity_T095"]["u_max"]
+    assert 0.75 * u_paper <= umax < 1.25 * u_paper
 
 
 def test_laplace_law(oracle_mod):
@@ -374,19 +425,59 @@ def test_laplace_law(oracle_mod):
 
 def test_zebra_phase_at_rest(oracle_mod):
     """Fig. 7 (top): zebra phase with A0 = 1e-4, lambda = 32, tau = 1,
-    kappa = 0.3, T = 0.95; bulk values 1.459906 / 0.580089.  The stripes are
-    flat interfaces, for which this reading of the force sits a few percent
-    below the paper's values (see the flat-interface check)."""
+    kappa = 0.3, T = 0.95.  The oracle's stripes equal the static state of
+    the discrete moment balances with the periodic force (solved without
+    any lattice Boltzmann step) to 1e-9 relative.  The paper prints bulk
+    values 1.459906 / 0.580089; this scheme's own fixed point sits 0.76 % /
+    3.06 % below them, as the flat interface sits below Maxwell, and no
+    reading of the printed equations closes that gap (design notes, table
+    of readings), so the printed values bound the result only loosely."""
     z = golden("paper_values.json")["zebra_T095"]
-    p = oracle_mod.Params(nx=32, ny=1, walls=False, T=z["T_reduced"] * TC_PAPER, tau=z["tau"],
+    T = z["T_reduced"] * TC_PAPER
+    p = oracle_mod.Params(nx=32, ny=1, walls=False, T=T, tau=z["tau"],
                           A0=z["A0"], lam=z["lambda"], N=0.3, Q=2.0, **PAPER)
     o = oracle_mod.Oracle(p).init_noise(1, 1.0, 0.003)
-    o.step(30000)
+    o.step(60000)
     n, ux, _ = o.moments()
-    assert abs(n.max() / z["n_L"] - 1) < 0.01
-    assert abs(n.min() / z["n_V"] - 1) < 0.035
-    # One liquid and one vapour stripe per wavelength, locked to the force.
-    assert np.argmax(n[0]) != np.argmin(n[0])
+    n = n[0]
+    x = np.arange(32)
+    n_init = n.mean() + 0.44 * np.cos(2 * np.pi * (x - 16) / 32)
+    nb = _discrete_balance_solve(n_init, T, z["A0"] * np.sin(2 * np.pi * x / z["lambda"]))
+    assert np.abs(n - nb).max() <= 1e-9 * n.max()  # the force fixes the stripes' position
+    assert abs(n.max() / z["n_L"] - 1 + 0.0076) < 1e-3
+    assert abs(n.min() / z["n_V"] - 1 + 0.0306) < 1e-3
+    # One liquid and one vapour stripe per wavelength, the liquid where the
+    # force converges (x = lambda / 2).
+    assert np.argmax(n) == 16 and np.argmin(n) == 0
+
+
+def test_table1_stencil_optima(oracle_mod):
+    """Table 1 at T = 0.95 (droplet R = 15, kappa = 0.3, tau = 1): over
+    N in {0.2, 0.3, 0.4} at the table's Q values the largest spurious
+    velocity is smallest at N = 0.3, the OVC row's N, and the density error
+    |n_L^th - n_L| + |n_V^th - n_V| is smallest at N = 0.4, the ODC row's N.
+    (A full scan, N in [0, 1] by 0.1 and Q in [0, 4] by 0.1, finds the same
+    two N; along Q both measures vary by a few percent only, so Q itself is
+    not pinned.)  The standard central scheme (0.5, 1.0) has larger spurious
+    velocities than OVC (Fig. 2)."""
+    from oracle import maxwell
+    T = 0.95 * TC_PAPER
+    nL, nV = maxwell.coexistence(PAPER["a"], PAPER["b"], T)
+    L = 64
+    yy, xx = np.mgrid[0:L, 0:L]
+    r = np.hypot(xx - L / 2 + 0.5, yy - L / 2 + 0.5)
+
+    def droplet(N, Q):
+        p = oracle_mod.Params(nx=L, ny=L, walls=False, T=T, tau=1.0, N=N, Q=Q, **PAPER)
+        o = oracle_mod.Oracle(p).init_fields(np.where(r < 15, nL, nV)).step(2000)
+        n, ux, uy = o.moments()
+        return float(np.hypot(ux, uy).max()), abs(n[L // 2, L // 2] - nL) + abs(n[0, 0] - nV)
+
+    for Q in (2.0, 2.1):
+        res = {N: droplet(N, Q) for N in (0.2, 0.3, 0.4)}
+        assert min(res, key=lambda N: res[N][0]) == 0.3, res
+        assert min(res, key=lambda N: res[N][1]) == 0.4, res
+    assert droplet(0.5, 1.0)[0] > 2.0 * droplet(0.3, 2.0)[0]
 
 
 def test_workload_parameter_readings():
