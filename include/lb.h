@@ -280,7 +280,9 @@ int lb_destroy(lb_handle *h);
  *  stream     cudaStream_t to enqueue on (NULL = default stream)
  * Enqueues two kernels and returns without synchronising.  The first call on
  * a device looks up the scratch array's device address (once per device);
- * make that first call before any stream capture.  All calls share the one
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: after cudaDeviceReset on a device it is stale,
+ * so do not call this entry point on a device that has been reset.  All calls share the one
  * scratch array, so calls that overlap on the GPU race and must be
  * serialised by the caller.  The row partials are summed in a fixed order,
  * so results are deterministic; they equal lb_reduce's up to the order of

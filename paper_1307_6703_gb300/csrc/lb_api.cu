@@ -830,6 +830,14 @@ struct lb_batch {
   int kpar = 0;           // parity of the next batch step
   bool dirty = true;      // device work list out of date
   cudaGraphExec_t graph = nullptr;  // two consecutive steps, kpar 0 then 1
+  // Multi-step launches (lb_batch_step with nsteps >= 2): per-item
+  // completion counters and dependency lists, rebuilt with the work list.
+  int persist_cap = 0;              // resident CTAs of that kernel (0: not queried, < 0: unavailable)
+  unsigned *d_done = nullptr;
+  int *d_dep = nullptr;             // CSR: nitems + 1 offsets, then indices
+  int done_cap = 0, dep_cap = 0;
+  unsigned *d_ticket = nullptr;     // ticket counter of a multi-step launch
+  unsigned epoch = 0;               // value of every counter between launches
   std::string err;
 };
 
@@ -887,6 +895,44 @@ int batch_rebuild(lb_batch *b) {
     b->items_cap = (int)items.size();
   }
   b->nitems = (int)items.size();
+  // Dependency lists of the multi-step kernel, per item: the tiles of the
+  // same lattice its tile depends on (lbk::sweep_deps), as item indices.
+  std::vector<int> csr(1, 0), dep_idx;
+  {
+    std::vector<std::vector<int>> item_of(n);
+    for (int i = 0; i < n; i++) item_of[i].assign((size_t)b->hs[i]->sweep_nstrips * b->hs[i]->sweep_nseg, -1);
+    for (int j = 0; j < (int)items.size(); j++) {
+      const lbk::BatchItem &it = items[j];
+      item_of[it.inst][(size_t)it.seg * b->hs[it.inst]->sweep_nstrips + it.strip] = j;
+    }
+    std::vector<std::vector<int>> ofs(n), idx(n);
+    for (int i = 0; i < n; i++) {
+      const lb_handle *h = b->hs[i];
+      lbk::sweep_deps(h->store, h->p.nx, h->p.ny, h->p.walls, h->sweep_nstrips, h->sweep_base, h->sweep_extra,
+                      h->sweep_seg, ofs[i], idx[i]);
+    }
+    for (const lbk::BatchItem &it : items) {
+      const size_t tile = (size_t)it.seg * b->hs[it.inst]->sweep_nstrips + it.strip;
+      for (int d = ofs[it.inst][tile]; d < ofs[it.inst][tile + 1]; d++) dep_idx.push_back(item_of[it.inst][idx[it.inst][d]]);
+      csr.push_back((int)dep_idx.size());
+    }
+    csr.insert(csr.end(), dep_idx.begin(), dep_idx.end());
+  }
+  if ((int)items.size() > b->done_cap || (int)csr.size() > b->dep_cap) {
+    LB_BCUDA(b, cudaStreamSynchronize(b->st));
+    cudaFree(b->d_done);
+    cudaFree(b->d_dep);
+    b->d_done = nullptr;
+    b->d_dep = nullptr;
+    b->done_cap = b->dep_cap = 0;
+    LB_BCUDA(b, cudaMalloc((void **)&b->d_done, items.size() * sizeof(unsigned)));
+    LB_BCUDA(b, cudaMalloc((void **)&b->d_dep, csr.size() * sizeof(int)));
+    b->done_cap = (int)items.size();
+    b->dep_cap = (int)csr.size();
+  }
+  LB_BCUDA(b, cudaMemsetAsync(b->d_done, 0, items.size() * sizeof(unsigned), b->st));
+  b->epoch = 0;
+  LB_BCUDA(b, cudaMemcpyAsync(b->d_dep, csr.data(), csr.size() * sizeof(int), cudaMemcpyHostToDevice, b->st));
   LB_BCUDA(b, cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(lbk::BatchItem),
                               cudaMemcpyHostToDevice, b->st));
   LB_BCUDA(b, cudaMemcpyAsync(b->d_args, args.data(), args.size() * sizeof(lbk::SweepArgs),
@@ -992,6 +1038,42 @@ int lb_batch_step(lb_batch *b, int64_t nsteps) {
   if (!batch_in_sync(b)) {
     int rc = batch_rebuild(b);
     if (rc != LB_OK) return rc;
+  }
+  if (nsteps >= 2 && b->persist_cap == 0) {
+    int cap = 0;
+    const cudaError_t e = lbk::persist_capacity(b->store, b->smem, &cap);
+    if (e != cudaSuccess) cudaGetLastError();
+    b->persist_cap = (e == cudaSuccess && cap > 0) ? cap : -1;
+  }
+  if (nsteps >= 2 && b->persist_cap > 0) {
+    // Every step in multi-step launches (chunks of at most 2^16 steps).
+    const int grid = std::min(b->nitems, b->persist_cap);
+    if (!b->d_ticket) LB_BCUDA(b, cudaMalloc((void **)&b->d_ticket, sizeof(unsigned)));
+    for (int64_t done = 0; done < nsteps;) {
+      const int chunk = (int)std::min<int64_t>(nsteps - done, std::max<int64_t>(1, (1LL << 30) / b->nitems));
+      lbk::PersistArgs P{};
+      P.nitems = b->nitems;
+      P.nsteps = chunk;
+      P.kpar0 = b->kpar;
+      P.epoch = b->epoch;
+      P.done = b->d_done;
+      P.dep_ofs = b->d_dep;
+      P.dep_idx = b->d_dep + b->nitems + 1;
+      P.next = b->d_ticket;
+      LB_BCUDA(b, cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned), b->st));
+      LB_BCUDA(b, lbk::launch_sweep_batch_persist(b->store, b->d_items, b->d_args, b->d_maps, P, grid, b->smem,
+                                                  b->st));
+      b->kpar = (b->kpar + chunk) & 1;
+      b->epoch += (unsigned)chunk;
+      done += chunk;
+    }
+    for (lb_handle *h : b->hs) {
+      h->cur ^= (int)(nsteps & 1);
+      h->step += nsteps;
+      h->cta_valid = true;
+      h->total_valid = false;
+    }
+    return LB_OK;
   }
   int64_t k = 0;
   if (b->kpar == 1) {  // one plain step to reach kpar 0
@@ -1127,6 +1209,9 @@ int lb_batch_destroy(lb_batch *b) {
   cudaFree(b->d_items);
   cudaFree(b->d_args);
   cudaFree(b->d_maps);
+  cudaFree(b->d_done);
+  cudaFree(b->d_dep);
+  cudaFree(b->d_ticket);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
   return LB_OK;

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -66,6 +67,11 @@ size_t sweep_buffer_bytes(int store, long long plane);
 cudaError_t launch_sweep(int store, const CUtensorMap &m0, const CUtensorMap &m1, const SweepArgs &A,
                          size_t smem, cudaStream_t st);
 
+// Dependency lists of the tiles (CSR): tile a waits for the tiles
+// idx[ofs[a] .. ofs[a+1]) before each step.
+void sweep_deps(int store, int nx, int ny, int walls, int nstrips, int base_w, int extra, int seg_h,
+                std::vector<int> &ofs, std::vector<int> &idx);
+
 // One CTA of the batched sweep: instance `inst`, its strip and segment, the
 // index of its mass/momentum record in the instance's record array, and the
 // parity of the instance's input buffer at kpar = 0.
@@ -77,6 +83,28 @@ struct BatchItem {
 // 16-bit storage or a copy of map 0), 64-byte aligned device memory.
 cudaError_t launch_sweep_batch(int store, const BatchItem *items, int nitems, const SweepArgs *args,
                                const CUtensorMap *maps, int kpar, int records, size_t smem, cudaStream_t st);
+// Multi-step batched sweep (one cooperative launch, many steps, per-item
+// completion counters instead of a grid-wide barrier between steps).
+// Item i of a step whose batch parity is kpar reads the input buffer
+// items[i].par0 ^ kpar of its lattice; kpar = (kpar0 + k) & 1 at step k.
+struct PersistArgs {
+  int nitems;
+  int nsteps;
+  int kpar0;
+  unsigned epoch;       // value of every done[] counter at launch
+  unsigned *done;       // one per item
+  const int *dep_ofs;   // item i depends on dep_idx[dep_ofs[i] .. dep_ofs[i+1])
+  const int *dep_idx;
+  unsigned *next;       // ticket counter, zero at launch
+};
+// Resident CTAs of the multi-step batched kernel on this device (its grid
+// may not exceed this: the dependency waits need every CTA resident).
+cudaError_t persist_capacity(int store, size_t smem, int *blocks);
+// P.nsteps batch steps in one cooperative launch of `grid` CTAs; the mass /
+// momentum records of the last step go to each instance's record array.
+cudaError_t launch_sweep_batch_persist(int store, const BatchItem *items, const SweepArgs *args,
+                                       const CUtensorMap *maps, const PersistArgs &P, int grid, size_t smem,
+                                       cudaStream_t st);
 // Copy the periodic images into the ghost band of `nplanes` planes of
 // `elem_bytes`-byte elements (4 or 2).
 cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,

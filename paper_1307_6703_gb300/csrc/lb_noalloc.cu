@@ -148,12 +148,17 @@ extern "C" int lb_reduce_noalloc(const void *f, int precision, int32_t nx, int32
   cudaStream_t st = (cudaStream_t)stream;
   const double nmax = b > 0.0 ? 1.0 / b : INFINITY;
   const int blocks = ny < 2048 ? ny : 2048;
-  if (precision == LB_FP64)
-    rows_pass<double><<<blocks, kThreads, 0, st>>>((const double *)f, nx, ny, nmax, rows);
-  else
-    rows_pass<float><<<blocks, kThreads, 0, st>>>((const float *)f, nx, ny, nmax, rows);
-  if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
-  rows_total<<<1, kThreads, 0, st>>>(rows, ny, out, flag);
-  if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
-  return LB_OK;
+  // Each launch reports its own error: the caller's pending error state is
+  // neither read nor cleared.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = st;
+  cudaError_t e = precision == LB_FP64
+                      ? cudaLaunchKernelEx(&cfg, rows_pass<double>, (const double *)f, (int)nx, (int)ny, nmax, rows)
+                      : cudaLaunchKernelEx(&cfg, rows_pass<float>, (const float *)f, (int)nx, (int)ny, nmax, rows);
+  if (e != cudaSuccess) return LB_ERR_CUDA;
+  cfg.gridDim = dim3(1);
+  e = cudaLaunchKernelEx(&cfg, rows_total, (const RowPartial *)rows, (int)ny, out, flag);
+  return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
 }

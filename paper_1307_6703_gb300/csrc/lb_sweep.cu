@@ -62,6 +62,8 @@
 // memory, which hides the launch gap between the two grids.
 #include <cstddef>
 #include <type_traits>
+#include <vector>
+#include <algorithm>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -159,6 +161,7 @@ struct __align__(128) SweepSmem {
   float2 PL[2][2][kCols];  // (P, lap n): one 64-bit load per stencil tap
   float2 J[2][2][kCols];   // (n u*_x, n u*_y)
   unsigned long long full[kPairs];
+  int abort;  // set by a thread whose copy wait gave up; read after a barrier
   static_assert(SlotBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
   static_assert(kPairs * SlotBytes >= (int)(sizeof(double) * 4 * kThreads + sizeof(unsigned)),
                 "the end-of-kernel reduction reuses the population ring");
@@ -175,10 +178,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar) {
 }
 
 // Wait for phase `parity` of an mbarrier; gives up after a bounded number
-// of polls and reports it (the data are then meaningless but every address
-// the kernel touches stays in bounds).
-__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *err) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+// of polls, reports it and returns false (the data are then meaningless but
+// every address the kernel touches stays in bounds; the caller stops the
+// CTA at its next barrier and drains the copies still in flight).
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -186,9 +190,14 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, int *er
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
-    if (done) return;
+    if (done) return true;
   }
+  return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+  if (mbar_try(bar, parity, kWaitLimit)) return true;
   atomicOr(err, 1);
+  return false;
 }
 
 __device__ __forceinline__ void tma_box(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad, int ypad) {
@@ -322,12 +331,32 @@ __device__ __forceinline__ void collide(const SweepArgs &A, const float *f, floa
 
 }  // namespace
 
+// Where one step's results go: the new state (fout; the deviation planes of
+// 16-bit storage at fdev) and, when arrivals is set, the fused global sums:
+// the CTA that finishes last adds the nrec records at recs into total (if
+// set) and monitor (if set, with mon_step) and resets *arrivals.
+struct StepIO {
+  float *fout;
+  void *fdev;
+  const double *recs;
+  unsigned nrec;
+  unsigned *arrivals;
+  double *total;
+  double *monitor;
+  double mon_step;
+};
+
 // One CTA's work: strip `strip`, segment `seg` of the lattice described by
 // A, whose input state the tensor maps tin (and tdev, the deviation planes
-// of 16-bit storage) describe; the CTA's mass/momentum record goes to rec.
-template <class St>
-__device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
-                                           const int strip, const int seg, double *rec, const bool records) {
+// of 16-bit storage) describe; results as O says; the CTA's mass/momentum
+// record goes to rec.  Returns false when a copy wait gave up (the CTA then
+// stopped at its next barrier and drained the copies still in flight).
+// kPersist: called once per tile by the multi-step kernel, which does not
+// hand its SM slots to a dependent grid early.
+template <class St, bool kPersist = false>
+__device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
+                                           const StepIO &O, const int strip, const int seg, double *rec,
+                                           const bool records) {
   using Row = typename St::Row;
   using Smem = SweepSmem<St::kSlotBytes>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -355,7 +384,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   const int npairs = kmax + 2;          // rows ya-4 .. ya+2*kmax+3
   const Sten st{A.N, A.M, A.Q, A.R, A.four_QR};
   float sinx = 0.f;
-  float *col = A.fout + A.off + x;  // f* (rest plane for 16-bit storage) of this column at interior row 0
+  float *col = O.fout + A.off + x;  // f* (rest plane for 16-bit storage) of this column at interior row 0
   const int pitch = A.pitch, plane = (int)A.plane;
   const int gx = (x < 4) ? nx : ((x >= nx - 4) ? -nx : 0);  // periodic image column
   // 16-bit storage: sum of the moving links' reference populations, and the
@@ -368,6 +397,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   if (t == 0) {
     for (int s = 0; s < kPairs; ++s) mbar_init(smem_u32(&S.full[s]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.abort = 0;
   }
   // Launched as a programmatic dependent of the previous step: wait until
   // that grid has finished and its writes are visible before any other
@@ -377,14 +407,15 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   // TMA writes need 128-byte aligned destinations: refuse to run otherwise.
   if (smem_u32(&S.pops[0][0]) & 127u) {
     if (t == 0) atomicOr(A.err, 2);
-    return;
+    return false;
   }
+  int issued = min(kPairs, npairs);  // pairs requested so far (thread 0's count)
   if (t == 0) {
-    for (int P = 0; P < min(kPairs, npairs); ++P)
+    for (int P = 0; P < issued; ++P)
       tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
   __syncthreads();
-  mbar_wait(smem_u32(&S.full[0]), 0, A.err);
+  if (!mbar_wait(smem_u32(&S.full[0]), 0, A.err)) S.abort = 1;
 
   float sxa[2] = {0.f, 0.f}, sya[2] = {0.f, 0.f};  // raw momentum of rows a-2, a-1 (from last A)
   float Fx_prev = 0.f, Fy_prev = 0.f;              // force of row a-3 (from last C)
@@ -397,7 +428,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   // interior rows of the segment (no wall rows or their mirrors, no warm-up
   // rows, no periodic ghost images in y), where every per-row condition
   // below is known to hold and the two rows of a stage are independent.
-  auto iteration = [&](const int k, auto steady_tag) {
+  auto iteration = [&](const int k, auto steady_tag) -> bool {
     constexpr bool kSteady = decltype(steady_tag)::value;
     const int s5m1 = dec(s5, kPairs), s5m2 = dec(s5m1, kPairs), s5p1 = inc(s5, kPairs);
     const int s3m1 = (s3 + 3) & 3, s3m2 = (s3 + 2) & 3;  // density ring: 4 pairs
@@ -409,9 +440,10 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       if (t == 0 && k + 2 < npairs) {
         const int slot = dec(s5m2, kPairs);
         tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k + 2));
+        ++issued;
       }
     }
-    mbar_wait(smem_u32(&S.full[s5p1]), par, A.err);  // newest pair needed: k+1
+    if (!mbar_wait(smem_u32(&S.full[s5p1]), par, A.err)) S.abort = 1;  // newest pair needed: k+1
     if (s5p1 == kPairs - 1) par ^= 1u;
     const int a = ya - 3 + 2 * k;
 
@@ -457,6 +489,9 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       for (int j = 0; j < 2; ++j)
         if (nw[j]) S.n[s3][j][t] = nv[j];
       __syncthreads();
+      // A copy wait that gave up (this iteration's or an earlier one's) was
+      // recorded before the barrier: every thread leaves here together.
+      if (S.abort) return false;
 
       // -------------------------------------- B: rows a-1, a -- P, lap n
       {
@@ -617,7 +652,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
               fs[q] = St::dec(code[q - 1]);
             }
             fs[0] = (n - r_sum) - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
-            H *od = reinterpret_cast<H *>(A.fdev) + (A.off + x + (long long)y * pitch);
+            H *od = reinterpret_cast<H *>(O.fdev) + (A.off + x + (long long)y * pitch);
             o[0] = fs[0];
 #pragma unroll
             for (int q = 0; q < 8; ++q) od[q * plane] = code[q];
@@ -678,6 +713,7 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
     }
     s5 = s5p1;
     s3 = (s3 + 1) & 3;
+    return true;
   };
   // Iteration k (a = ya - 3 + 2k) is steady -- every row of its four stages
   // interior, see the lambda's note -- when k >= 3, a - 2 < yb and, with
@@ -688,16 +724,28 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
   const int klo = max(3, ceil2((walls ? 7 : 10) - ya));
   const int khi = min(min(kmax + 1, ceil2(yb - ya + 5)), walls ? ((ny - ya) >> 1) + 1 : ceil2(ny - ya - 2));
   int k = 0;
-  for (; k < min(klo, kmax + 1); ++k) iteration(k, std::false_type{});
-  for (; k < khi; ++k) iteration(k, std::true_type{});
-  for (; k <= kmax; ++k) iteration(k, std::false_type{});
+  bool ok = true;
+  for (; ok && k < min(klo, kmax + 1); ++k) ok = iteration(k, std::false_type{});
+  for (; ok && k < khi; ++k) ok = iteration(k, std::true_type{});
+  for (; ok && k <= kmax; ++k) ok = iteration(k, std::false_type{});
+  if (!ok) {
+    // A copy wait gave up: wait (again bounded) for every copy this CTA may
+    // still have in flight -- the last kPairs requested -- so that none
+    // lands in shared memory after the CTA has moved on, then stop.
+    if (t == 0) {
+      for (int P = max(0, issued - kPairs); P < issued; ++P)
+        (void)mbar_try(smem_u32(&S.full[P % kPairs]), (uint32_t)((P / kPairs) & 1), kWaitLimit);
+    }
+    __syncthreads();
+    return false;
+  }
   // The next step may be scheduled now (it waits for this grid to finish).
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if constexpr (!kPersist) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // CTA partial sums of the stored state (FP64, fixed order), when asked
   // for.  Every TMA copy has been waited for, so the population ring is
   // free for them.
-  if (!records) return;
+  if (!records) return true;
   double *red = reinterpret_cast<double *>(&S.pops[0][0]);
   __syncthreads();
   red[0 * kThreads + t] = (double)acc_m;
@@ -726,24 +774,24 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
       for (int q = 0; q < 4; ++q) rec[q] = v[q];
     }
   }
-  if (A.total == nullptr) return;
+  if (O.arrivals == nullptr) return true;
 
   // The last CTA to finish sums every CTA's record (FP64, fixed order:
   // thread t takes records t, t + 124, ..., then warp 0's tree), so the
   // global sums of the new state need no further kernel.
-  const unsigned nrec = gridDim.x * gridDim.y;
+  const unsigned nrec = O.nrec;
   unsigned *last = reinterpret_cast<unsigned *>(red + 4 * kThreads);
   if (t == 0) {
     __threadfence();  // this CTA's record before its arrival
-    *last = (atomicAdd(A.arrivals, 1u) == nrec - 1) ? 1u : 0u;
+    *last = (atomicAdd(O.arrivals, 1u) == nrec - 1) ? 1u : 0u;
   }
   __syncthreads();
-  if (*last == 0u) return;
+  if (*last == 0u) return true;
   __threadfence();
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (unsigned b = t; b < nrec; b += kThreads) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += __ldcg(A.partials + 4 * (size_t)b + q);
+    for (int q = 0; q < 4; ++q) acc[q] += __ldcg(O.recs + 4 * (size_t)b + q);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) red[q * kThreads + t] = acc[q];
@@ -763,24 +811,29 @@ __device__ __forceinline__ void sweep_body(const CUtensorMap *tin, const CUtenso
     }
     if (t == 0) {
       const double r[5] = {v[0], v[1], v[2], v[3] != 0.0 ? 1.0 : 0.0, __ldcg(A.err) != 0 ? 1.0 : 0.0};
+      if (O.total) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) A.total[q] = r[q];
-      if (A.monitor) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) A.monitor[q] = r[q];
-        A.monitor[5] = A.mon_step;
+        for (int q = 0; q < 5; ++q) O.total[q] = r[q];
       }
-      *A.arrivals = 0u;
+      if (O.monitor) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) O.monitor[q] = r[q];
+        O.monitor[5] = O.mon_step;
+      }
+      *O.arrivals = 0u;
     }
   }
+  return true;
 }
 
 template <class St>
 __global__ void __launch_bounds__(kThreads, St::kMinBlocks)
 sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tdev,
                   const SweepArgs A) {
-  sweep_body<St>(&tin, &tdev, A, blockIdx.x, blockIdx.y,
-                 A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), A.records != 0);
+  const StepIO O{A.fout, A.fdev, A.partials, gridDim.x * gridDim.y, A.total ? A.arrivals : nullptr,
+                 A.total, A.monitor, A.mon_step};
+  (void)sweep_body<St>(&tin, &tdev, A, O, blockIdx.x, blockIdx.y,
+                       A.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), A.records != 0);
 }
 
 // Batched step: CTA b works on items[b] (instance, strip, segment) of a
@@ -802,7 +855,107 @@ sweep_batch_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restr
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m + 1) : "memory");
   }
   __syncthreads();
-  sweep_body<St>(m, m + 1, A, it.strip, it.seg, A.partials + 4 * (size_t)it.rec, records != 0);
+  const StepIO O{A.fout, A.fdev, A.partials, 0u, nullptr, nullptr, nullptr, 0.0};
+  (void)sweep_body<St>(m, m + 1, A, O, it.strip, it.seg, A.partials + 4 * (size_t)it.rec, records != 0);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Multi-step batched sweep: one launch runs P.nsteps steps of every lattice
+// of a work list.  CTAs take (step, item) tickets from a counter, step
+// after step, items in work-list order (longest first).  Instead of a grid-wide
+// barrier between steps, every item carries a completion counter done[item]
+// (the steps it has finished, offset by P.epoch): before step k of an item,
+// its threads wait until every item it depends on -- the tiles of the same
+// lattice whose stored sites (ghost images included) its TMA boxes read,
+// and the tiles whose boxes read its own sites (they must have read the
+// buffer it is about to overwrite) -- has reached epoch + k.  Lattices
+// never wait for one another, and a tile starts as soon as its
+// neighbourhood has finished the previous step.  All CTAs are co-resident
+// (cooperative launch) and no step-(k+1) ticket is handed out before every
+// step-k ticket, so the smallest unfinished ticket can always proceed.  Every wait is bounded: on give-up the CTA sets its lattice's
+// error flag (bit 4 for a dependency wait) and stops, and the items that
+// depend on it give up in turn.
+template <class St>
+__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+sweep_batch_persist_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restrict__ args,
+                           const CUtensorMap *__restrict__ maps, const PersistArgs P) {
+  __shared__ SweepArgs A;
+  __shared__ int dep_ok;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  auto &S = *reinterpret_cast<SweepSmem<St::kSlotBytes> *>(smem_raw);
+  __shared__ unsigned ticket;
+  const int t = threadIdx.x;
+  bool first = true;
+  const unsigned total = (unsigned)P.nsteps * (unsigned)P.nitems;
+  for (;;) {
+    // Tickets are handed out in step-major order: every item of step k is
+    // taken before any item of step k+1, so the smallest ticket not yet
+    // finished always has its dependencies (earlier tickets) done.
+    if (t == 0) ticket = atomicAdd(P.next, 1u);
+    __syncthreads();
+    const unsigned tk = ticket;
+    if (tk >= total) break;
+    const int k = (int)(tk / (unsigned)P.nitems), i = (int)(tk % (unsigned)P.nitems);
+    const int kpar = (P.kpar0 + k) & 1;
+    const bool records = k == P.nsteps - 1;
+    const unsigned target = P.epoch + (unsigned)k;
+    {
+      const BatchItem it = items[i];
+      const int par = it.par0 ^ kpar;
+      const CUtensorMap *m = maps + 4 * it.inst + 2 * par;  // [instance][input buffer][map]
+      // Wait for the neighbourhood to finish step k-1 (one thread per
+      // dependency, bounded).  The barrier also ends the previous item.
+      if (t == 0) dep_ok = 1;
+      __syncthreads();
+      for (int d = P.dep_ofs[i] + t; d < P.dep_ofs[i + 1]; d += kThreads) {
+        const unsigned *f = P.done + P.dep_idx[d];
+        uint32_t n = 0;
+        while ((int)(ld_acquire_gpu(f) - target) < 0) {
+          if (++n > kWaitLimit) {
+            dep_ok = 0;
+            atomicOr(args[2 * it.inst].err, 4);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      if (t == 0) {
+        A = args[2 * it.inst + par];
+        // the maps were written through the generic proxy (a host copy)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m + 1) : "memory");
+        // the neighbours' stores, made visible by the acquires, for this
+        // CTA's TMA (async proxy) reads
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (!first) {  // the ring's barriers are initialised again by the sweep
+          for (int q = 0; q < kPairs; ++q)
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[q])) : "memory");
+        }
+      }
+      __syncthreads();
+      if (!dep_ok) return;
+      first = false;
+      const StepIO O{A.fout, A.fdev, A.partials, 0u, nullptr, nullptr, nullptr, 0.0};
+      if (!sweep_body<St, true>(m, m + 1, A, O, it.strip, it.seg, A.partials + 4 * (size_t)it.rec, records))
+        return;
+      // Release this item's step: its stores (generic proxy) before the
+      // counter, ordered for the neighbours' TMA (async proxy) reads.
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      __syncthreads();
+      if (t == 0) {
+        __threadfence();
+        st_release_gpu(P.done + i, target + 1u);
+      }
+    }
+  }
 }
 
 // Copy the periodic images into the ghost band of nplanes padded planes.
@@ -935,6 +1088,37 @@ cudaError_t launch_one(const CUtensorMap &m0, const CUtensorMap &m1, const Sweep
   return cudaLaunchKernelEx(&cfg, sweep_step_kernel<St>, m0, m1, A);
 }
 
+template <class St>
+cudaError_t launch_batch_persist_one(const BatchItem *items, const SweepArgs *args, const CUtensorMap *maps,
+                                     const PersistArgs &P, int grid, size_t smem, cudaStream_t st) {
+  // Cooperative launch: the runtime refuses a grid that cannot be resident
+  // all at once, which the dependency waits rely on.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_batch_persist_kernel<St>, items, args, maps, P);
+}
+
+template <class St>
+cudaError_t persist_capacity_one(size_t smem, int *blocks) {
+  cudaError_t e = cudaFuncSetAttribute(sweep_batch_persist_kernel<St>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_persist_kernel<St>, kThreads, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *blocks = per_sm * sms;
+  return e;
+}
+
 unsigned elementwise_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
 
 }  // namespace
@@ -1004,6 +1188,79 @@ cudaError_t launch_sweep_batch(int store, const BatchItem *items, int nitems, co
     case kStoreFP16: return launch_batch_one<StoreFP16>(items, nitems, args, maps, kpar, records, smem, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t persist_capacity(int store, size_t smem, int *blocks) {
+  switch (store) {
+    case kStoreF32: return persist_capacity_one<StoreF32>(smem, blocks);
+    case kStoreBF16: return persist_capacity_one<StoreBF16>(smem, blocks);
+    case kStoreFP16: return persist_capacity_one<StoreFP16>(smem, blocks);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_batch_persist(int store, const BatchItem *items, const SweepArgs *args,
+                                       const CUtensorMap *maps, const PersistArgs &P, int grid, size_t smem,
+                                       cudaStream_t st) {
+  switch (store) {
+    case kStoreF32: return launch_batch_persist_one<StoreF32>(items, args, maps, P, grid, smem, st);
+    case kStoreBF16: return launch_batch_persist_one<StoreBF16>(items, args, maps, P, grid, smem, st);
+    case kStoreFP16: return launch_batch_persist_one<StoreFP16>(items, args, maps, P, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Tiles each tile of the sweep depends on (see sweep_batch_persist_kernel): the
+// owners of every site its TMA boxes read -- columns x0-4 .. x0+123 and
+// rows ya-4 .. yb+4, periodic images mapped back to the site they copy
+// (rows outside the lattice with walls are never written) -- and,
+// symmetrically, every tile whose window reads its sites.
+void sweep_deps(int store, int nx, int ny, int walls, int nstrips, int base_w, int extra, int seg_h,
+                std::vector<int> &ofs, std::vector<int> &idx) {
+  const int qn = quantum_of(store);
+  const int nseg = (ny + seg_h - 1) / seg_h;
+  const int ntiles = nstrips * nseg;
+  std::vector<int> strip_of(nx);
+  for (int s = 0; s < nstrips; ++s) {
+    const int x0 = s * base_w + qn * std::min(s, extra);
+    const int W = base_w + (s < extra ? qn : 0);
+    for (int x = x0; x < x0 + W; ++x) strip_of[x] = s;
+  }
+  std::vector<std::vector<int>> deps(ntiles);
+  std::vector<int> cs, gs;
+  for (int s = 0; s < nstrips; ++s) {
+    const int x0 = s * base_w + qn * std::min(s, extra);
+    cs.clear();
+    // the widest box: 128 columns of the 16-bit deviation planes
+    for (int x = x0 - 4; x < x0 - 4 + StoreBF16::kDevCols; ++x) cs.push_back(strip_of[((x % nx) + nx) % nx]);
+    std::sort(cs.begin(), cs.end());
+    cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+    for (int g = 0; g < nseg; ++g) {
+      const int ya = g * seg_h, yb = std::min(ny, ya + seg_h);
+      gs.clear();
+      for (int y = ya - 4; y <= yb + 4; ++y) {
+        if (walls && (y < 0 || y >= ny)) continue;
+        gs.push_back((((y % ny) + ny) % ny) / seg_h);
+      }
+      std::sort(gs.begin(), gs.end());
+      gs.erase(std::unique(gs.begin(), gs.end()), gs.end());
+      const int a = s + nstrips * g;
+      for (int s2 : cs)
+        for (int g2 : gs) {
+          const int b = s2 + nstrips * g2;
+          deps[a].push_back(b);  // a reads b's sites
+          deps[b].push_back(a);  // so b must not overwrite them before a has read them
+        }
+    }
+  }
+  ofs.assign(ntiles + 1, 0);
+  idx.clear();
+  for (int a = 0; a < ntiles; ++a) {
+    std::sort(deps[a].begin(), deps[a].end());
+    deps[a].erase(std::unique(deps[a].begin(), deps[a].end()), deps[a].end());
+    idx.insert(idx.end(), deps[a].begin(), deps[a].end());
+    ofs[a + 1] = (int)idx.size();
+  }
 }
 
 cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,
