@@ -49,6 +49,15 @@ struct lb_handle {
   unsigned *d_arrive = nullptr;  // CTA arrival counter of the fused sums
   double *mon_ring = nullptr;    // device address of the monitoring ring (lb_monitor)
   int mon_cap = 0;
+  // Multi-step launches (lb_step with nsteps >= 2 while not monitoring):
+  // per-tile completion counters and dependency lists of the current tiling.
+  int persist_cap = 0;           // resident CTAs of that kernel (0: not queried, < 0: unavailable)
+  unsigned *d_done = nullptr;
+  int *d_dep = nullptr;          // CSR: ntiles + 1 offsets, then indices
+  unsigned *d_ticket = nullptr;  // ticket counter of a launch
+  int deps_gen = -1;             // plan_gen the lists were built for
+  int deps_ntiles = 0;
+  unsigned epoch = 0;            // value of every counter between launches
   bool in_batch = false;         // instance of an lb_batch
   int red_blocks = 0;
   int64_t step = 0;
@@ -329,6 +338,81 @@ cudaError_t ensure_records(lb_handle *h, int nseg) {
   return cudaSuccess;
 }
 
+// Dependency lists and counters of the multi-step kernel for the current
+// tiling (rebuilt when the tiling changes; counters then restart at 0).
+cudaError_t ensure_deps(lb_handle *h) {
+  if (h->deps_gen == h->plan_gen) return cudaSuccess;
+  std::vector<int> ofs, idx;
+  lbk::sweep_deps(h->store, h->p.nx, h->p.ny, h->p.walls, h->sweep_nstrips, h->sweep_base, h->sweep_extra,
+                  h->sweep_seg, ofs, idx);
+  const int ntiles = h->sweep_nstrips * h->sweep_nseg;
+  std::vector<int> csr(ofs);
+  csr.insert(csr.end(), idx.begin(), idx.end());
+  cudaError_t e = cudaStreamSynchronize(h->st);  // no launch may still use the old lists
+  if (e != cudaSuccess) return e;
+  cudaFree(h->d_dep);
+  cudaFree(h->d_done);
+  h->d_dep = nullptr;
+  h->d_done = nullptr;
+  h->deps_gen = -1;
+  e = cudaMalloc((void **)&h->d_dep, csr.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_dep, csr.data(), csr.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_done, (size_t)ntiles * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->d_done, 0, (size_t)ntiles * sizeof(unsigned));
+  if (e == cudaSuccess && !h->d_ticket) e = cudaMalloc((void **)&h->d_ticket, sizeof(unsigned));
+  if (e != cudaSuccess) return e;
+  h->deps_ntiles = ntiles;
+  h->epoch = 0;
+  h->deps_gen = h->plan_gen;
+  return cudaSuccess;
+}
+
+// nsteps >= 2 steps of a strip-sweep handle in multi-step launches.
+// Returns LB_OK, an error code, or 1 when that kernel cannot run here (the
+// caller then launches one kernel per step).
+int multi_steps(lb_handle *h, int64_t nsteps) {
+  if (h->persist_cap == 0) {
+    int cap = 0;
+    const cudaError_t e = lbk::persist_capacity(h->store, h->sweep_smem, &cap);
+    if (e != cudaSuccess) cudaGetLastError();
+    h->persist_cap = (e == cudaSuccess && cap > 0) ? cap : -1;
+  }
+  if (h->persist_cap < 0) return 1;
+  LB_CUDA(h, ensure_deps(h));
+  const int ntiles = h->deps_ntiles;
+  const lbk::SweepArgs A = sweep_args(h, nullptr);
+  const int grid = std::min(ntiles, h->persist_cap);
+  lbk::MultiOut Q{};
+  for (int b = 0; b < 2; ++b) {
+    Q.fout[b] = (float *)h->f[b ^ 1];  // a step reading buffer b writes buffer b ^ 1
+    Q.fdev[b] = dev16(h) ? (void *)((char *)h->f[b ^ 1] + (size_t)h->plane * sizeof(float)) : nullptr;
+  }
+  Q.total = h->d_out;
+  Q.arrivals = h->d_arrive;
+  for (int64_t done = 0; done < nsteps;) {
+    const int chunk = (int)std::min<int64_t>(nsteps - done, std::max<int64_t>(2, (1LL << 30) / ntiles));
+    lbk::PersistArgs P{};
+    P.nitems = ntiles;
+    P.nsteps = chunk;
+    P.kpar0 = h->cur;
+    P.epoch = h->epoch;
+    P.done = h->d_done;
+    P.dep_ofs = h->d_dep;
+    P.dep_idx = h->d_dep + ntiles + 1;
+    P.next = h->d_ticket;
+    LB_CUDA(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(unsigned), h->st));
+    const cudaError_t e = lbk::launch_sweep_multi(h->store, h->tmap, A, P, Q, grid, h->sweep_smem, h->st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lb_step: multi-step sweep kernel");
+    h->cur ^= chunk & 1;
+    h->step += chunk;
+    h->epoch += (unsigned)chunk;
+    h->cta_valid = true;
+    h->total_valid = true;
+    done += chunk;
+  }
+  return LB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -492,6 +576,11 @@ int lb_step(lb_handle *h, int64_t nsteps) {
       h->step++;
     }
   } else if (h->sweep) {
+    // Two steps or more (not monitoring): multi-step launches.
+    if (nsteps >= 2 && h->mon_cap == 0) {
+      const int rc = multi_steps(h, nsteps);
+      if (rc != 1) return rc;
+    }
     // Per-CTA mass/momentum records only on the last step: lb_reduce reads
     // only the current state's.
     for (int64_t k = 0; k < nsteps; k++) {
@@ -800,6 +889,9 @@ int lb_destroy(lb_handle *h) {
   cudaFree(h->d_cta);
   cudaFree(h->d_err);
   cudaFree(h->wide);
+  cudaFree(h->d_done);
+  cudaFree(h->d_dep);
+  cudaFree(h->d_ticket);
   delete h;
   return LB_OK;
 }

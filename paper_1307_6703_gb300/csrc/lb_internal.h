@@ -97,6 +97,21 @@ struct PersistArgs {
   const int *dep_idx;
   unsigned *next;       // ticket counter, zero at launch
 };
+// Outputs of the single-lattice multi-step kernel: the step that reads
+// buffer b writes fout[b] (and fdev[b], the deviation planes of 16-bit
+// storage); the last step's CTA records are summed into total[0..4] by the
+// CTA that finishes last (arrival counter *arrivals, zero between
+// launches).
+struct MultiOut {
+  float *fout[2];
+  void *fdev[2];
+  double *total;
+  unsigned *arrivals;
+};
+// One lattice, P.nsteps steps in one cooperative launch (P.kpar0 = the
+// input buffer of the first step; items are the tiles in index order).
+cudaError_t launch_sweep_multi(int store, const CUtensorMap (&maps)[2][2], const SweepArgs &A, const PersistArgs &P,
+                               const MultiOut &Q, int grid, size_t smem, cudaStream_t st);
 // Resident CTAs of the multi-step batched kernel on this device (its grid
 // may not exceed this: the dependency waits need every CTA resident).
 cudaError_t persist_capacity(int store, size_t smem, int *blocks);

@@ -868,93 +868,163 @@ __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Multi-step batched sweep: one launch runs P.nsteps steps of every lattice
-// of a work list.  CTAs take (step, item) tickets from a counter, step
-// after step, items in work-list order (longest first).  Instead of a grid-wide
-// barrier between steps, every item carries a completion counter done[item]
+// Multi-step sweeps.  One launch runs P.nsteps steps.  CTAs take
+// (step, item) tickets from a counter in step-major order, items in
+// work-list order.  Instead of a grid-wide barrier between steps, every
+// item (one tile of one lattice) carries a completion counter done[item]
 // (the steps it has finished, offset by P.epoch): before step k of an item,
 // its threads wait until every item it depends on -- the tiles of the same
 // lattice whose stored sites (ghost images included) its TMA boxes read,
 // and the tiles whose boxes read its own sites (they must have read the
-// buffer it is about to overwrite) -- has reached epoch + k.  Lattices
-// never wait for one another, and a tile starts as soon as its
-// neighbourhood has finished the previous step.  All CTAs are co-resident
-// (cooperative launch) and no step-(k+1) ticket is handed out before every
-// step-k ticket, so the smallest unfinished ticket can always proceed.  Every wait is bounded: on give-up the CTA sets its lattice's
-// error flag (bit 4 for a dependency wait) and stops, and the items that
-// depend on it give up in turn.
+// buffer it is about to overwrite) -- has reached epoch + k.  A tile starts
+// as soon as its neighbourhood has finished the previous step and a CTA
+// that is done takes the next ticket, so SMs do not idle at step
+// boundaries; lattices of a batch never wait for one another.  All CTAs are
+// co-resident (cooperative launch) and no step-(k+1) ticket is handed out
+// before every step-k ticket, so the smallest unfinished ticket always has
+// its dependencies done and can proceed.  Every wait is bounded: on give-up
+// the CTA sets the lattice's error flag (bit 4 for a dependency wait) and
+// stops, and the items that depend on it give up in turn.
+
+// The next ticket (thread 0 draws, the barrier publishes).
+__device__ __forceinline__ unsigned next_ticket(const PersistArgs &P, unsigned *slot) {
+  if (threadIdx.x == 0) *slot = atomicAdd(P.next, 1u);
+  __syncthreads();
+  return *slot;
+}
+
+// Bounded wait of the CTA's threads (one per dependency) until every item
+// item i depends on has finished `target` steps; false on give-up.  The
+// caller's next barrier publishes *ok.
+__device__ __forceinline__ void wait_deps(const PersistArgs &P, int i, unsigned target, int *err, int *ok) {
+  for (int d = P.dep_ofs[i] + (int)threadIdx.x; d < P.dep_ofs[i + 1]; d += kThreads) {
+    const unsigned *f = P.done + P.dep_idx[d];
+    uint32_t n = 0;
+    while ((int)(ld_acquire_gpu(f) - target) < 0) {
+      if (++n > kWaitLimit) {
+        *ok = 0;
+        atomicOr(err, 4);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+}
+
+// Release item i's step: its stores (generic proxy) before the counter,
+// ordered for the neighbours' TMA (async proxy) reads.
+__device__ __forceinline__ void release_item(const PersistArgs &P, int i, unsigned value) {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release_gpu(P.done + i, value);
+  }
+}
+
+// Before a CTA's second and later items: the ring's mbarriers are
+// initialised again by the sweep body.
+template <class St>
+__device__ __forceinline__ void inval_ring() {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  auto &S = *reinterpret_cast<SweepSmem<St::kSlotBytes> *>(smem_raw);
+  for (int q = 0; q < kPairs; ++q)
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[q])) : "memory");
+}
+
+// Batched form: items[i] names the lattice, tile and record; arguments and
+// tensor maps of every lattice (both buffer parities) in device memory.
 template <class St>
 __global__ void __launch_bounds__(kThreads, St::kMinBlocks)
 sweep_batch_persist_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restrict__ args,
                            const CUtensorMap *__restrict__ maps, const PersistArgs P) {
   __shared__ SweepArgs A;
   __shared__ int dep_ok;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  auto &S = *reinterpret_cast<SweepSmem<St::kSlotBytes> *>(smem_raw);
   __shared__ unsigned ticket;
   const int t = threadIdx.x;
   bool first = true;
   const unsigned total = (unsigned)P.nsteps * (unsigned)P.nitems;
   for (;;) {
-    // Tickets are handed out in step-major order: every item of step k is
-    // taken before any item of step k+1, so the smallest ticket not yet
-    // finished always has its dependencies (earlier tickets) done.
-    if (t == 0) ticket = atomicAdd(P.next, 1u);
-    __syncthreads();
-    const unsigned tk = ticket;
+    const unsigned tk = next_ticket(P, &ticket);
     if (tk >= total) break;
     const int k = (int)(tk / (unsigned)P.nitems), i = (int)(tk % (unsigned)P.nitems);
-    const int kpar = (P.kpar0 + k) & 1;
-    const bool records = k == P.nsteps - 1;
     const unsigned target = P.epoch + (unsigned)k;
-    {
-      const BatchItem it = items[i];
-      const int par = it.par0 ^ kpar;
-      const CUtensorMap *m = maps + 4 * it.inst + 2 * par;  // [instance][input buffer][map]
-      // Wait for the neighbourhood to finish step k-1 (one thread per
-      // dependency, bounded).  The barrier also ends the previous item.
-      if (t == 0) dep_ok = 1;
-      __syncthreads();
-      for (int d = P.dep_ofs[i] + t; d < P.dep_ofs[i + 1]; d += kThreads) {
-        const unsigned *f = P.done + P.dep_idx[d];
-        uint32_t n = 0;
-        while ((int)(ld_acquire_gpu(f) - target) < 0) {
-          if (++n > kWaitLimit) {
-            dep_ok = 0;
-            atomicOr(args[2 * it.inst].err, 4);
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      if (t == 0) {
-        A = args[2 * it.inst + par];
-        // the maps were written through the generic proxy (a host copy)
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m + 1) : "memory");
-        // the neighbours' stores, made visible by the acquires, for this
-        // CTA's TMA (async proxy) reads
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        if (!first) {  // the ring's barriers are initialised again by the sweep
-          for (int q = 0; q < kPairs; ++q)
-            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[q])) : "memory");
-        }
-      }
-      __syncthreads();
-      if (!dep_ok) return;
-      first = false;
-      const StepIO O{A.fout, A.fdev, A.partials, 0u, nullptr, nullptr, nullptr, 0.0};
-      if (!sweep_body<St, true>(m, m + 1, A, O, it.strip, it.seg, A.partials + 4 * (size_t)it.rec, records))
-        return;
-      // Release this item's step: its stores (generic proxy) before the
-      // counter, ordered for the neighbours' TMA (async proxy) reads.
+    const BatchItem it = items[i];
+    const int par = it.par0 ^ ((P.kpar0 + k) & 1);
+    const CUtensorMap *m = maps + 4 * it.inst + 2 * par;  // [instance][input buffer][map]
+    if (t == 0) dep_ok = 1;
+    __syncthreads();  // also ends the previous item
+    wait_deps(P, i, target, args[2 * it.inst].err, &dep_ok);
+    if (t == 0) {
+      A = args[2 * it.inst + par];
+      // the maps were written through the generic proxy (a host copy)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m + 1) : "memory");
+      // the neighbours' stores, made visible by the acquires, for this
+      // CTA's TMA (async proxy) reads
       asm volatile("fence.proxy.async.global;" ::: "memory");
-      __syncthreads();
-      if (t == 0) {
-        __threadfence();
-        st_release_gpu(P.done + i, target + 1u);
-      }
+      if (!first) inval_ring<St>();
     }
+    __syncthreads();
+    if (!dep_ok) return;
+    first = false;
+    const StepIO O{A.fout, A.fdev, A.partials, 0u, nullptr, nullptr, nullptr, 0.0};
+    if (!sweep_body<St, true>(m, m + 1, A, O, it.strip, it.seg, A.partials + 4 * (size_t)it.rec,
+                              k == P.nsteps - 1))
+      return;
+    release_item(P, i, target + 1u);
+  }
+}
+
+// Single-lattice form: item i is tile i (strip i % nstrips, segment
+// i / nstrips); arguments and maps are kernel parameters.  The last step
+// writes the per-tile records and the CTA that finishes last adds them into
+// `total` (mass, momentum, flags).
+template <class St>
+__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+sweep_multi_kernel(const __grid_constant__ CUtensorMap tin0, const __grid_constant__ CUtensorMap tdev0,
+                   const __grid_constant__ CUtensorMap tin1, const __grid_constant__ CUtensorMap tdev1,
+                   const SweepArgs A, const PersistArgs P, const MultiOut Q) {
+  __shared__ int dep_ok;
+  __shared__ unsigned ticket;
+  const int t = threadIdx.x;
+  bool first = true;
+  const unsigned total = (unsigned)P.nsteps * (unsigned)P.nitems;
+  for (;;) {
+    const unsigned tk = next_ticket(P, &ticket);
+    if (tk >= total) break;
+    const int k = (int)(tk / (unsigned)P.nitems), i = (int)(tk % (unsigned)P.nitems);
+    const unsigned target = P.epoch + (unsigned)k;
+    const int par = (P.kpar0 + k) & 1;  // input buffer of step k
+    const bool last = k == P.nsteps - 1;
+    if (t == 0) dep_ok = 1;
+    __syncthreads();  // also ends the previous item
+    wait_deps(P, i, target, A.err, &dep_ok);
+    if (t == 0) {
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      if (!first) inval_ring<St>();
+    }
+    __syncthreads();
+    if (!dep_ok) {
+      if (t == 0) Q.total[4] = 1.0;  // the sums of this launch will not be written
+      return;
+    }
+    first = false;
+    StepIO O;
+    O.fout = par ? Q.fout[1] : Q.fout[0];  // (no dynamic indexing of the parameter space)
+    O.fdev = par ? Q.fdev[1] : Q.fdev[0];
+    O.recs = A.partials;
+    O.nrec = (unsigned)P.nitems;
+    O.arrivals = last ? Q.arrivals : nullptr;
+    O.total = Q.total;
+    O.monitor = nullptr;
+    O.mon_step = 0.0;
+    if (!sweep_body<St, true>(par ? &tin1 : &tin0, par ? &tdev1 : &tdev0, A, O, i % A.nstrips, i / A.nstrips,
+                              A.partials + 4 * (size_t)i, last)) {
+      if (t == 0) Q.total[4] = 1.0;
+      return;
+    }
+    release_item(P, i, target + 1u);
   }
 }
 
@@ -1107,12 +1177,41 @@ cudaError_t launch_batch_persist_one(const BatchItem *items, const SweepArgs *ar
 }
 
 template <class St>
+cudaError_t launch_multi_one(const CUtensorMap (&m)[2][2], const SweepArgs &A, const PersistArgs &P,
+                             const MultiOut &Q, int grid, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_multi_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_multi_kernel<St>, m[0][0], m[0][1], m[1][0], m[1][1], A, P, Q);
+}
+
+template <class St>
 cudaError_t persist_capacity_one(size_t smem, int *blocks) {
+  // the smaller residency of the two multi-step kernels
   cudaError_t e = cudaFuncSetAttribute(sweep_batch_persist_kernel<St>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_multi_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, per_sm2 = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_persist_kernel<St>, kThreads, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, sweep_multi_kernel<St>, kThreads, smem);
+  per_sm = std::min(per_sm, per_sm2);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   *blocks = per_sm * sms;
@@ -1195,6 +1294,16 @@ cudaError_t persist_capacity(int store, size_t smem, int *blocks) {
     case kStoreF32: return persist_capacity_one<StoreF32>(smem, blocks);
     case kStoreBF16: return persist_capacity_one<StoreBF16>(smem, blocks);
     case kStoreFP16: return persist_capacity_one<StoreFP16>(smem, blocks);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep_multi(int store, const CUtensorMap (&maps)[2][2], const SweepArgs &A, const PersistArgs &P,
+                               const MultiOut &Q, int grid, size_t smem, cudaStream_t st) {
+  switch (store) {
+    case kStoreF32: return launch_multi_one<StoreF32>(maps, A, P, Q, grid, smem, st);
+    case kStoreBF16: return launch_multi_one<StoreBF16>(maps, A, P, Q, grid, smem, st);
+    case kStoreFP16: return launch_multi_one<StoreFP16>(maps, A, P, Q, grid, smem, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,8 +1,8 @@
-"""The multi-step batched sweep (lb_batch_step with nsteps >= 2: one
-cooperative launch per chunk of steps over the whole work list, per-item
+"""The multi-step sweeps (lb_step and lb_batch_step with nsteps >= 2: one
+cooperative launch per chunk of steps, (step, item) tickets and per-item
 completion counters in place of a grid-wide barrier between steps) against
-the one-launch-per-step batched sweep (lb_batch_step(1) repeated) and
-against the FP64 oracle.
+one launch per step (lb_step(1) / lb_batch_step(1) repeated) and against the
+FP64 oracle.
 
 Both launch forms run the same per-site arithmetic on the same items; they
 are different kernels, compiled separately, so they are compared to FP32
@@ -92,6 +92,52 @@ def test_multistep_matches_single_steps(case, prec):
     assert abs(ra[1][0] - rb[1][0]) <= 1e-7 * ra[1][0]
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", [LB_FP32, LB_BF16DEV, LB_FP16DEV])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}{'w' if c[2] else 'p'}s{c[3]}")
+def test_single_lattice_multistep_matches_single_steps(case, prec):
+    nx, ny, walls, seg, steps = case
+    w = C2(0.05).with_(nx=nx, ny=ny, walls=walls, u_bot=-0.05 if walls else 0.0,
+                       u_top=0.05 if walls else 0.0, lam=float(nx // 2))
+    a = _solver(w, prec).init_fields(noise_field(w))
+    b = _solver(w, prec).init_fields(noise_field(w))
+    if seg:
+        a.set_seg_h(seg)
+        b.set_seg_h(seg)
+    for _ in range(steps):
+        a.step(1)
+    b.step(steps)
+    assert a.t == b.t == steps
+    err, same = _state_diff(prec, a.get_state(), b.get_state())
+    print(f"single {nx}x{ny} prec {prec}: max rel diff {err:.2e}, bitwise {same}")
+    assert err <= 2e-6
+    ra, rb = a.reduce(), b.reduce()
+    assert ra[0] == rb[0] == 0
+    assert abs(ra[1][0] - rb[1][0]) <= 1e-7 * ra[1][0]
+    a.close()
+    b.close()
+
+
+def test_single_lattice_multistep_full_size():
+    """The 4096 x 1024 workload at the tilings the autotuner tries (48- and
+    24-row segments: 792 and 1548 tiles, more than one wave of CTAs): 12
+    steps in one launch against 12 launches, and the fused sums of the last
+    step against a fresh reduction of the same state."""
+    from paper_1307_6703_gb300.workloads import C4
+    for seg in (48, 24):
+        a = solver_for(C4, LB_FP32).init_noise(7, C4.rho_mean, C4.noise).set_seg_h(seg)
+        b = solver_for(C4, LB_FP32).init_noise(7, C4.rho_mean, C4.noise).set_seg_h(seg)
+        for _ in range(12):
+            a.step(1)
+        b.step(12)
+        err, same = _state_diff(LB_FP32, a.get_state(), b.get_state())
+        print(f"4096x1024 seg {seg}: max rel diff {err:.2e}, bitwise {same}")
+        assert err <= 2e-6
+        ra, rb = a.reduce(), b.reduce()
+        assert ra[0] == rb[0] == 0 and abs(ra[1][0] - rb[1][0]) <= 1e-7 * ra[1][0]
+        a.close()
+        b.close()
 
 
 @pytest.mark.parametrize("prec", [LB_FP32, LB_BF16DEV])
