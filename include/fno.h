@@ -84,6 +84,23 @@ int fno_adam(fno_handle *h, float lr, float beta1, float beta2, float eps, int32
 int fno_destroy(fno_handle *h);
 const char *fno_last_error(const fno_handle *h);
 
+/* The network's matrix product on the tensor cores, as a building block
+ * (the paper has no counterpart): for b = 0 .. batch-1,
+ *   C[b](m, n) = sum_k X[b](m, k) Y[b](n, k) + beta C[b](m, n)
+ * with BF16 operands and FP32 accumulation.  X is M x K with row pitch ldx,
+ * Y is N x K with row pitch ldy (k contiguous in both), batch strides sX,
+ * sY in elements (0: one matrix shared by every batch); pitches and strides
+ * multiples of 8 elements, ldx, ldy >= K, bases 16-byte aligned.  C is FP32,
+ * element (b, m, n) at C + b sC + m cm + n cn (any strides, so C or its
+ * transpose).  X, Y, C and err are DEVICE pointers; err points to an int the
+ * kernel sets to 1 when one of its bounded waits gave up (results then
+ * meaningless).  Enqueued on `stream` (cudaStream_t, NULL = default) without
+ * synchronising.  Errors: LB_ERR_ARG (shapes, pitches, alignment, null
+ * pointers), LB_ERR_CUDA.                                                  */
+int fno_gemm_bf16(const void *X, int32_t ldx, int64_t sX, const void *Y, int32_t ldy, int64_t sY, float *C,
+                  int64_t cm, int64_t cn, int64_t sC, int32_t M, int32_t N, int32_t K, int32_t batch, float beta,
+                  int *err, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

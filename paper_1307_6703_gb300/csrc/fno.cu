@@ -1,11 +1,17 @@
 // fno.cu -- the learned warm start (include/fno.h): forward and backward
 // passes of a small Fourier neural operator, its loss and its Adam update,
 // as CUDA kernels of this library.  The truncated Fourier transforms along x
-// and the per-site channel mixing are plain GEMMs and go to cuBLAS (BF16
-// inputs, FP32 accumulation, tensor cores); the transforms along y, the
+// and the per-site channel mixing are matrix products: in BF16 mode they run
+// on the tensor cores through this library's tcgen05 product (gemm_tc.cu:
+// BF16 operands with the contracted index contiguous, FP32 accumulation),
+// in FP32 mode through its SIMT product; the transforms along y, the
 // per-mode complex channel mixing, the lift, the projection, the
 // activations, the loss, every reduction of the backward pass and the
-// optimizer are the kernels below.
+// optimizer are the kernels below.  The tensor-core product contracts over
+// the contiguous index of both operands, so the kernels that write BF16
+// copies also keep, where a product contracts over channels, a site-major
+// copy ([b][site][channel]), and the weights and DFT tables have transposed
+// BF16 copies.
 //
 // Activation layout: [batch][channel][ny][nx] (x fastest).  A "row" of the
 // x-transform is one (batch, channel, y) line, so the x-transform of all
@@ -17,11 +23,11 @@
 #include <string>
 #include <vector>
 
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "fno.h"
+#include "gemm_tc.h"
 
 namespace {
 
@@ -478,7 +484,7 @@ __global__ void ydft_back_kernel(const float *__restrict__ dS, const float2 *__r
 // Truncated DFT matrices for nx: Fx[x][j] (forward, e^{-i phi}) and
 // Fxi[j][x] (real inverse with c_kx and 1/(nx ny)).
 __global__ void dft_tables_kernel(int nx, int ny, int mx, int my, float *Fx, float *Fxi, __nv_bfloat16 *Fxb,
-                                  __nv_bfloat16 *Fxib, float2 *Ty) {
+                                  __nv_bfloat16 *Fxib, __nv_bfloat16 *FxTb, __nv_bfloat16 *FxiTb, float2 *Ty) {
   // y twiddles: Ty[k][y] = (cos, sin)(2 pi ky y / ny), argument reduced mod ny
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < my * ny; i += gridDim.x * blockDim.x) {
     const int k = i / ny, y = i - k * ny;
@@ -501,6 +507,11 @@ __global__ void dft_tables_kernel(int nx, int ny, int mx, int my, float *Fx, flo
     Fxb[x * 2 * mx + mx + k] = __float2bfloat16_rn(-sn);
     Fxib[k * nx + x] = __float2bfloat16_rn(sc * cs);
     Fxib[(mx + k) * nx + x] = __float2bfloat16_rn(-sc * sn);
+    // transposed copies: FxT[j][x] = Fx[x][j], FxiT[x][j] = Fxi[j][x]
+    FxTb[k * nx + x] = __float2bfloat16_rn(cs);
+    FxTb[(mx + k) * nx + x] = __float2bfloat16_rn(-sn);
+    FxiTb[x * 2 * mx + k] = __float2bfloat16_rn(sc * cs);
+    FxiTb[x * 2 * mx + mx + k] = __float2bfloat16_rn(-sc * sn);
   }
 }
 
@@ -519,6 +530,42 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
   }
 }
 
+// out[b][c][r] = in[b][r][c] for batch b (R x Cc BF16 matrices), through
+// 32 x 32 shared-memory tiles so that reads and writes are both coalesced.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, long long R, int Cc,
+                                      __nv_bfloat16 *__restrict__ out) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32, b = blockIdx.z;
+  in += (long long)b * R * Cc;
+  out += (long long)b * R * Cc;
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+    const int rr = i / 32, cc = i % 32;
+    if (r0 + rr < R && c0 + cc < Cc) tile[rr][cc] = in[(r0 + rr) * Cc + c0 + cc];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+    const int cc = i / 32, rr = i % 32;
+    if (r0 + rr < R && c0 + cc < Cc) out[(long long)(c0 + cc) * R + r0 + rr] = tile[rr][cc];
+  }
+}
+
+// Transposed BF16 weights for the tensor-core products: WT_l[c][o] =
+// W_l[o][c] (layer l at l C C), then Q1T[c][h] = Q1[h][c].
+__global__ void weights_t_kernel(const __nv_bfloat16 *__restrict__ prmb, Offsets o, int C, int H, int L,
+                                 __nv_bfloat16 *__restrict__ wt) {
+  const int n = L * C * C + C * H;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < L * C * C) {
+      const int l = i / (C * C), r = i - l * C * C, c = r / C, oo = r - c * C;
+      wt[i] = prmb[o.W[l] + (size_t)oo * C + c];
+    } else {
+      const int r = i - L * C * C, c = r / H, hh = r - c * H;
+      wt[i] = prmb[o.Q1 + (size_t)hh * C + c];
+    }
+  }
+}
+
 __global__ void to_bf16_kernel(const float *__restrict__ a, long long n, __nv_bfloat16 *__restrict__ b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = __float2bfloat16_rn(a[i]);
@@ -531,7 +578,6 @@ __global__ void to_bf16_kernel(const float *__restrict__ a, long long n, __nv_bf
 struct fno_handle {
   fno_config c{};
   cudaStream_t st = nullptr;
-  cublasHandle_t blas = nullptr;
   Offsets o{};
   float *prm = nullptr, *grd = nullptr, *m1 = nullptr, *m2 = nullptr;
   __nv_bfloat16 *prmb = nullptr;
@@ -546,7 +592,11 @@ struct fno_handle {
   double *partial = nullptr, *loss = nullptr, *rpart = nullptr;
   float *wpart = nullptr;  // per-field weight gradients [B][max(C, H) * C]
   float *Fx = nullptr, *Fxi = nullptr;
-  __nv_bfloat16 *Fxb = nullptr, *Fxib = nullptr;
+  __nv_bfloat16 *Fxb = nullptr, *Fxib = nullptr, *FxTb = nullptr, *FxiTb = nullptr;
+  // site-major BF16 copies ([b][site][channel]) for the products that
+  // contract over channels; transposed BF16 weights (W_l^T per layer, Q1^T)
+  __nv_bfloat16 *VbT[kMaxLayers + 1] = {}, *dZT = nullptr, *dhpT = nullptr, *wTb = nullptr;
+  int *gerr = nullptr;  // set by a tensor-core product whose bounded wait gave up
   float2 *Ty = nullptr;
   int tab_nx = 0, tab_ny = 0;
   int B = 0, nx = 0, ny = 0;  // shape of the last forward pass
@@ -572,25 +622,35 @@ int ffail(fno_handle *h, int code, const std::string &m) {
                    std::string(#call) + ": " + cudaGetErrorString(e_));                                        \
   } while (0)
 
-#define FNO_BLAS(h, call)                                                                                      \
+#define FNO_GEMM(h, call)                                                                                      \
   do {                                                                                                         \
-    cublasStatus_t s_ = (call);                                                                                \
-    if (s_ != CUBLAS_STATUS_SUCCESS) return ffail(h, LB_ERR_CUDA, std::string(#call) + ": cuBLAS status " + std::to_string((int)s_)); \
+    cudaError_t e_ = (call);                                                                                   \
+    if (e_ != cudaSuccess) return ffail(h, LB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
   } while (0)
 
-// Row-major C[m x n] = op(A)[m x k] op(B)[k x n] + beta C, strided batches.
-// A16 / B16: BF16 copies used when the handle's GEMMs run in BF16.
-cublasStatus_t gemm(fno_handle *h, bool tA, bool tB, int m, int n, int k, const float *A32,
-                    const __nv_bfloat16 *A16, int lda, long long sA, const float *B32, const __nv_bfloat16 *B16, int ldb,
-                    long long sB, float *C, int ldc, long long sC, int batch, float beta) {
-  const bool bf = h->c.gemm_bf16 != 0;
-  const void *A = bf ? (const void *)A16 : (const void *)A32;
-  const void *Bm = bf ? (const void *)B16 : (const void *)B32;
-  const cudaDataType_t t = bf ? CUDA_R_16BF : CUDA_R_32F;
-  const float alpha = 1.0f;
-  return cublasGemmStridedBatchedEx(h->blas, tB ? CUBLAS_OP_T : CUBLAS_OP_N, tA ? CUBLAS_OP_T : CUBLAS_OP_N, n, m, k,
-                                    &alpha, Bm, t, ldb, sB, A, t, lda, sA, &beta, C, CUDA_R_32F, ldc, sC, batch,
-                                    CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+// K-split of the weight-gradient products (K = sites): the split partial
+// products land in separate slices of wpart, summed with the fields.
+constexpr int kWSplit = 8;
+
+// Tensor-core product (BF16 mode): C(m, n) = sum_k X(m, k) Y(n, k), see
+// gemm_tc.h for the argument layout.
+cudaError_t tcg(fno_handle *h, const __nv_bfloat16 *X, int ldx, long long sX, const __nv_bfloat16 *Y, int ldy,
+                long long sY, float *C, long long cm, long long cn, long long sC, int M, int N, int K, int batch,
+                int ksplit, float beta) {
+  return tc::gemm_tn_bf16(X, ldx, sX, Y, ldy, sY, C, cm, cn, sC, M, N, K, batch, ksplit, beta, h->gerr, h->st);
+}
+
+// SIMT product (FP32 mode): C(m, n) = sum_k A(m, k) B(k, n), general strides.
+cudaError_t sg(fno_handle *h, const float *A, long long am, long long ak, long long sA, const float *B, long long bk,
+               long long bn, long long sB, float *C, long long cm, long long cn, long long sC, int M, int N, int K,
+               int batch, float beta) {
+  return tc::gemm_f32(A, am, ak, sA, B, bk, bn, sB, C, cm, cn, sC, M, N, K, batch, beta, h->st);
+}
+
+// Site-major copy of a [B][rows][S] BF16 activation: out[b][s][row].
+void site_major(fno_handle *h, const __nv_bfloat16 *in, int B, int rows, long long S, __nv_bfloat16 *out) {
+  const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((S + 31) / 32), (unsigned)B);
+  transpose_bf16_kernel<<<grid, 256, 0, h->st>>>(in, rows, (int)S, out);
 }
 
 // out[ch] = sum over (b, s) of a[b, ch, s] for the C channels of a.
@@ -617,13 +677,16 @@ cudaError_t alloc(T **p, long long n) {
 
 void free_workspace(fno_handle *h) {
   void *ps[] = {h->x0, h->A, h->G, h->Gb, h->hp, h->out, h->dout, h->dhp, h->dhpb, h->dV, h->dZ, h->dZb, h->dG,
-                h->dA, h->dAb, h->dY, h->dS, h->partial, h->loss, h->Fx, h->Fxi, h->Fxb, h->Fxib, h->rpart, h->wpart, h->Ty};
+                h->dA, h->dAb, h->dY, h->dS, h->partial, h->loss, h->Fx, h->Fxi, h->Fxb, h->Fxib, h->rpart, h->wpart, h->Ty,
+                h->FxTb, h->FxiTb, h->dZT, h->dhpT, h->wTb, h->gerr};
   for (void *p : ps) cudaFree(p);
   for (int l = 0; l <= kMaxLayers; l++) {
     cudaFree(h->V[l]);
     cudaFree(h->Vb[l]);
+    cudaFree(h->VbT[l]);
     h->V[l] = nullptr;
     h->Vb[l] = nullptr;
+    h->VbT[l] = nullptr;
   }
   for (int l = 0; l < kMaxLayers; l++) {
     cudaFree(h->Z[l]);
@@ -645,7 +708,13 @@ cudaError_t alloc_workspace(fno_handle *h) {
   for (int l = 0; l <= c.layers && e == cudaSuccess; l++) {
     e = alloc(&h->V[l], h->cap_bcs);
     if (e == cudaSuccess) e = alloc(&h->Vb[l], h->cap_bcs);
+    if (e == cudaSuccess && c.gemm_bf16) e = alloc(&h->VbT[l], h->cap_bcs);
   }
+  if (e == cudaSuccess && c.gemm_bf16) e = alloc(&h->dZT, h->cap_bcs);
+  if (e == cudaSuccess && c.gemm_bf16) e = alloc(&h->dhpT, h->cap_bhs);
+  if (e == cudaSuccess) e = alloc(&h->wTb, (long long)c.layers * c.width * c.width + (long long)c.width * c.hidden);
+  if (e == cudaSuccess) e = alloc(&h->gerr, 1);
+  if (e == cudaSuccess) e = cudaMemset(h->gerr, 0, sizeof(int));
   for (int l = 0; l < c.layers && e == cudaSuccess; l++) {
     e = alloc(&h->Z[l], h->cap_bcs);
     if (e == cudaSuccess) e = alloc(&h->Sh[l], h->cap_modes);
@@ -670,12 +739,14 @@ cudaError_t alloc_workspace(fno_handle *h) {
   if (e == cudaSuccess)
     e = alloc(&h->rpart, std::max((long long)std::max(c.width * kFeatures, c.hidden * c.outputs) * kOuterBlocks,
                                   (long long)std::max(std::max(c.width, c.hidden), c.outputs) * kReduceBlocks));
-  if (e == cudaSuccess) e = alloc(&h->wpart, B * (long long)std::max(c.width, c.hidden) * c.width);
+  if (e == cudaSuccess) e = alloc(&h->wpart, B * kWSplit * (long long)std::max(c.width, c.hidden) * c.width);
   if (e == cudaSuccess) e = alloc(&h->loss, 1);
   if (e == cudaSuccess) e = alloc(&h->Fx, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Fxi, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Fxb, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Fxib, (long long)c.nx_max * 2 * c.modes_x);
+  if (e == cudaSuccess) e = alloc(&h->FxTb, (long long)c.nx_max * 2 * c.modes_x);
+  if (e == cudaSuccess) e = alloc(&h->FxiTb, (long long)c.nx_max * 2 * c.modes_x);
   if (e == cudaSuccess) e = alloc(&h->Ty, (long long)c.ny_max * c.modes_y);
   return e;
 }
@@ -693,6 +764,9 @@ int fno_create(const fno_config *cfg, fno_handle **out) {
       c.modes_y > c.ny_max || c.width * c.modes_y * 2 * (int)sizeof(float) > 48 * 1024 || c.outputs < 1 ||
       c.outputs > kMaxOutputs)
     return ffail(nullptr, LB_ERR_ARG, "fno_create: bad sizes");
+  if (c.gemm_bf16 && (c.width % 8 || c.hidden % 8 || (2 * c.modes_x) % 8))
+    return ffail(nullptr, LB_ERR_ARG, "fno_create: BF16 tensor-core products need width, hidden and 2 modes_x "
+                                      "divisible by 8");
   fno_handle *h = new (std::nothrow) fno_handle();
   if (!h) return ffail(nullptr, LB_ERR_OOM, "fno_create: host allocation failed");
   h->c = c;
@@ -715,10 +789,6 @@ int fno_create(const fno_config *cfg, fno_handle **out) {
     fno_destroy(h);
     return ffail(nullptr, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, m);
   }
-  if (cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(h->blas, h->st) != CUBLAS_STATUS_SUCCESS) {
-    fno_destroy(h);
-    return ffail(nullptr, LB_ERR_CUDA, "fno_create: cuBLAS initialisation failed");
-  }
   *out = h;
   return LB_OK;
 }
@@ -730,6 +800,8 @@ int fno_set_params(fno_handle *h, const float *host) {
   const long long np = (long long)h->o.total;
   FNO_CUDA(h, cudaMemcpyAsync(h->prm, host, np * sizeof(float), cudaMemcpyHostToDevice, h->st));
   to_bf16_kernel<<<blocks_for(np), kThreads, 0, h->st>>>(h->prm, np, h->prmb);
+  weights_t_kernel<<<blocks_for(np), kThreads, 0, h->st>>>(h->prmb, h->o, h->c.width, h->c.hidden, h->c.layers,
+                                                           h->wTb);
   FNO_CUDA(h, cudaGetLastError());
   FNO_CUDA(h, cudaStreamSynchronize(h->st));
   return LB_OK;
@@ -754,13 +826,14 @@ int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *p
   const fno_config &c = h->c;
   if (B < 1 || B > c.batch_max || nx > c.nx_max || ny > c.ny_max || nx < 2 * c.modes_x || ny < c.modes_y)
     return ffail(h, LB_ERR_ARG, "fno_forward: batch or lattice outside the workspace bounds");
+  if (c.gemm_bf16 && nx % 8) return ffail(h, LB_ERR_ARG, "fno_forward: BF16 products need nx divisible by 8");
   const int C = c.width, H = c.hidden, L = c.layers, mx = c.modes_x, my = c.modes_y;
   const long long S = (long long)nx * ny;
   const int R = B * C * ny;
   cudaStream_t st = h->st;
   if (h->tab_nx != nx || h->tab_ny != ny) {
     dft_tables_kernel<<<blocks_for((long long)std::max(nx * mx, ny * my)), kThreads, 0, st>>>(
-        nx, ny, mx, my, h->Fx, h->Fxi, h->Fxb, h->Fxib, h->Ty);
+        nx, ny, mx, my, h->Fx, h->Fxi, h->Fxb, h->Fxib, h->FxTb, h->FxiTb, h->Ty);
     FNO_CUDA(h, cudaGetLastError());
     h->tab_nx = nx;
     h->tab_ny = ny;
@@ -769,27 +842,41 @@ int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *p
   features_kernel<<<blocks_for((long long)B * S), kThreads, 0, st>>>(params_dev, B, nx, ny, h->x0);
   lift_kernel<<<grid2(S, B * C), kThreads, 0, st>>>(h->x0, P + h->o.P, P + h->o.p, C, S, h->V[0], h->Vb[0]);
   FNO_CUDA(h, cudaGetLastError());
+  const bool bf = c.gemm_bf16 != 0;
+  if (bf) site_major(h, h->Vb[0], B, C, S, h->VbT[0]);
+  const long long CS = (long long)C * S;
   for (int l = 0; l < L; l++) {
     // x-transform of every line: A[R, 2mx] = V[R, nx] Fx[nx, 2mx]
-    FNO_BLAS(h, gemm(h, false, false, R, 2 * mx, nx, h->V[l], h->Vb[l], nx, 0, h->Fx, h->Fxb, 2 * mx, 0, h->A, 2 * mx,
-                     0, 1, 0.f));
+    if (bf)
+      FNO_GEMM(h, tcg(h, h->Vb[l], nx, 0, h->FxTb, nx, 0, h->A, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 1, 0.f));
+    else
+      FNO_GEMM(h, sg(h, h->V[l], nx, 1, 0, h->Fx, 2 * mx, 1, 0, h->A, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 0.f));
     ydft_kernel<<<B * C, kThreads, 0, st>>>(h->A, h->Ty, ny, mx, my, h->Sh[l]);
     mix_iy_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->Sh[l], P + h->o.Rr[l], P + h->o.Ri[l], h->Ty,
                                                                           C, ny, mx, my, h->G, h->Gb);
     FNO_CUDA(h, cudaGetLastError());
     // inverse x-transform into z: Z[R, nx] = G[R, 2mx] Fxi[2mx, nx]
-    FNO_BLAS(h, gemm(h, false, false, R, nx, 2 * mx, h->G, h->Gb, 2 * mx, 0, h->Fxi, h->Fxib, nx, 0, h->Z[l], nx, 0, 1,
-                     0.f));
-    // z[b] += W v[b]  (one GEMM per field, strided)
-    FNO_BLAS(h, gemm(h, false, false, C, (int)S, C, P + h->o.W[l], h->prmb + h->o.W[l], C, 0, h->V[l], h->Vb[l], (int)S,
-                     (long long)C * S, h->Z[l], (int)S, (long long)C * S, B, 1.f));
+    if (bf)
+      FNO_GEMM(h, tcg(h, h->Gb, 2 * mx, 0, h->FxiTb, 2 * mx, 0, h->Z[l], nx, 1, 0, R, nx, 2 * mx, 1, 1, 0.f));
+    else
+      FNO_GEMM(h, sg(h, h->G, 2 * mx, 1, 0, h->Fxi, nx, 1, 0, h->Z[l], nx, 1, 0, R, nx, 2 * mx, 1, 0.f));
+    // z[b][o][s] += sum_c W[o][c] v[b][c][s]  (tensor cores: sites as rows,
+    // the site-major copy of v against W, written transposed)
+    if (bf)
+      FNO_GEMM(h, tcg(h, h->VbT[l], C, CS, h->prmb + h->o.W[l], C, 0, h->Z[l], 1, S, CS, (int)S, C, C, B, 1, 1.f));
+    else
+      FNO_GEMM(h, sg(h, P + h->o.W[l], C, 1, 0, h->V[l], S, 1, CS, h->Z[l], S, 1, CS, C, (int)S, C, B, 1.f));
     bias_act_kernel<<<grid2(S, B * C), kThreads, 0, st>>>(h->Z[l], P + h->o.w[l], C, S, l < L - 1 ? 1 : 0,
                                                            h->V[l + 1], h->Vb[l + 1]);
     FNO_CUDA(h, cudaGetLastError());
+    if (bf) site_major(h, h->Vb[l + 1], B, C, S, h->VbT[l + 1]);
   }
-  // projection: hp[b] = Q1 v_L[b]; out = Q2 gelu(hp + q1) + q2
-  FNO_BLAS(h, gemm(h, false, false, H, (int)S, C, P + h->o.Q1, h->prmb + h->o.Q1, C, 0, h->V[L], h->Vb[L], (int)S,
-                   (long long)C * S, h->hp, (int)S, (long long)H * S, B, 0.f));
+  // projection: hp[b][h][s] = sum_c Q1[h][c] v_L[b][c][s]; out = Q2 gelu(hp + q1) + q2
+  if (bf)
+    FNO_GEMM(h, tcg(h, h->VbT[L], C, CS, h->prmb + h->o.Q1, C, 0, h->hp, 1, S, (long long)H * S, (int)S, H, C, B, 1,
+                    0.f));
+  else
+    FNO_GEMM(h, sg(h, P + h->o.Q1, C, 1, 0, h->V[L], S, 1, CS, h->hp, S, 1, (long long)H * S, H, (int)S, C, B, 0.f));
   project_kernel<<<grid2(S, B), kThreads, 0, st>>>(h->hp, P + h->o.q1, P + h->o.Q2, P + h->o.q2, H,
                                                                      c.outputs, S, h->out, out);
   FNO_CUDA(h, cudaGetLastError());
@@ -821,41 +908,66 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
   project_back_kernel<<<grid2(S, B * H), kThreads, 0, st>>>(h->hp, P + o.Q2, h->dout, H, O, S, h->dhp, h->dhpb);
   chan_reduce(h, h->dhp, B, H, S, g + o.q1);
   FNO_CUDA(h, cudaGetLastError());
-  // dQ1 = sum_b dhp[b] v_L[b]^T: one batched GEMM into per-field parts, then their sum
-  FNO_BLAS(h, gemm(h, false, true, H, C, (int)S, h->dhp, h->dhpb, (int)S, (long long)H * S, h->V[L], h->Vb[L], (int)S,
-                   (long long)C * S, h->wpart, C, (long long)H * C, B, 0.f));
-  sum_fields_kernel<<<blocks_for((long long)H * C), kThreads, 0, st>>>(h->wpart, B, H * C, g + o.Q1);
-  FNO_BLAS(h, gemm(h, true, false, C, (int)S, H, P + o.Q1, h->prmb + o.Q1, C, 0, h->dhp, h->dhpb, (int)S,
-                   (long long)H * S, h->dV, (int)S, (long long)C * S, B, 0.f));
+  const bool bf = c.gemm_bf16 != 0;
+  const long long CS = (long long)C * S, HS = (long long)H * S;
+  // dQ1 = sum_b dhp[b] v_L[b]^T: per-field (and K-split) parts, then their sum
+  int parts = B;
+  if (bf) {
+    parts = B * kWSplit;
+    FNO_GEMM(h, tcg(h, h->dhpb, (int)S, HS, h->Vb[L], (int)S, CS, h->wpart, C, 1, (long long)H * C, H, C, (int)S, B,
+                    kWSplit, 0.f));
+  } else {
+    FNO_GEMM(h, sg(h, h->dhp, S, 1, HS, h->V[L], 1, S, CS, h->wpart, C, 1, (long long)H * C, H, C, (int)S, B, 0.f));
+  }
+  sum_fields_kernel<<<blocks_for((long long)H * C), kThreads, 0, st>>>(h->wpart, parts, H * C, g + o.Q1);
+  // dv[b][c][s] = sum_h Q1[h][c] dhp[b][h][s]
+  if (bf) {
+    site_major(h, h->dhpb, B, H, S, h->dhpT);
+    FNO_GEMM(h, tcg(h, h->dhpT, H, HS, h->wTb + (size_t)L * C * C, H, 0, h->dV, 1, S, CS, (int)S, C, H, B, 1, 0.f));
+  } else {
+    FNO_GEMM(h, sg(h, P + o.Q1, 1, C, 0, h->dhp, S, 1, HS, h->dV, S, 1, CS, C, (int)S, H, B, 0.f));
+  }
   for (int l = L - 1; l >= 0; l--) {
     act_back_kernel<<<blocks_for(BCS), kThreads, 0, st>>>(h->dV, h->Z[l], BCS, l < L - 1 ? 1 : 0, h->dZ, h->dZb);
     chan_reduce(h, h->dZ, B, C, S, g + o.w[l]);
     FNO_CUDA(h, cudaGetLastError());
     // dW = sum_b dz[b] v[b]^T
-    FNO_BLAS(h, gemm(h, false, true, C, C, (int)S, h->dZ, h->dZb, (int)S, (long long)C * S, h->V[l], h->Vb[l], (int)S,
-                     (long long)C * S, h->wpart, C, (long long)C * C, B, 0.f));
-    sum_fields_kernel<<<blocks_for((long long)C * C), kThreads, 0, st>>>(h->wpart, B, C * C, g + o.W[l]);
+    if (bf)
+      FNO_GEMM(h, tcg(h, h->dZb, (int)S, CS, h->Vb[l], (int)S, CS, h->wpart, C, 1, (long long)C * C, C, C, (int)S, B,
+                      kWSplit, 0.f));
+    else
+      FNO_GEMM(h, sg(h, h->dZ, S, 1, CS, h->V[l], 1, S, CS, h->wpart, C, 1, (long long)C * C, C, C, (int)S, B, 0.f));
+    sum_fields_kernel<<<blocks_for((long long)C * C), kThreads, 0, st>>>(h->wpart, parts, C * C, g + o.W[l]);
     // spectral path: dG = dz Fxi^T, then the adjoints of the mixing and of the y-transform
-    FNO_BLAS(h, gemm(h, false, true, R, 2 * mx, nx, h->dZ, h->dZb, nx, 0, h->Fxi, h->Fxib, nx, 0, h->dG, 2 * mx, 0, 1,
-                     0.f));
+    if (bf)
+      FNO_GEMM(h, tcg(h, h->dZb, nx, 0, h->Fxib, nx, 0, h->dG, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 1, 0.f));
+    else
+      FNO_GEMM(h, sg(h, h->dZ, nx, 1, 0, h->Fxi, 1, nx, 0, h->dG, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 0.f));
     mix_iy_back_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->dG, P + o.Rr[l], P + o.Ri[l], h->Ty, C, ny,
                                                                                mx, my, h->dY, h->dS);
     dR_kernel<<<my * mx, kThreads, 0, st>>>(h->Sh[l], h->dY, B, C, mx, my, g + o.Rr[l], g + o.Ri[l]);
     ydft_back_kernel<<<B * C, kThreads, 0, st>>>(h->dS, h->Ty, ny, mx, my, h->dA, h->dAb);
     FNO_CUDA(h, cudaGetLastError());
     // dv = W^T dz (pointwise path) + dA Fx^T (spectral path)
-    FNO_BLAS(h, gemm(h, true, false, C, (int)S, C, P + o.W[l], h->prmb + o.W[l], C, 0, h->dZ, h->dZb, (int)S,
-                     (long long)C * S, h->dV, (int)S, (long long)C * S, B, 0.f));
-    FNO_BLAS(h, gemm(h, false, true, R, nx, 2 * mx, h->dA, h->dAb, 2 * mx, 0, h->Fx, h->Fxb, 2 * mx, 0, h->dV, nx, 0, 1,
-                     1.f));
+    if (bf) {
+      site_major(h, h->dZb, B, C, S, h->dZT);
+      FNO_GEMM(h, tcg(h, h->dZT, C, CS, h->wTb + (size_t)l * C * C, C, 0, h->dV, 1, S, CS, (int)S, C, C, B, 1, 0.f));
+      FNO_GEMM(h, tcg(h, h->dAb, 2 * mx, 0, h->Fxb, 2 * mx, 0, h->dV, nx, 1, 0, R, nx, 2 * mx, 1, 1, 1.f));
+    } else {
+      FNO_GEMM(h, sg(h, P + o.W[l], 1, C, 0, h->dZ, S, 1, CS, h->dV, S, 1, CS, C, (int)S, C, B, 0.f));
+      FNO_GEMM(h, sg(h, h->dA, 2 * mx, 1, 0, h->Fx, 1, 2 * mx, 0, h->dV, nx, 1, 0, R, nx, 2 * mx, 1, 1.f));
+    }
   }
   // lift: dp = sum dv0, dP[o, c] = sum dv0[b, o, s] x0[b, c, s]
   chan_reduce(h, h->dV, B, C, S, g + o.p);
   outer_reduce<8, kFeatures, false>(h, h->dV, h->x0, B, C, kFeatures, S, g + o.P);
   FNO_CUDA(h, cudaGetLastError());
   if (loss) {
+    int gerr = 0;
     FNO_CUDA(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FNO_CUDA(h, cudaMemcpyAsync(&gerr, h->gerr, sizeof(int), cudaMemcpyDeviceToHost, st));
     FNO_CUDA(h, cudaStreamSynchronize(st));
+    if (gerr) return ffail(h, LB_ERR_TIMEOUT, "fno_backward: a tensor-core product's bounded wait gave up");
   }
   return LB_OK;
 }
@@ -866,6 +978,8 @@ int fno_adam(fno_handle *h, float lr, float beta1, float beta2, float eps, int32
   const float c1 = 1.0f - powf(beta1, (float)t), c2 = 1.0f - powf(beta2, (float)t);
   adam_kernel<<<blocks_for(np), kThreads, 0, h->st>>>(h->prm, h->grd, h->m1, h->m2, np, lr, beta1, beta2, eps, c1, c2,
                                                        h->prmb);
+  weights_t_kernel<<<blocks_for(np), kThreads, 0, h->st>>>(h->prmb, h->o, h->c.width, h->c.hidden, h->c.layers,
+                                                           h->wTb);
   FNO_CUDA(h, cudaGetLastError());
   return LB_OK;
 }
@@ -879,7 +993,6 @@ int fno_destroy(fno_handle *h) {
   cudaFree(h->m1);
   cudaFree(h->m2);
   cudaFree(h->prmb);
-  if (h->blas) cublasDestroy(h->blas);
   delete h;
   return LB_OK;
 }

@@ -58,6 +58,9 @@ struct lb_handle {
   int deps_gen = -1;             // plan_gen the lists were built for
   int deps_ntiles = 0;
   unsigned epoch = 0;            // value of every counter between launches
+  double *d_mon_recs = nullptr;  // per-step record slots of a monitored multi-step launch
+  unsigned *d_mon_arr = nullptr; // their arrival counters (zero between launches)
+  int mon_tiles = 0;             // tiles the slots were sized for
   bool in_batch = false;         // instance of an lb_batch
   int red_blocks = 0;
   int64_t step = 0;
@@ -367,6 +370,25 @@ cudaError_t ensure_deps(lb_handle *h) {
   return cudaSuccess;
 }
 
+constexpr int kMonSlots = 64;  // steps per multi-step launch while monitoring
+
+// Record slots of a monitored multi-step launch (one per step of a launch).
+cudaError_t ensure_mon_slots(lb_handle *h, int ntiles) {
+  if (h->d_mon_recs && h->mon_tiles >= ntiles) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return e;
+  cudaFree(h->d_mon_recs);
+  cudaFree(h->d_mon_arr);
+  h->d_mon_recs = nullptr;
+  h->d_mon_arr = nullptr;
+  h->mon_tiles = 0;
+  e = cudaMalloc((void **)&h->d_mon_recs, 4 * sizeof(double) * (size_t)ntiles * kMonSlots);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_mon_arr, kMonSlots * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->d_mon_arr, 0, kMonSlots * sizeof(unsigned));
+  if (e == cudaSuccess) h->mon_tiles = ntiles;
+  return e;
+}
+
 // nsteps >= 2 steps of a strip-sweep handle in multi-step launches.
 // Returns LB_OK, an error code, or 1 when that kernel cannot run here (the
 // caller then launches one kernel per step).
@@ -389,8 +411,17 @@ int multi_steps(lb_handle *h, int64_t nsteps) {
   }
   Q.total = h->d_out;
   Q.arrivals = h->d_arrive;
+  const bool mon = h->mon_cap > 0;
+  if (mon) {
+    LB_CUDA(h, ensure_mon_slots(h, ntiles));
+    Q.mon_recs = h->d_mon_recs;
+    Q.mon_arr = h->d_mon_arr;
+    Q.mon_ring = h->mon_ring;
+    Q.mon_cap = h->mon_cap;
+  }
   for (int64_t done = 0; done < nsteps;) {
-    const int chunk = (int)std::min<int64_t>(nsteps - done, std::max<int64_t>(2, (1LL << 30) / ntiles));
+    const int chunk = (int)std::min<int64_t>(nsteps - done, mon ? kMonSlots : std::max<int64_t>(2, (1LL << 30) / ntiles));
+    Q.mon_step0 = h->step + 1;  // step number of the first step's result
     lbk::PersistArgs P{};
     P.nitems = ntiles;
     P.nsteps = chunk;
@@ -406,7 +437,7 @@ int multi_steps(lb_handle *h, int64_t nsteps) {
     h->cur ^= chunk & 1;
     h->step += chunk;
     h->epoch += (unsigned)chunk;
-    h->cta_valid = true;
+    h->cta_valid = !mon;  // monitored launches keep their records in the slots
     h->total_valid = true;
     done += chunk;
   }
@@ -576,8 +607,8 @@ int lb_step(lb_handle *h, int64_t nsteps) {
       h->step++;
     }
   } else if (h->sweep) {
-    // Two steps or more (not monitoring): multi-step launches.
-    if (nsteps >= 2 && h->mon_cap == 0) {
+    // Two steps or more: multi-step launches.
+    if (nsteps >= 2) {
       const int rc = multi_steps(h, nsteps);
       if (rc != 1) return rc;
     }
@@ -892,6 +923,8 @@ int lb_destroy(lb_handle *h) {
   cudaFree(h->d_done);
   cudaFree(h->d_dep);
   cudaFree(h->d_ticket);
+  cudaFree(h->d_mon_recs);
+  cudaFree(h->d_mon_arr);
   delete h;
   return LB_OK;
 }

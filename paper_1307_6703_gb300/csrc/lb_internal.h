@@ -107,6 +107,16 @@ struct MultiOut {
   void *fdev[2];
   double *total;
   unsigned *arrivals;
+  // Monitoring (mon_ring non-null): every step k writes its records into
+  // slot k of mon_recs (4 doubles per tile) and counts on mon_arr[k]; the
+  // CTA that finishes step k last adds them and writes the step's record
+  // {mass, J_x, J_y, unstable, wait error, step number} at
+  // mon_ring + 6 * ((mon_step0 + k) % mon_cap).
+  double *mon_recs;
+  unsigned *mon_arr;
+  double *mon_ring;
+  int mon_cap;
+  long long mon_step0;
 };
 // One lattice, P.nsteps steps in one cooperative launch (P.kpar0 = the
 // input buffer of the first step; items are the tiles in index order).

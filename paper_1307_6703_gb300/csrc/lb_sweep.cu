@@ -979,7 +979,8 @@ sweep_batch_persist_kernel(const BatchItem *__restrict__ items, const SweepArgs 
 // Single-lattice form: item i is tile i (strip i % nstrips, segment
 // i / nstrips); arguments and maps are kernel parameters.  The last step
 // writes the per-tile records and the CTA that finishes last adds them into
-// `total` (mass, momentum, flags).
+// `total` (mass, momentum, flags); while monitoring, every step does so into
+// its own record slot and writes its record into the host ring.
 template <class St>
 __global__ void __launch_bounds__(kThreads, St::kMinBlocks)
 sweep_multi_kernel(const __grid_constant__ CUtensorMap tin0, const __grid_constant__ CUtensorMap tdev0,
@@ -1010,17 +1011,18 @@ sweep_multi_kernel(const __grid_constant__ CUtensorMap tin0, const __grid_consta
       return;
     }
     first = false;
+    const bool mon = Q.mon_ring != nullptr;
     StepIO O;
     O.fout = par ? Q.fout[1] : Q.fout[0];  // (no dynamic indexing of the parameter space)
     O.fdev = par ? Q.fdev[1] : Q.fdev[0];
-    O.recs = A.partials;
+    O.recs = mon ? Q.mon_recs + 4 * (size_t)P.nitems * k : A.partials;
     O.nrec = (unsigned)P.nitems;
-    O.arrivals = last ? Q.arrivals : nullptr;
-    O.total = Q.total;
-    O.monitor = nullptr;
-    O.mon_step = 0.0;
+    O.arrivals = mon ? Q.mon_arr + k : (last ? Q.arrivals : nullptr);
+    O.total = last ? Q.total : nullptr;
+    O.monitor = mon ? Q.mon_ring + 6 * ((Q.mon_step0 + k) % Q.mon_cap) : nullptr;
+    O.mon_step = (double)(Q.mon_step0 + k);
     if (!sweep_body<St, true>(par ? &tin1 : &tin0, par ? &tdev1 : &tdev0, A, O, i % A.nstrips, i / A.nstrips,
-                              A.partials + 4 * (size_t)i, last)) {
+                              const_cast<double *>(O.recs) + 4 * (size_t)i, last || mon)) {
       if (t == 0) Q.total[4] = 1.0;
       return;
     }

@@ -40,6 +40,10 @@ def _lib():
         lib.fno_destroy.argtypes = [P]
         lib.fno_last_error.argtypes = [P]
         lib.fno_last_error.restype = C.c_char_p
+        lib.fno_gemm_bf16.argtypes = [P, C.c_int32, C.c_int64, P, C.c_int32, C.c_int64, P, C.c_int64,
+                                      C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                      C.c_float, P, P]
+        lib.fno_gemm_bf16.restype = C.c_int
         for n in ("fno_create", "fno_set_params", "fno_get_params", "fno_get_grads", "fno_forward",
                   "fno_backward", "fno_adam", "fno_destroy"):
             getattr(lib, n).restype = C.c_int
@@ -162,3 +166,13 @@ def fno_destroy(h):
 def fno_last_error(h) -> str:
     s = _lib().fno_last_error(h)
     return s.decode() if s else ""
+
+
+def fno_gemm_bf16(X, ldx: int, sX: int, Y, ldy: int, sY: int, Cout, cm: int, cn: int, sC: int,
+                  M: int, N: int, K: int, batch: int, beta: float, err, stream=None):
+    """C[b](m, n) = sum_k X[b](m, k) Y[b](n, k) + beta C[b](m, n) on the
+    tensor cores (BF16 operands, FP32 result); device buffers."""
+    rc = _lib().fno_gemm_bf16(_ptr(X), ldx, sX, _ptr(Y), ldy, sY, _ptr(Cout), cm, cn, sC, M, N, K, batch,
+                              beta, _ptr(err), stream)
+    if rc != 0:
+        raise LBError(rc, "fno_gemm_bf16: bad arguments or CUDA error")

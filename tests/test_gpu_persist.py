@@ -201,3 +201,26 @@ def test_multistep_after_retiling_and_restore():
         assert err <= 2e-6
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("steps", [2, 63, 64, 65, 150])
+def test_monitor_across_multistep_launches(steps):
+    """While monitoring, a multi-step launch covers at most 64 steps, each
+    with its own record slot and arrival counter: every step's record lands
+    in the host ring, and the last equals lb_reduce bit for bit."""
+    import torch
+    w = C2(0.05).with_(nx=256, ny=128)
+    s = solver_for(w, LB_FP32).init_noise(2, w.rho_mean, w.noise)
+    cap = 200
+    ring = torch.full((cap, 6), -1.0, dtype=torch.float64).pin_memory()
+    s.monitor(ring)
+    s.step(steps)
+    torch.cuda.synchronize()
+    r = ring.numpy().copy()
+    got = sorted(int(v) for v in r[:, 5] if v >= 0)
+    assert got == list(range(1, steps + 1))
+    rc, vals = s.reduce()
+    assert rc == 0 and list(r[steps % cap, :3]) == vals
+    assert np.all(np.abs(r[r[:, 5] >= 0, 0] - vals[0]) <= 1e-6 * vals[0])
+    assert np.all(r[r[:, 5] >= 0, 3:5] == 0.0)
+    s.close()
