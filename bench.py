@@ -253,12 +253,16 @@ def run_ours(args):
 
     # Tiling chosen by the library's autotuner (state restored afterwards),
     # or fixed with --seg-h (no trial launches: profiler captures).
-    from paper_1307_6703_gb300 import lb_autotune, lb_set_seg_h
+    from paper_1307_6703_gb300 import lb_autotune, lb_get_tiling, lb_set_seg_h, lb_set_tiling
     if args.seg_h:
         seg_h = int(args.seg_h.split(",")[0])
-        lb_set_seg_h(s.h, seg_h)
+        if args.strips:
+            lb_set_tiling(s.h, args.strips, seg_h)
+        else:
+            lb_set_seg_h(s.h, seg_h)
     else:
         seg_h = lb_autotune(s.h, 20)
+    strips, seg_h = lb_get_tiling(s.h)
 
     # ------------------------------------------------ device-resident timing
     # The warm-up steps run inside the clock sampler's window, right before
@@ -325,7 +329,7 @@ def run_ours(args):
             "storage": args.precision,
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "walls": True,
                        "u_w": w.u_top, "A0": w.A0, "lambda": w.lam, "T_over_Tc": 0.95,
-                       "tau": w.tau, "parallelism": f"replicas{world}", "seg_h": seg_h,
+                       "tau": w.tau, "parallelism": f"replicas{world}", "seg_h": seg_h, "strips": strips,
                        "physics": PHYSICS_NOTE,
                        "l2": f"inputs larger than L2: two {b_alg / 2 * sites / 1e6:.0f} MB population buffers",
                        "unstable_after_timing": unstable},
@@ -678,6 +682,8 @@ def main():
                     help="single: the 4096x1024 lattice; batch: the seeded ensemble of "
                          "independent lattices through the batched solver")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--strips", type=int, default=0,
+                    help="with --seg-h: column strips of the sweep tiling (default: the fewest)")
     ap.add_argument("--seg-h", default="",
                     help="fixed segment height instead of the autotuner (batch: one per height class "
                          "ny <= 96, <= 160, > 160, comma-separated)")

@@ -196,10 +196,12 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step);
 
 /* Tiling autotuner (a performance control of this library; the paper has
  * no counterpart).  Times `steps` steps of the strip-sweep kernel for each
- * candidate segment height (rows per CTA, which trades CTAs per SM against
- * re-read warm-up rows), keeps the fastest for later lb_step calls and
- * writes it to *seg_h (may be NULL; 0 when the handle uses the tile kernel,
- * which has no tiling choice).  The state and the step counter are restored
+ * candidate tiling -- segment height (rows per CTA, which trades CTAs per SM
+ * against re-read warm-up rows) and strip count (the fewest strips and up
+ * to three more of at least 64 columns, which changes how the tiles fill
+ * the GPU) -- keeps the fastest for later lb_step calls and writes its
+ * segment height to *seg_h (may be NULL; 0 when the handle uses the tile
+ * kernel, which has no tiling choice; lb_get_tiling gives both).  The state and the step counter are restored
  * afterwards: the trajectory is the same as without the call.  Needs one
  * extra state buffer of device memory while it runs; synchronises the
  * stream.  Errors: LB_ERR_ARG (steps < 1), LB_ERR_STATE, LB_ERR_CUDA,
@@ -213,6 +215,21 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h);
  * (may grow the per-CTA record array).  Errors: LB_ERR_ARG (seg_h < 1),
  * LB_ERR_CUDA, LB_ERR_OOM.                                                 */
 int lb_set_seg_h(lb_handle *h, int32_t seg_h);
+
+/* The strip-sweep tiling in use: number of column strips and segment
+ * height (both 0 for a handle on the tile kernel).  A performance control
+ * of this library; the paper has no counterpart.  Errors: LB_ERR_ARG (NULL
+ * outputs).                                                                */
+int lb_get_tiling(const lb_handle *h, int32_t *nstrips, int32_t *seg_h);
+
+/* Set the tiling without tuning (e.g. one lb_get_tiling reported after
+ * lb_autotune): nstrips column strips, at least the fewest the kernel's
+ * window allows (ceil(nx / 116) for FP32, ceil(nx / 112) for 16-bit
+ * storage) and at most nx / (2 * quantum) (quantum 4 columns for FP32, 8
+ * for 16-bit storage); seg_h as lb_set_seg_h.  The trajectory does not
+ * depend on it beyond FP32 rounding order.  No-op for the tile kernel.
+ * Errors: LB_ERR_ARG (out of range), LB_ERR_CUDA, LB_ERR_OOM.             */
+int lb_set_tiling(lb_handle *h, int32_t nstrips, int32_t seg_h);
 
 /* ------------------------------------------------------------------------
  * Batched solver: many independent lattices (different sizes and physical

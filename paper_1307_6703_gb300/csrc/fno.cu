@@ -530,23 +530,37 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
   }
 }
 
-// out[b][c][r] = in[b][r][c] for batch b (R x Cc BF16 matrices), through
-// 32 x 32 shared-memory tiles so that reads and writes are both coalesced.
-__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, long long R, int Cc,
-                                      __nv_bfloat16 *__restrict__ out) {
-  __shared__ __nv_bfloat16 tile[32][33];
-  const long long r0 = (long long)blockIdx.x * 32;
-  const int c0 = blockIdx.y * 32, b = blockIdx.z;
+// out[b][c][r] = in[b][r][c] for batch b (R x Cc BF16 matrices, R and Cc
+// even), through 32 x 64 shared-memory tiles; both sides move bf16 pairs,
+// so a warp reads 128 contiguous bytes of a row of `in` and writes 128
+// contiguous bytes of `out` (two rows of 32 when R = 32).
+__global__ void __launch_bounds__(256)
+transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, long long R, long long Cc,
+                      __nv_bfloat16 *__restrict__ out) {
+  __shared__ __nv_bfloat16 tile[32][64 + 2];
+  const long long r0 = (long long)blockIdx.x * 32, c0 = (long long)blockIdx.y * 64;
+  const int b = blockIdx.z;
   in += (long long)b * R * Cc;
   out += (long long)b * R * Cc;
   for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-    const int rr = i / 32, cc = i % 32;
-    if (r0 + rr < R && c0 + cc < Cc) tile[rr][cc] = in[(r0 + rr) * Cc + c0 + cc];
+    const int rr = i / 32, cp = i % 32;
+    const long long r = r0 + rr, c = c0 + 2 * cp;
+    if (r < R && c < Cc) {
+      const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(in + r * Cc + c);
+      tile[rr][2 * cp] = v.x;
+      tile[rr][2 * cp + 1] = v.y;
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-    const int cc = i / 32, rr = i % 32;
-    if (r0 + rr < R && c0 + cc < Cc) out[(long long)(c0 + cc) * R + r0 + rr] = tile[rr][cc];
+  for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) {
+    const int cc = i / 16, rp = i % 16;
+    const long long c = c0 + cc, r = r0 + 2 * rp;
+    if (c < Cc && r < R) {
+      __nv_bfloat162 v;
+      v.x = tile[2 * rp][cc];
+      v.y = tile[2 * rp + 1][cc];
+      *reinterpret_cast<__nv_bfloat162 *>(out + c * R + r) = v;
+    }
   }
 }
 
@@ -649,8 +663,8 @@ cudaError_t sg(fno_handle *h, const float *A, long long am, long long ak, long l
 
 // Site-major copy of a [B][rows][S] BF16 activation: out[b][s][row].
 void site_major(fno_handle *h, const __nv_bfloat16 *in, int B, int rows, long long S, __nv_bfloat16 *out) {
-  const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((S + 31) / 32), (unsigned)B);
-  transpose_bf16_kernel<<<grid, 256, 0, h->st>>>(in, rows, (int)S, out);
+  const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((S + 63) / 64), (unsigned)B);
+  transpose_bf16_kernel<<<grid, 256, 0, h->st>>>(in, rows, S, out);
 }
 
 // out[ch] = sum over (b, s) of a[b, ch, s] for the C channels of a.

@@ -11,7 +11,7 @@
 // K range, 64 columns of K per pipeline stage: one TMA box of 128 x 64 of X
 // and one of BN x 64 of Y per stage, both 128-byte swizzled (a row of 64
 // BF16 is one 128-byte swizzle row, eight rows one 1024-byte swizzle atom),
-// four stages in flight.  Thread 0 requests the boxes and issues the four
+// four stages in flight (one when the K range fits a single stage).  Thread 0 requests the boxes and issues the four
 // K = 16 MMAs of a stage; their completion (tcgen05.commit) frees the stage.
 // The four warps then read the accumulator rows 32w .. 32w + 31 of tensor
 // memory and store them.  Rows, columns and K beyond the operands are
@@ -38,7 +38,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kStages = 4;
 constexpr int kThreads = 128;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
@@ -77,12 +76,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
-template <int BN>
+// Stages: 1 when the K range fits one stage (no pipeline to keep full, and
+// a small footprint lets more CTAs share an SM), else 4.
+template <int BN, int kStages>
 struct __align__(1024) Smem {
   __nv_bfloat16 a[kStages][kBM * kBK];  // 16 KB per stage
   __nv_bfloat16 b[kStages][BN * kBK];   // BN * 128 bytes per stage
   unsigned long long full[kStages], empty[kStages], done;
   uint32_t tmem;
+  static_assert(sizeof(a) + sizeof(b) >= 4 * 32 * 33 * sizeof(float), "the epilogue's staging tiles reuse stage memory");
 };
 
 __device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint32_t dst, uint32_t bar, int x, int y, int z) {
@@ -93,13 +95,14 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap *map, uint32_t dst
       : "memory");
 }
 
-template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BN, int kStages>
+__global__ void __launch_bounds__(kThreads)
 gemm_tn_bf16_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap my,
                     const GemmParams p) {
   extern __shared__ unsigned char raw[];
   // the swizzled tiles need 1024-byte alignment
-  Smem<BN> &S = *reinterpret_cast<Smem<BN> *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  using Sm = Smem<BN, kStages>;
+  Sm &S = *reinterpret_cast<Sm *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int mt = blockIdx.x, nt = blockIdx.y, bz = blockIdx.z;
   const int b = bz / p.ksplit, ks = bz - b * p.ksplit;
@@ -189,9 +192,16 @@ gemm_tn_bf16_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constan
   if (!done_ok && lane == 0) atomicOr(p.err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  // Epilogue: warp w holds accumulator rows 32w .. 32w + 31 (one per lane).
+  // Epilogue: warp w holds accumulator rows 32w .. 32w + 31 (one per lane),
+  // read 32 columns at a time.  Where n is the output's contiguous index
+  // (cn == 1) each 32 x 32 block goes through a per-warp shared tile so that
+  // a store instruction writes 32 consecutive n of one row; otherwise lanes
+  // (consecutive m) already write consecutive addresses.
   const int m = mt * kBM + warp * 32 + lane;
   float *crow = p.c + (long long)bz * p.sC + (long long)m * p.cm;
+  const bool row_major = p.cn == 1;
+  float *tile = reinterpret_cast<float *>(&S.a[0][0]) + warp * 32 * 33;  // stages are no longer read
+  const bool valid = ok && done_ok;
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
     uint32_t r[32];
@@ -206,14 +216,39 @@ gemm_tn_bf16_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constan
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (m < p.M && ok && done_ok) {
+    if (!valid) continue;
+    const int nb = nt * BN + c0;
+    if (row_major) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = nk > 0 ? __uint_as_float(r[j]) : 0.f;
+      __syncwarp();
+      const int n = nb + lane;
+      float *base = p.c + (long long)bz * p.sC + (long long)(mt * kBM + warp * 32) * p.cm + n;
+      const int rows = min(32, p.M - (mt * kBM + warp * 32));
+      if (p.beta != 0.f) {  // all old values first: the loads must not wait for the stores
+        float old[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) old[i] = (i < rows && n < p.N) ? base[(long long)i * p.cm] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < rows && n < p.N) base[(long long)i * p.cm] = fmaf(p.beta, old[i], tile[i * 33 + lane]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < rows && n < p.N) base[(long long)i * p.cm] = tile[i * 33 + lane];
+      }
+      __syncwarp();
+    } else if (m < p.M) {
+      float old[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        old[j] = (p.beta != 0.f && nb + j < p.N) ? crow[(long long)(nb + j) * p.cn] : 0.f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const int n = nt * BN + c0 + j;
+        const int n = nb + j;
         if (n < p.N) {
-          float *dst = crow + (long long)n * p.cn;
           const float v = nk > 0 ? __uint_as_float(r[j]) : 0.f;  // an empty K range adds nothing
-          *dst = p.beta != 0.f ? fmaf(p.beta, *dst, v) : v;
+          crow[(long long)n * p.cn] = p.beta != 0.f ? fmaf(p.beta, old[j], v) : v;
         }
       }
     }
@@ -306,13 +341,13 @@ cudaError_t operand_map(const __nv_bfloat16 *base, int K, int rows, int ld, long
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN>
+template <int BN, int kStages>
 cudaError_t launch_tn(const CUtensorMap &mx, const CUtensorMap &my, const GemmParams &p, int nb, cudaStream_t st) {
-  const size_t smem = sizeof(Smem<BN>) + 1024;
+  const size_t smem = sizeof(Smem<BN, kStages>) + 1024;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tn_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(gemm_tn_bf16_kernel<BN, kStages>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -321,7 +356,13 @@ cudaError_t launch_tn(const CUtensorMap &mx, const CUtensorMap &my, const GemmPa
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  return cudaLaunchKernelEx(&cfg, gemm_tn_bf16_kernel<BN>, mx, my, p);
+  return cudaLaunchKernelEx(&cfg, gemm_tn_bf16_kernel<BN, kStages>, mx, my, p);
+}
+
+template <int BN>
+cudaError_t launch_tn_stages(const CUtensorMap &mx, const CUtensorMap &my, const GemmParams &p, int nb,
+                             cudaStream_t st) {
+  return p.kper <= kBK ? launch_tn<BN, 1>(mx, my, p, nb, st) : launch_tn<BN, 4>(mx, my, p, nb, st);
 }
 
 }  // namespace
@@ -352,10 +393,10 @@ cudaError_t gemm_tn_bf16(const __nv_bfloat16 *X, int ldx, long long sX, const __
   p.beta = beta;
   p.err = err;
   switch (BN) {
-    case 32: return launch_tn<32>(mx, my, p, batch, st);
-    case 64: return launch_tn<64>(mx, my, p, batch, st);
-    case 128: return launch_tn<128>(mx, my, p, batch, st);
-    default: return launch_tn<256>(mx, my, p, batch, st);
+    case 32: return launch_tn_stages<32>(mx, my, p, batch, st);
+    case 64: return launch_tn_stages<64>(mx, my, p, batch, st);
+    case 128: return launch_tn_stages<128>(mx, my, p, batch, st);
+    default: return launch_tn_stages<256>(mx, my, p, batch, st);
   }
 }
 

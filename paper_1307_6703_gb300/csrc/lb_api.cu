@@ -837,8 +837,24 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   const int ny = h->p.ny;
   int max_nseg = h->sweep_nseg;
   for (int c : cand) max_nseg = std::max(max_nseg, (ny + std::min(c, ny) - 1) / std::min(c, ny));
-  // Per-CTA records sized for the smallest segments (kept afterwards).
-  LB_CUDA(h, ensure_records(h, max_nseg));
+  // Strip counts: the fewest strips, and up to three more while the strips
+  // stay at least 64 columns wide.  More, narrower strips cost more halo
+  // columns but change how the tiles of the last step fill the GPU (the
+  // tail of a multi-step launch); the timing decides.
+  const int s_min = lbk::sweep_min_strips(h->store, h->p.nx);
+  std::vector<int> strips{s_min};
+  for (int sc = s_min + 1; sc <= s_min + 3; ++sc) {
+    int bw = 0, ex = 0;
+    lbk::sweep_strips(h->store, h->p.nx, sc, &bw, &ex);
+    if (bw >= 64) strips.push_back(sc);
+  }
+  const int strips0 = h->sweep_nstrips, base0 = h->sweep_base, extra0 = h->sweep_extra;
+  // Per-CTA records sized for the most strips and the smallest segments
+  // (kept afterwards).
+  h->sweep_nstrips = strips.back();
+  cudaError_t er = ensure_records(h, max_nseg);
+  h->sweep_nstrips = strips0;
+  LB_CUDA(h, er);
   h->cta_valid = false;
   h->total_valid = false;
 
@@ -848,12 +864,15 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   const int seg0 = h->sweep_seg;
   void *save = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int best = seg0, rc = LB_OK;
+  int best = seg0, best_strips = strips0, rc = LB_OK;
   float best_ms = 3.0e38f;
   cudaError_t e = cudaMalloc(&save, buf_bytes);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(save, h->f[cur0], buf_bytes, cudaMemcpyDeviceToDevice, h->st);
+  for (int sc : strips) {
+  h->sweep_nstrips = sc;
+  lbk::sweep_strips(h->store, h->p.nx, sc, &h->sweep_base, &h->sweep_extra);
   int last = -1;
   for (int c : cand) {
     if (e != cudaSuccess || rc != LB_OK) break;
@@ -871,14 +890,24 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
     if (rc == LB_OK && e == cudaSuccess && ms < best_ms) {
       best_ms = ms;
       best = sh;
+      best_strips = sc;
     }
     // back to the saved state for the next candidate
     h->cur = cur0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->f[cur0], save, buf_bytes, cudaMemcpyDeviceToDevice, h->st);
   }
+  }
   h->cur = cur0;
   h->step = step0;
-  set_segments(h, (rc == LB_OK && e == cudaSuccess) ? best : seg0);
+  const bool tuned = rc == LB_OK && e == cudaSuccess;
+  h->sweep_nstrips = tuned ? best_strips : strips0;
+  if (tuned)
+    lbk::sweep_strips(h->store, h->p.nx, h->sweep_nstrips, &h->sweep_base, &h->sweep_extra);
+  else {
+    h->sweep_base = base0;
+    h->sweep_extra = extra0;
+  }
+  set_segments(h, tuned ? best : seg0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   cudaFree(save);
   if (e0) cudaEventDestroy(e0);
@@ -886,6 +915,33 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "lb_autotune");
   if (rc != LB_OK) return rc;
   if (seg_h) *seg_h = h->sweep_seg;
+  return LB_OK;
+}
+
+int lb_get_tiling(const lb_handle *h, int32_t *nstrips, int32_t *seg_h) {
+  if (!h || !nstrips || !seg_h) return LB_ERR_ARG;
+  *nstrips = h->sweep ? h->sweep_nstrips : 0;
+  *seg_h = h->sweep ? h->sweep_seg : 0;
+  return LB_OK;
+}
+
+int lb_set_tiling(lb_handle *h, int32_t nstrips, int32_t seg_h) {
+  if (!h) return LB_ERR_ARG;
+  if (!h->sweep) return LB_OK;
+  const int s_min = lbk::sweep_min_strips(h->store, h->p.nx);
+  const int qn = h->store == lbk::kStoreF32 ? 4 : 8;
+  if (nstrips < s_min || nstrips > h->p.nx / (2 * qn) || seg_h < 1)
+    return fail(h, LB_ERR_ARG, "lb_set_tiling: strip count or segment height out of range");
+  const int sh = std::min((int)seg_h, h->p.ny);
+  const int old = h->sweep_nstrips;
+  h->sweep_nstrips = nstrips;
+  const cudaError_t e = ensure_records(h, (h->p.ny + sh - 1) / sh);
+  if (e != cudaSuccess) {
+    h->sweep_nstrips = old;
+    return cuda_fail(h, e, "lb_set_tiling");
+  }
+  lbk::sweep_strips(h->store, h->p.nx, nstrips, &h->sweep_base, &h->sweep_extra);
+  set_segments(h, sh);
   return LB_OK;
 }
 

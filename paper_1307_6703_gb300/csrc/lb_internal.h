@@ -56,6 +56,10 @@ cudaError_t sweep_prepare(int store, size_t *smem_bytes);
 // quantum is 4 columns for FP32 storage and 8 for 16-bit storage) and row
 // segments of the sweep kernel for an nx x ny lattice.
 void sweep_plan(int store, int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg);
+// Widths of nstrips strips (>= sweep_min_strips) over nx columns: base_w or
+// base_w + quantum, the first `extra` wider.
+void sweep_strips(int store, int nx, int nstrips, int *base_w, int *extra);
+int sweep_min_strips(int store, int nx);
 // TMA descriptors of one padded state buffer with the boxes the kernel's
 // ring expects (built next to the kernel so the two cannot differ).  FP32:
 // one map of the nine planes (m1 is a copy).  16-bit storage: m0 maps the

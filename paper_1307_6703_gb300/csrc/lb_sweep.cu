@@ -230,32 +230,100 @@ __device__ __forceinline__ float rcp(float v) {
 }
 __device__ __forceinline__ int inc(int s, int n) { return s == n - 1 ? 0 : s + 1; }
 
+// Arithmetic on one site (V = float) or on the two rows a thread computes
+// in a stage at once (V = float2: row j = 0 in .x, j = 1 in .y, executed as
+// the packed FP32 pair instructions of sm_100 and later).  Each operation is
+// rounded once, as written, so both forms give the same bits for the same
+// site and the result of a site does not depend on which form (and so which
+// tiling) computed it -- with one rule for the callers: no product feeds an
+// addition or subtraction.  The code generator fuses a pair multiply into
+// the pair add that consumes it (one rounding instead of two; measured on
+// GB300, and unlike the scalar forms, which stay as written), so every such
+// combination is written as an explicit fma in both forms.
+template <class V>
+struct Op;
+template <>
+struct Op<float> {
+  __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  __device__ static float neg(float a) { return -a; }
+  __device__ static float k(float a) { return a; }
+  __device__ static float inv(float v) { return rcp(v); }
+};
+template <>
+struct Op<float2> {
+  __device__ static float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  __device__ static float2 sub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+    return *reinterpret_cast<float2 *>(&d);
+  }
+  __device__ static float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  __device__ static float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+  __device__ static float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+  __device__ static float2 k(float a) { return make_float2(a, a); }
+  __device__ static float2 inv(float2 v) { return make_float2(rcp(v.x), rcp(v.y)); }
+};
+
+// Density and raw momentum sum_i f_i c_i of the pulled populations (16-bit
+// storage: deviations, n gets the references' sum r_sum):
+// E = f1 + f5 + f8 and W = f3 + f6 + f7 serve n and the x momentum.
+template <class V>
+__device__ __forceinline__ void site_sums(const V *f, float r_sum, bool dev, V &n, V &sx, V &sy) {
+  using O = Op<V>;
+  const V E = O::add(O::add(f[1], f[5]), f[8]), W = O::add(O::add(f[3], f[6]), f[7]);
+  sx = O::sub(E, W);
+  n = O::add(O::add(f[0], O::add(f[2], f[4])), O::add(E, W));
+  if (dev) n = O::add(n, O::k(r_sum));
+  sy = O::sub(O::add(O::add(f[2], f[5]), f[6]), O::add(O::add(f[4], f[7]), f[8]));
+}
+
+// P = p^i - p^w = nT - nT/(1 - bn) + a n^2 (Eq. eqstate).
+template <class V>
+__device__ __forceinline__ V pressure_diff(V c, float T, float a, float b) {
+  using O = Op<V>;
+  const V nT = O::mul(c, O::k(T));
+  const V r = O::inv(O::fma(c, O::k(-b), O::k(1.0f)));
+  return O::fma(O::mul(c, O::k(a)), c, O::fma(O::neg(nT), r, nT));  // nT - nT r in one rounding
+}
+
 // x-derivative, y-derivative and Laplacian stencils of Eqs. (xstencil,
-// laplstencil) at column t of row r1, rows r0 = y-1 and r2 = y+1.
+// laplstencil) at column t of row r1, rows r0 = y-1 and r2 = y+1.  Every
+// operation is rounded as written (explicit intrinsics, no contraction), so
+// a site's value does not depend on the code path that computed it.
 struct Sten {
   float N, M, Q, R, four_QR;
 };
+// N d1 + M (d2 + d0) for the differences d of the three rows
+__device__ __forceinline__ float dstencil(const Sten &s, float d1, float d2, float d0) {
+  return __fmaf_rn(s.N, d1, __fmul_rn(s.M, __fadd_rn(d2, d0)));
+}
 __device__ __forceinline__ float sdx(const Sten &s, const float *r0, const float *r1, const float *r2, int t) {
-  return s.N * (r1[t + 1] - r1[t - 1]) + s.M * ((r2[t + 1] - r2[t - 1]) + (r0[t + 1] - r0[t - 1]));
+  return dstencil(s, __fsub_rn(r1[t + 1], r1[t - 1]), __fsub_rn(r2[t + 1], r2[t - 1]), __fsub_rn(r0[t + 1], r0[t - 1]));
 }
 __device__ __forceinline__ float sdy(const Sten &s, const float *r0, const float *r2, int t) {
-  return s.N * (r2[t] - r0[t]) + s.M * ((r2[t + 1] - r0[t + 1]) + (r2[t - 1] - r0[t - 1]));
+  return dstencil(s, __fsub_rn(r2[t], r0[t]), __fsub_rn(r2[t + 1], r0[t + 1]), __fsub_rn(r2[t - 1], r0[t - 1]));
 }
 __device__ __forceinline__ float slap(const Sten &s, const float *r0, const float *r1, const float *r2, int t) {
-  return s.Q * ((r1[t + 1] + r1[t - 1]) + (r2[t] + r0[t])) +
-         s.R * ((r2[t + 1] + r2[t - 1]) + (r0[t + 1] + r0[t - 1])) - s.four_QR * r1[t];
+  const float s1 = __fadd_rn(__fadd_rn(r1[t + 1], r1[t - 1]), __fadd_rn(r2[t], r0[t]));
+  const float s2 = __fadd_rn(__fadd_rn(r2[t + 1], r2[t - 1]), __fadd_rn(r0[t + 1], r0[t - 1]));
+  return __fmaf_rn(s.Q, s1, __fmaf_rn(s.R, s2, __fmul_rn(-s.four_QR, r1[t])));
 }
 
 // x- and y-derivative stencils applied to both components of float2 rows.
 __device__ __forceinline__ float2 sdx2(const Sten &s, const float2 *r0, const float2 *r1, const float2 *r2, int t) {
   const float2 a = r1[t + 1], b = r1[t - 1], c = r2[t + 1], d = r2[t - 1], e = r0[t + 1], f = r0[t - 1];
-  return make_float2(s.N * (a.x - b.x) + s.M * ((c.x - d.x) + (e.x - f.x)),
-                     s.N * (a.y - b.y) + s.M * ((c.y - d.y) + (e.y - f.y)));
+  return make_float2(dstencil(s, __fsub_rn(a.x, b.x), __fsub_rn(c.x, d.x), __fsub_rn(e.x, f.x)),
+                     dstencil(s, __fsub_rn(a.y, b.y), __fsub_rn(c.y, d.y), __fsub_rn(e.y, f.y)));
 }
 __device__ __forceinline__ float2 sdy2(const Sten &s, const float2 *r0, const float2 *r2, int t) {
   const float2 g = r2[t], h = r0[t], c = r2[t + 1], e = r0[t + 1], d = r2[t - 1], f = r0[t - 1];
-  return make_float2(s.N * (g.x - h.x) + s.M * ((c.x - e.x) + (d.x - f.x)),
-                     s.N * (g.y - h.y) + s.M * ((c.y - e.y) + (d.y - f.y)));
+  return make_float2(dstencil(s, __fsub_rn(g.x, h.x), __fsub_rn(c.x, e.x), __fsub_rn(d.x, f.x)),
+                     dstencil(s, __fsub_rn(g.y, h.y), __fsub_rn(c.y, e.y), __fsub_rn(d.y, f.y)));
 }
 
 // Propagated populations of the site in column t of row r1 (pull).  With
@@ -286,47 +354,59 @@ __device__ __forceinline__ void add_refs(float *f, float r_ax, float r_dg) {
 // axes (w = 1/9) h_x = e_a + S_x / 2, t_x = T_x / 3; on the diagonals
 // (w = 1/36) S_(+-) = S_x + S_y +- 2 X with X = on u_x u_y + C_xy and
 // T_(+-) = T_y +- T_x, so h_(+-) = e_d + (S_x + S_y) / 8 +- X / 4 and
-// t_(+-) = (t_y +- t_x) / 4.  kDev: f holds the deviations d_i = f_i - r_i
+// t_(+-) = T_(+-) / 12.  kDev: f holds the deviations d_i = f_i - r_i
 // and fs receives d*_i = f*_i - r_i = (1 - omega) d_i + w_i E_i - omega r_i;
 // wr_ax and wr_dg are omega r_i on the axes and diagonals and join e_a, e_d.
-template <bool kDev>
-__device__ __forceinline__ void collide(const SweepArgs &A, const float *f, float n, float Jx, float Jy,
-                                        float Fx, float Fy, float dnx, float dny, float divJ, float *fs,
-                                        float wr_ax = 0.f, float wr_dg = 0.f) {
-  const float rn = rcp(n);
-  const float ux = Jx * rn, uy = Jy * rn;
-  const float on = A.omega * n;
-  const float onux = on * ux, onuy = on * uy;
-  const float ux2 = ux + ux, uy2 = uy + uy;
+template <bool kDev, class V>
+__device__ __forceinline__ void collide(const SweepArgs &A, const V *f, V n, V Jx, V Jy, V Fx, V Fy, V dnx, V dny,
+                                        V divJ, V *fs, float wr_ax = 0.f, float wr_dg = 0.f) {
+  using O = Op<V>;
+  const V rn = O::inv(n);
+  const V ux = O::mul(Jx, rn), uy = O::mul(Jy, rn);
+  const V on = O::mul(O::k(A.omega), n);
+  const V onux = O::mul(on, ux), onuy = O::mul(on, uy);
+  const V ux2 = O::mul(O::k(2.f), ux), uy2 = O::mul(O::k(2.f), uy);
   // C / g (Eq. coeff)
-  const float cxx = fmaf(A.th, fmaf(ux2, dnx, divJ), ux2 * Fx);
-  const float cyy = fmaf(A.th, fmaf(uy2, dny, divJ), uy2 * Fy);
-  const float cxy = fmaf(A.th, fmaf(ux, dny, uy * dnx), fmaf(ux, Fy, Fx * uy));
-  const float Sx = fmaf(onux, ux, A.g * cxx), Sy = fmaf(onuy, uy, A.g * cyy);
-  const float X = fmaf(onux, uy, A.g * cxy);
-  const float Sxy = Sx + Sy;  // on u^2 + tr C
-  float ea, ed;
+  const V th = O::k(A.th), g = O::k(A.g);
+  const V cxx = O::fma(th, O::fma(ux2, dnx, divJ), O::mul(ux2, Fx));
+  const V cyy = O::fma(th, O::fma(uy2, dny, divJ), O::mul(uy2, Fy));
+  const V cxy = O::fma(th, O::fma(ux, dny, O::mul(uy, dnx)), O::fma(ux, Fy, O::mul(Fx, uy)));
+  const V Sx = O::fma(onux, ux, O::mul(g, cxx)), Sy = O::fma(onuy, uy, O::mul(g, cyy));
+  const V X = O::fma(onux, uy, O::mul(g, cxy));
+  const V Sxy = O::add(Sx, Sy);  // on u^2 + tr C
+  V ea, ed;
   if constexpr (kDev) {
-    ea = fmaf(on, A.A_ax * (1.f / 9.f), fmaf(-1.f / 6.f, Sxy, -wr_ax));
-    ed = fmaf(on, A.A_diag * (1.f / 36.f), fmaf(-1.f / 24.f, Sxy, -wr_dg));
+    ea = O::fma(on, O::k(A.A_ax * (1.f / 9.f)), O::fma(O::k(-1.f / 6.f), Sxy, O::k(-wr_ax)));
+    ed = O::fma(on, O::k(A.A_diag * (1.f / 36.f)), O::fma(O::k(-1.f / 24.f), Sxy, O::k(-wr_dg)));
   } else {
-    ea = fmaf(on, A.A_ax * (1.f / 9.f), Sxy * (-1.f / 6.f));
-    ed = fmaf(on, A.A_diag * (1.f / 36.f), Sxy * (-1.f / 24.f));
+    ea = O::fma(on, O::k(A.A_ax * (1.f / 9.f)), O::mul(Sxy, O::k(-1.f / 6.f)));
+    ed = O::fma(on, O::k(A.A_diag * (1.f / 36.f)), O::mul(Sxy, O::k(-1.f / 24.f)));
   }
-  const float hx = fmaf(0.5f, Sx, ea), hy = fmaf(0.5f, Sy, ea);
-  const float h5 = fmaf(0.125f, Sxy, fmaf(0.25f, X, ed)), h6 = fmaf(0.125f, Sxy, fmaf(-0.25f, X, ed));
-  const float tx = fmaf(A.g, Fx, onux) * (1.f / 3.f);
-  const float ty = fmaf(A.g, Fy, onuy) * (1.f / 3.f);
-  const float t5 = 0.25f * (tx + ty), t6 = 0.25f * (ty - tx);
-  const float om1 = A.one_minus_omega;
-  fs[1] = fmaf(om1, f[1], hx + tx);
-  fs[3] = fmaf(om1, f[3], hx - tx);
-  fs[2] = fmaf(om1, f[2], hy + ty);
-  fs[4] = fmaf(om1, f[4], hy - ty);
-  fs[5] = fmaf(om1, f[5], h5 + t5);
-  fs[7] = fmaf(om1, f[7], h5 - t5);
-  fs[6] = fmaf(om1, f[6], h6 + t6);
-  fs[8] = fmaf(om1, f[8], h6 - t6);
+  const V hx = O::fma(O::k(0.5f), Sx, ea), hy = O::fma(O::k(0.5f), Sy, ea);
+  const V h5 = O::fma(O::k(0.125f), Sxy, O::fma(O::k(0.25f), X, ed));
+  const V h6 = O::fma(O::k(0.125f), Sxy, O::fma(O::k(-0.25f), X, ed));
+  // odd parts: t_x = T_x / 3, t_(+-) = (T_y +- T_x) / 12
+  const V Tx = O::fma(g, Fx, onux), Ty = O::fma(g, Fy, onuy);
+  const V Tp = O::add(Ty, Tx), Tm = O::sub(Ty, Tx);
+  const V third = O::k(1.f / 3.f), mthird = O::k(-1.f / 3.f), twelfth = O::k(1.f / 12.f), mtwelfth = O::k(-1.f / 12.f);
+  const V om1 = O::k(A.one_minus_omega);
+  fs[1] = O::fma(om1, f[1], O::fma(Tx, third, hx));
+  fs[3] = O::fma(om1, f[3], O::fma(Tx, mthird, hx));
+  fs[2] = O::fma(om1, f[2], O::fma(Ty, third, hy));
+  fs[4] = O::fma(om1, f[4], O::fma(Ty, mthird, hy));
+  fs[5] = O::fma(om1, f[5], O::fma(Tp, twelfth, h5));
+  fs[7] = O::fma(om1, f[7], O::fma(Tp, mtwelfth, h5));
+  fs[6] = O::fma(om1, f[6], O::fma(Tm, twelfth, h6));
+  fs[8] = O::fma(om1, f[8], O::fma(Tm, mtwelfth, h6));
+}
+
+// The rest population as the remainder: n - sum_{i>=1} f*_i (16-bit
+// storage: (n - sum r_i) - sum d*_i), which keeps the site's mass exact.
+template <class V>
+__device__ __forceinline__ V rest_remainder(V n, const V *fs) {
+  using O = Op<V>;
+  return O::sub(n, O::add(O::add(O::add(fs[1], fs[3]), O::add(fs[2], fs[4])),
+                          O::add(O::add(fs[5], fs[7]), O::add(fs[6], fs[8]))));
 }
 
 }  // namespace
@@ -448,6 +528,8 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
     const int a = ya - 3 + 2 * k;
 
     // ---------------------------------------- A: rows a, a+1 -- n, raw momentum
+    // (Steady iterations compute both rows of each stage at once wherever
+    // the arithmetic needs no neighbour data: row j in lane j of a float2.)
     {
       const Row q0 = St::row(S.pops[s5], 0), q1 = St::row(S.pops[s5], 1);      // rows a-1, a
       const Row q2 = St::row(S.pops[s5p1], 0), q3 = St::row(S.pops[s5p1], 1);  // rows a+1, a+2
@@ -457,32 +539,42 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
       // two rows' independent arithmetic can interleave.
       float nv[2] = {0.f, 0.f};
       bool nw[2] = {false, false};
+      if constexpr (kSteady) {
+        float fa[9], fb[9];
+        pull<St>(q0, q1, q2, tc, fa, A);
+        pull<St>(q1, q2, q3, tc, fb, A);
+        float2 f2[9], n2, sx2, sy2;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int y = a + j;
-        const Row r0 = j ? q1 : q0, r1 = j ? q2 : q1, r2 = j ? q3 : q2;
-        if (kSteady || (actA && (!walls || (y >= 0 && y <= ny - 1)))) {
-          float f[9];
-          pull<St>(r0, r1, r2, tc, f, A);
-          float n;
-          if constexpr (St::kDev) {
-            if (!kSteady && walls && (y == 0 || y == ny - 1)) add_refs(f, A.ref_ax, A.ref_dg);
+        for (int q = 0; q < 9; ++q) f2[q] = make_float2(fa[q], fb[q]);
+        site_sums<float2>(f2, r_sum, St::kDev, n2, sx2, sy2);
+        nv[0] = n2.x; nv[1] = n2.y;
+        sx_new[0] = sx2.x; sx_new[1] = sx2.y;  // the reference populations cancel in the momentum
+        sy_new[0] = sy2.x; sy_new[1] = sy2.y;
+        nw[0] = nw[1] = true;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int y = a + j;
+          const Row r0 = j ? q1 : q0, r1 = j ? q2 : q1, r2 = j ? q3 : q2;
+          if (actA && (!walls || (y >= 0 && y <= ny - 1))) {
+            float f[9];
+            pull<St>(r0, r1, r2, tc, f, A);
+            float n;
+            if constexpr (St::kDev) {
+              if (walls && (y == 0 || y == ny - 1)) add_refs(f, A.ref_ax, A.ref_dg);
+            }
+            if (walls && y == 0) {
+              n = St::get(r1, 0, t, A) + St::get(r1, 4, t, A) + St::get(r1, 7, t, A) + St::get(r1, 8, t, A) +
+                  f[1] + f[3] + f[4] + f[7] + f[8];
+            } else if (walls && y == ny - 1) {
+              n = St::get(r1, 0, t, A) + St::get(r1, 2, t, A) + St::get(r1, 6, t, A) + St::get(r1, 5, t, A) +
+                  f[1] + f[3] + f[2] + f[6] + f[5];
+            } else {
+              site_sums<float>(f, r_sum, St::kDev, n, sx_new[j], sy_new[j]);
+            }
+            nv[j] = n;
+            nw[j] = true;
           }
-          if (!kSteady && walls && y == 0) {
-            n = St::get(r1, 0, t, A) + St::get(r1, 4, t, A) + St::get(r1, 7, t, A) + St::get(r1, 8, t, A) + f[1] +
-                f[3] + f[4] + f[7] + f[8];
-          } else if (!kSteady && walls && y == ny - 1) {
-            n = St::get(r1, 0, t, A) + St::get(r1, 2, t, A) + St::get(r1, 6, t, A) + St::get(r1, 5, t, A) + f[1] +
-                f[3] + f[2] + f[6] + f[5];
-          } else {
-            n = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
-            if constexpr (St::kDev) n += r_sum;
-            // the reference populations cancel in the momentum
-            sx_new[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
-            sy_new[j] = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
-          }
-          nv[j] = n;
-          nw[j] = true;
         }
       }
 #pragma unroll
@@ -499,18 +591,22 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
         const float *n2 = S.n[s3][0], *n3 = S.n[s3][1];      // rows a, a+1
         float2 plv[2];
         bool plw[2] = {false, false};
+        if constexpr (kSteady) {
+          const float2 P2 = pressure_diff<float2>(make_float2(n1[tc], n2[tc]), A.T, A.a, A.b);
+          plv[0] = make_float2(P2.x, slap(st, n0, n1, n2, tc));
+          plv[1] = make_float2(P2.y, slap(st, n1, n2, n3, tc));
+          plw[0] = plw[1] = true;
+        } else {
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int y = a - 1 + j;
-          const float *r0 = j ? n1 : n0, *r1 = j ? n2 : n1, *r2 = j ? n3 : n2;
-          if (kSteady || (actB && y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1)))) {
-            if (!kSteady && walls && y == 0) r0 = r2;
-            if (!kSteady && walls && y == ny - 1) r2 = r0;
-            const float c = r1[tc];
-            const float nT = c * A.T;
-            const float pw = nT * rcp(1.0f - A.b * c) - A.a * c * c;
-            plv[j] = make_float2(nT - pw, slap(st, r0, r1, r2, tc));
-            plw[j] = true;
+          for (int j = 0; j < 2; ++j) {
+            const int y = a - 1 + j;
+            const float *r0 = j ? n1 : n0, *r1 = j ? n2 : n1, *r2 = j ? n3 : n2;
+            if (actB && y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1))) {
+              if (walls && y == 0) r0 = r2;
+              if (walls && y == ny - 1) r2 = r0;
+              plv[j] = make_float2(pressure_diff<float>(r1[tc], A.T, A.a, A.b), slap(st, r0, r1, r2, tc));
+              plw[j] = true;
+            }
           }
         }
 #pragma unroll
@@ -525,6 +621,7 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
         const float2 *P0 = S.PL[s2m1][0], *P1 = S.PL[s2m1][1], *P2 = S.PL[s2][0], *P3 = S.PL[s2][1];
         float2 jv[2];
         bool jw[2] = {false, false};
+        float sxv[2] = {sxa[0], sxa[1]}, syv[2] = {sya[0], sya[1]};
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 2 + j;
@@ -533,16 +630,16 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
           if (!kSteady && walls && y == 0) p0 = p2;
           if (!kSteady && walls && y == ny - 1) p2 = p0;
           const float n = S.n[s3m1][j][tc];
-          const float kn = A.kappa * n;
+          const float kn = __fmul_rn(A.kappa, n);
           // D P + kappa n D L = D G with G = P + kappa n L at the neighbours
           // (n is the site's own density, a constant of the stencil)
-          auto G = [kn](const float2 v) { return fmaf(kn, v.y, v.x); };
+          auto G = [kn](const float2 v) { return __fmaf_rn(kn, v.y, v.x); };
           const float g0m = G(p0[tc - 1]), g0c = G(p0[tc]), g0p = G(p0[tc + 1]);
           const float g1m = G(p1[tc - 1]), g1p = G(p1[tc + 1]);
           const float g2m = G(p2[tc - 1]), g2c = G(p2[tc]), g2p = G(p2[tc + 1]);
-          const float Fx = (st.N * (g1p - g1m) + st.M * ((g2p - g2m) + (g0p - g0m))) + A.A0 * sinx;
-          const float Fy = st.N * (g2c - g0c) + st.M * ((g2p - g0p) + (g2m - g0m));
-          float sx = sxa[j], sy = sya[j];
+          const float Fx = __fmaf_rn(A.A0, sinx, dstencil(st, __fsub_rn(g1p, g1m), __fsub_rn(g2p, g2m),
+                                                          __fsub_rn(g0p, g0m)));
+          const float Fy = dstencil(st, __fsub_rn(g2c, g0c), __fsub_rn(g2p, g0p), __fsub_rn(g2m, g0m));
           if (!kSteady && walls && (y == 0 || y == ny - 1)) {
             // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
             const Row w0 = St::row(S.pops[s5m1], 0), w1 = St::row(S.pops[s5m1], 1);
@@ -552,13 +649,25 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
             if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
             const bool top = y != 0;
             wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
-            sx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
-            sy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+            sxv[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
+            syv[j] = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
           }
-          jv[j] = make_float2(sx + 0.5f * Fx, sy + 0.5f * Fy);
           jw[j] = true;
           Fx_cur[j] = Fx;
           Fy_cur[j] = Fy;
+        }
+        // n u* = sum f c + F / 2 (Eq. newvel)
+        if constexpr (kSteady) {
+          using O2 = Op<float2>;
+          const float2 h = O2::k(0.5f);
+          const float2 jx = O2::fma(h, make_float2(Fx_cur[0], Fx_cur[1]), make_float2(sxv[0], sxv[1]));
+          const float2 jy = O2::fma(h, make_float2(Fy_cur[0], Fy_cur[1]), make_float2(syv[0], syv[1]));
+          jv[0] = make_float2(jx.x, jy.x);
+          jv[1] = make_float2(jx.y, jy.y);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            jv[j] = make_float2(Op<float>::fma(0.5f, Fx_cur[j], sxv[j]), Op<float>::fma(0.5f, Fy_cur[j], syv[j]));
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j)
@@ -575,9 +684,12 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
         // population rows a-4 .. a-1: pair k-2 row 1, pair k-1 rows 0, 1, pair k row 0
         const Row q0p = St::row(S.pops[s5m2], 1), q1p = St::row(S.pops[s5m1], 0);
         const Row q2p = St::row(S.pops[s5m1], 1), q3p = St::row(S.pops[s5], 0);
-        // collision of row a-3+j (its inputs from the rings); fs, n, J, F out
-        auto site = [&](const int j, const int y, float *fs, float &n_o, float &Jx_o, float &Jy_o, float &Fx_o,
-                        float &Fy_o) {
+        // inputs of the collision of row a-3+j: gradients from the rings,
+        // n, n u*, F; pulled populations in f
+        struct In {
+          float n, Jx, Jy, Fx, Fy, dnx, dny, divJ;
+        };
+        auto inputs = [&](const int j, const int y, float *f) -> In {
           const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
           const float2 *j0p = j ? J1 : J0, *j1p = j ? J2 : J1, *j2p = j ? J3 : J2;
           const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
@@ -588,43 +700,41 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
             float sgm = 1.f, sgp = 1.f;
             if (bot) { m0 = m2; j0p = j2p; sgm = -1.f; }
             if (top) { m2 = m0; j2p = j0p; sgp = -1.f; }
-            const float2 g = j2p[t], h = j0p[t], c = j2p[t + 1], e = j0p[t + 1], d = j2p[t - 1], f = j0p[t - 1];
-            dJy = st.N * (sgp * g.y - sgm * h.y) + st.M * ((sgp * c.y - sgm * e.y) + (sgp * d.y - sgm * f.y));
+            const float2 g = j2p[t], h = j0p[t], c = j2p[t + 1], e = j0p[t + 1], d = j2p[t - 1], ff = j0p[t - 1];
+            dJy = st.N * (sgp * g.y - sgm * h.y) + st.M * ((sgp * c.y - sgm * e.y) + (sgp * d.y - sgm * ff.y));
             dJx = sdx2(st, j0p, j1p, j2p, t).x;
           } else {
             dJx = sdx2(st, j0p, j1p, j2p, tc).x;
             dJy = sdy2(st, j0p, j2p, tc).y;
           }
-          const float n = m1[tc];
-          const float dnx = sdx(st, m0, m1, m2, tc), dny = sdy(st, m0, m2, tc);
-          const float divJ = dJx + dJy;
+          In in;
+          in.n = m1[tc];
+          in.dnx = sdx(st, m0, m1, m2, tc);
+          in.dny = sdy(st, m0, m2, tc);
+          in.divJ = __fadd_rn(dJx, dJy);
           const float2 Jc = j1p[tc];
-          const float Jx = Jc.x, Jy = Jc.y;
-          float f[9];
+          in.Jx = Jc.x;
+          in.Jy = Jc.y;
+          in.Fx = Fx;
+          in.Fy = Fy;
           pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, tc, f, A);
           if (bot || top) {
             if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
-            wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
+            wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, in.n, f);
             if constexpr (St::kDev) add_refs(f, -A.ref_ax, -A.ref_dg);
           }
-          collide<St::kDev>(A, f, n, Jx, Jy, Fx, Fy, dnx, dny, divJ, fs, wr_ax, wr_dg);
-          n_o = n;
-          Jx_o = Jx;
-          Jy_o = Jy;
-          Fx_o = Fx;
-          Fy_o = Fy;
+          return in;
         };
-        // store row y and add it to the CTA's records
-        auto emit = [&](const int y, float *fs, const float n, const float Jx, const float Jy, const float Fx,
-                      const float Fy) {
+        // store row y and add it to the CTA's records; fs[0] is the rest
+        // population's remainder for FP32 storage, computed after the
+        // rounding for 16-bit storage
+        auto emit = [&](const int y, float *fs, const In &in) {
+          const float n = in.n, Jx = in.Jx, Jy = in.Jy, Fx = in.Fx, Fy = in.Fy;
           const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
           float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
             // The new state is streamed out (evict-first stores): it is
             // read again only by the next step.
-            // Collision conserves the site's mass exactly (A = 0, sum f^eq =
-            // n); the remainder form keeps rounded weights from biasing it.
-            fs[0] = n - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
 #pragma unroll
             for (int q = 0; q < 9; ++q) __stcs(o + q * plane, fs[q]);
             if (gx != 0) {
@@ -651,7 +761,7 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
               code[q - 1] = St::enc(fs[q]);
               fs[q] = St::dec(code[q - 1]);
             }
-            fs[0] = (n - r_sum) - (((fs[1] + fs[3]) + (fs[2] + fs[4])) + ((fs[5] + fs[7]) + (fs[6] + fs[8])));
+            fs[0] = rest_remainder<float>(Op<float>::sub(n, r_sum), fs);
             H *od = reinterpret_cast<H *>(O.fdev) + (A.off + x + (long long)y * pitch);
             o[0] = fs[0];
 #pragma unroll
@@ -689,22 +799,40 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
           }
         };
         if constexpr (kSteady) {
-          // both rows first, then their stores (inactive columns store nothing)
-          float fs[2][9], nv_[2], jx[2], jy[2], fx[2], fy[2];
+          // both rows at once (the collision in float2 lanes), then their
+          // stores (inactive columns store nothing)
+          float fa[9], fb[9];
+          const In ia = inputs(0, a - 3, fa), ib = inputs(1, a - 2, fb);
+          float2 f2[9], fs2[9];
 #pragma unroll
-          for (int j = 0; j < 2; ++j) site(j, a - 3 + j, fs[j], nv_[j], jx[j], jy[j], fx[j], fy[j]);
+          for (int q = 0; q < 9; ++q) f2[q] = make_float2(fa[q], fb[q]);
+          const float2 n2 = make_float2(ia.n, ib.n);
+          collide<St::kDev, float2>(A, f2, n2, make_float2(ia.Jx, ib.Jx), make_float2(ia.Jy, ib.Jy),
+                                    make_float2(ia.Fx, ib.Fx), make_float2(ia.Fy, ib.Fy),
+                                    make_float2(ia.dnx, ib.dnx), make_float2(ia.dny, ib.dny),
+                                    make_float2(ia.divJ, ib.divJ), fs2, wr_ax, wr_dg);
+          if constexpr (!St::kDev) fs2[0] = rest_remainder<float2>(n2, fs2);
           if (actD) {
+            float fsa[9], fsb[9];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) emit(a - 3 + j, fs[j], nv_[j], jx[j], jy[j], fx[j], fy[j]);
+            for (int q = 0; q < 9; ++q) {
+              fsa[q] = fs2[q].x;
+              fsb[q] = fs2[q].y;
+            }
+            emit(a - 3, fsa, ia);
+            emit(a - 2, fsb, ib);
           }
         } else {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             const int y = a - 3 + j;
             if (!(actD && y >= ya && y < yb)) continue;
-            float fs[9], nn, jxx, jyy, fxx, fyy;
-            site(j, y, fs, nn, jxx, jyy, fxx, fyy);
-            emit(y, fs, nn, jxx, jyy, fxx, fyy);
+            float f[9], fs[9];
+            const In in = inputs(j, y, f);
+            collide<St::kDev, float>(A, f, in.n, in.Jx, in.Jy, in.Fx, in.Fy, in.dnx, in.dny, in.divJ, fs, wr_ax,
+                                     wr_dg);
+            if constexpr (!St::kDev) fs[0] = rest_remainder<float>(in.n, fs);
+            emit(y, fs, in);
           }
         }
       }
@@ -1251,6 +1379,14 @@ cudaError_t sweep_make_maps(int store, void *base, int pitch, int ny, long long 
   return encode_map(store == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, dev,
                     pitch, ny, plane, 8, StoreBF16::kDevCols, m1);
 }
+
+void sweep_strips(int store, int nx, int nstrips, int *base_w, int *extra) {
+  const int qn = quantum_of(store);
+  *base_w = qn * (nx / (qn * nstrips));
+  *extra = (nx - *base_w * nstrips) / qn;
+}
+
+int sweep_min_strips(int store, int nx) { return (nx + maxw_of(store) - 1) / maxw_of(store); }
 
 void sweep_plan(int store, int nx, int ny, int *nstrips, int *base_w, int *extra, int *seg_h, int *nseg) {
   const int qn = quantum_of(store), maxw = maxw_of(store);

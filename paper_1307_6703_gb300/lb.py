@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_reduce_noalloc.argtypes = [P, C.c_int, C.c_int32, C.c_int32, C.c_double, P, P, P]
         lib.lb_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
         lib.lb_set_seg_h.argtypes = [P, C.c_int32]
+        lib.lb_get_tiling.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        lib.lb_set_tiling.argtypes = [P, C.c_int32, C.c_int32]
         lib.lb_batch_create.argtypes = [C.POINTER(lb_params), C.c_int32, C.POINTER(P)]
         lib.lb_batch_handle.argtypes = [P, C.c_int32]
         lib.lb_batch_handle.restype = P
@@ -91,7 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_batch_last_error.restype = C.c_char_p
         for name in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_reduce",
                      "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy",
-                     "lb_reduce_noalloc", "lb_autotune", "lb_batch_create", "lb_batch_step",
+                     "lb_reduce_noalloc", "lb_autotune", "lb_get_tiling", "lb_set_tiling", "lb_batch_create", "lb_batch_step",
                      "lb_batch_autotune", "lb_batch_destroy"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
@@ -213,6 +215,18 @@ def lb_autotune(h, steps: int = 20) -> int:
 def lb_set_seg_h(h, seg_h: int) -> None:
     """Fix the sweep kernel's segment height (rows per CTA) without tuning."""
     _check(load_library().lb_set_seg_h(h, seg_h), h)
+
+
+def lb_get_tiling(h) -> tuple[int, int]:
+    """(strip count, segment height) of the sweep kernel's tiling."""
+    ns, sh = C.c_int32(0), C.c_int32(0)
+    _check(load_library().lb_get_tiling(h, C.byref(ns), C.byref(sh)), h)
+    return ns.value, sh.value
+
+
+def lb_set_tiling(h, nstrips: int, seg_h: int) -> None:
+    """Fix the sweep kernel's strip count and segment height without tuning."""
+    _check(load_library().lb_set_tiling(h, nstrips, seg_h), h)
 
 
 def _bcheck(rc: int, b) -> int:

@@ -142,10 +142,15 @@ def test_fp32_config_512x256_1000_steps(u_w):
     The noisy symmetric quench is linearly unstable (spinodal
     decomposition): perturbations of FP32 size are amplified ~1e3 between
     steps 100 and 500.  The max relative density error is held to 1e-5 at
-    step 100, before the amplification, and at 1000 steps to the drift that
-    FP32 rounding produces in the oracle itself: at most 30x the divergence
-    of the oracle with its state rounded to FP32 after every step (FP32
-    arithmetic rounds each population ~25 times per step)."""
+    step 100, before the amplification, and at 1000 steps to a multiple of
+    the drift that FP32 rounding produces in the oracle itself (its state
+    rounded to FP32 after every step).  FP32 arithmetic rounds each
+    population ~25 times per step, and the amplification carries that
+    excess along: an ablation on this workload put FP32 kernels at 5-17x
+    that floor at step 1000 (the paper's term order with IEEE division
+    8.6x / 16.6x at U_w = 0.01 / 0.05; this kernel 7.0x / 12.8x, 4.7x /
+    10.2x with IEEE division in place of the approximate reciprocal).  The
+    bound, 20x, is 1.5x this kernel's largest measured ratio."""
     w = C2(u_w)
     n0 = noise_field(w)
     ref = oracle_for(w).init_fields(n0)
@@ -164,7 +169,8 @@ def test_fp32_config_512x256_1000_steps(u_w):
     print(f"fp32 error curve (step, max rel density error): {curve}; "
           f"oracle FP32-storage divergence at 1000 steps: {floor:.3e}")
     assert curve[0][1] <= 1e-5, curve
-    assert curve[-1][1] <= 30.0 * floor, (curve, floor)
+    print(f"ratio to the FP32-storage floor at 1000 steps: {curve[-1][1] / floor:.1f}")
+    assert curve[-1][1] <= 20.0 * floor, (curve, floor)
 
 
 def _settled_droplet():
