@@ -68,23 +68,41 @@ def kernel_source_digest() -> str:
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
-def profiled_traffic(precision: str):
-    """DRAM bytes per launch (read + write) of the step kernel from the
-    committed ncu summary, if it was taken on the current kernel source
-    (the summary states the source digest it was taken on); else None."""
+def profiled_traffic(precision: str, steps_per_launch: int):
+    """DRAM bytes (read + write) per launch of the timed kernel, from the
+    committed ncu summary: its back-to-back bytes per step (the dram
+    counters of one multi-step launch divided by its steps) times the steps
+    one timed launch runs.  Returned with its basis, and only if the summary
+    was taken on the current kernel source (it states the source digest);
+    else (None, reason)."""
     try:
         with open(PROFILE[precision]) as fh:
             text = fh.read()
     except OSError:
-        return None
-    digest, traffic = None, None
+        return None, "no committed ncu summary"
+    digest, per_step, basis = None, None, None
     for line in text.splitlines():
         if line.startswith("kernel source digest:"):
             m = re.search(r"`([0-9a-f]+)`", line)
             digest = m.group(1) if m else None
-        if line.startswith("dram bytes per launch:"):
-            traffic = float(line.split(":", 1)[1].split()[0])
-    return traffic if digest == kernel_source_digest() else None
+        if line.startswith("dram bytes per step:"):
+            per_step = float(line.split(":", 1)[1].split()[0])
+            basis = line.split(":", 1)[1].strip()
+    if per_step is None:
+        return None, "the summary gives no per-step dram bytes"
+    if digest != kernel_source_digest():
+        return None, "the kernel changed since the dram counters were taken"
+    return per_step * steps_per_launch, f"{steps_per_launch} steps x {basis}"
+
+
+def step_launches(steps: int, ntiles: int) -> tuple[int, str]:
+    """Kernel launches of one lb_step(h, steps) call and the kernel: one
+    step-kernel launch for a single step, else multi-step launches of at
+    most max(2, 2^30 / tiles) steps each."""
+    if steps == 1:
+        return 1, "lbk::sweep_step_kernel"
+    chunk = max(2, (1 << 30) // ntiles)
+    return -(-steps // chunk), "lbk::sweep_multi_kernel"
 
 
 def measured_peaks(key: str = "hbm_gbs"):
@@ -286,9 +304,15 @@ def run_ours(args):
 
     t_max = max_over_ranks(t_ms, dist)
     value = job_mlups(sites, args.steps, world, t_max)
-    per_launch_s = t_ms * 1e-3 / args.steps
-    achieved = b_alg * sites / per_launch_s / 1e9
+    nseg = -(-w.ny // seg_h)
+    launches, kernel = step_launches(args.steps, strips * nseg)
+    steps_per_launch = args.steps // launches
+    # algorithmic bytes of one launch over its duration (CUDA events around
+    # the timed call, which makes `launches` launches of equal length)
+    per_launch_s = t_ms * 1e-3 / launches
+    achieved = b_alg * sites * steps_per_launch / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
+    traffic, traffic_basis = profiled_traffic(args.precision, steps_per_launch)
 
     # --------------------------------------------- end to end through the ABI
     # Host input from pinned memory; every step's result (mass, momentum,
@@ -335,14 +359,15 @@ def run_ours(args):
                        "unstable_after_timing": unstable},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": profiled_traffic(args.precision),
-                         "peak_kind": peak_kind, "kernel": "lbk::sweep_step_kernel",
+                         "traffic": traffic, "traffic_basis": traffic_basis,
+                         "peak_kind": peak_kind, "kernel": kernel, "steps_per_launch": steps_per_launch,
+                         "algorithmic_bytes_per_launch": b_alg * sites * steps_per_launch,
                          "bytes_per_site": b_alg, "kernel_source_digest": kernel_source_digest()},
             "clocks": clocks,
             "e2e": {"value": round(e2e_mlups, 1), "unit": "MLUPS",
                     "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
                     "steps": k_e2e, "per_step_records_ok": e2e_ok},
-            "gpu_launches": args.steps,
+            "gpu_launches": launches,
         }
         if not args.no_cpu_baseline and world == 1:  # the host baseline is an N = 1 figure
             mlups, nth, sample = cpu_oracle_mlups(w, args.cpu_seconds, 64)
@@ -430,7 +455,12 @@ def run_batch(args):
     value = job_mlups(total_sites, args.steps, 1, t_ms)
     seq = sites * k_seq / (seq_ms * 1e-3) / 1e6
     peak, peak_kind = measured_peaks()
-    achieved = b_alg * sites / (t_ms * 1e-3 / args.steps) / 1e9
+    # one lb_batch_step call is one launch: a single step-kernel launch, or
+    # one persistent launch (its chunks hold 2^30 / items steps, over a
+    # million for this ensemble's few hundred items)
+    launches = 1
+    kernel = "lbk::sweep_batch_kernel" if args.steps == 1 else "lbk::sweep_batch_persist_kernel"
+    achieved = b_alg * sites * (args.steps // launches) / (t_ms * 1e-3 / launches) / 1e9
     if rank == 0:
         line = {
             "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
@@ -443,12 +473,13 @@ def run_batch(args):
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_kind": peak_kind, "kernel": "lbk::sweep_batch_kernel",
+                         "traffic_basis": "not captured for the ensemble",
+                         "peak_kind": peak_kind, "kernel": kernel, "steps_per_launch": args.steps // launches,
                          "bytes_per_site": b_alg},
             "one_by_one": {"value": round(seq, 1), "unit": "MLUPS", "steps": k_seq,
                            "launches_per_step": len(ws), "rank": 0},
             "clocks": clk.summary(),
-            "gpu_launches": args.steps,
+            "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -6,11 +6,8 @@
 // columns (W <= 116 for FP32 storage, <= 112 for 16-bit storage, strip
 // origins on 16-byte TMA coordinates) and row segments of up to 64 rows.  One
 // CTA of 124 threads, one per column of the 124-column window x0-4 ..
-// x0+119 (strip plus 4-column halos), sweeps its segment, two rows per
-// iteration: upwards in even segments, downwards in odd ones, so that the
-// rows two neighbouring segments both read (the 4-row warm-up of each, the
-// edge rows of the other) are read by both at about the same time and come
-// from L2 the second time.  Every row of the previous state is read by
+// x0+119 (strip plus 4-column halos), sweeps its segment upwards, two rows
+// per iteration.  Every row of the previous state is read from HBM once by
 // the TMA engine: tensor copies bring a pair of rows of all nine population
 // planes into a 5-slot ring in shared memory (one mbarrier per slot, waits
 // bounded): pair k+2 is requested as iteration k starts, into the slot that
@@ -101,8 +98,6 @@ struct StoreF32 {
   }
   __device__ static float get(Row p, int q, int c, const SweepArgs &) { return p[q * 2 * kCols + c]; }
   __device__ static float getd(Row p, int q, int c, const SweepArgs &) { return p[q * 2 * kCols + c]; }
-  // moving population (plane q >= 1, possibly known only at run time)
-  __device__ static float getv(Row p, int q, int c) { return p[q * 2 * kCols + c]; }
 };
 
 // 16-bit deviation storage: a float box {kCols, 2, 1} of the rest plane and a
@@ -139,9 +134,6 @@ struct StoreDev {
     if (q == 0) return p.f0[c];
     return dec(p.d[(q - 1) * 2 * kDevCols + c]);
   }
-  // deviation of a moving population (plane q >= 1, possibly known only at
-  // run time)
-  __device__ static float getv(const Row &p, int q, int c) { return dec(p.d[(q - 1) * 2 * kDevCols + c]); }
 };
 template <>
 __device__ __forceinline__ float StoreDev<__nv_bfloat16>::dec(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -279,20 +271,15 @@ struct Op<float2> {
 
 // Density and raw momentum sum_i f_i c_i of the pulled populations (16-bit
 // storage: deviations, n gets the references' sum r_sum):
-// E = f1 + (f5 + f8) and W = f3 + (f6 + f7) serve n and the x momentum,
-// N = f2 + (f5 + f6) and S = f4 + (f7 + f8) the y momentum.  Grouped so,
-// every sum keeps its bits when the lattice is mirrored in y (2 <-> 4,
-// 5 <-> 8, 6 <-> 7), which swaps N and S and so flips the sign of N - S
-// exactly: a tile swept downwards (which works in the mirrored frame) gives
-// the same bits as one swept upwards.
+// E = f1 + f5 + f8 and W = f3 + f6 + f7 serve n and the x momentum.
 template <class V>
 __device__ __forceinline__ void site_sums(const V *f, float r_sum, bool dev, V &n, V &sx, V &sy) {
   using O = Op<V>;
-  const V E = O::add(f[1], O::add(f[5], f[8])), W = O::add(f[3], O::add(f[6], f[7]));
+  const V E = O::add(O::add(f[1], f[5]), f[8]), W = O::add(O::add(f[3], f[6]), f[7]);
   sx = O::sub(E, W);
   n = O::add(O::add(f[0], O::add(f[2], f[4])), O::add(E, W));
   if (dev) n = O::add(n, O::k(r_sum));
-  sy = O::sub(O::add(f[2], O::add(f[5], f[6])), O::add(f[4], O::add(f[7], f[8])));
+  sy = O::sub(O::add(O::add(f[2], f[5]), f[6]), O::add(O::add(f[4], f[7]), f[8]));
 }
 
 // P = p^i - p^w = nT - nT/(1 - bn) + a n^2 (Eq. eqstate).
@@ -339,24 +326,15 @@ __device__ __forceinline__ float2 sdy2(const Sten &s, const float2 *r0, const fl
                      dstencil(s, __fsub_rn(g.y, h.y), __fsub_rn(c.y, e.y), __fsub_rn(d.y, f.y)));
 }
 
-// Stored planes of the populations with a y component, in the frame a tile
-// works in: a tile swept downwards sees the lattice mirrored in y, where
-// population 2 is the stored 4, 5 the stored 8 and 6 the stored 7 (and back).
-struct Mir {
-  int p2, p4, p5, p6, p7, p8;
-};
-
-// Propagated populations of the site in column t of row r1 (pull; rows r0
-// and r2 below and above it in the tile's frame).  With 16-bit storage
-// f[1..8] are the deviations d_i = f_i - r_i and f[0] is the rest
-// population; with FP32 storage they are the populations.
+// Propagated populations of the site in column t of row r1 (pull).  With
+// 16-bit storage f[1..8] are the deviations d_i = f_i - r_i and f[0] is the
+// rest population; with FP32 storage they are the populations.
 template <class St>
 __device__ __forceinline__ void pull(const typename St::Row &r0, const typename St::Row &r1,
-                                     const typename St::Row &r2, int t, float *f, const SweepArgs &A,
-                                     const Mir &m) {
+                                     const typename St::Row &r2, int t, float *f, const SweepArgs &A) {
   f[0] = St::getd(r1, 0, t, A); f[1] = St::getd(r1, 1, t - 1, A); f[3] = St::getd(r1, 3, t + 1, A);
-  f[2] = St::getv(r0, m.p2, t); f[5] = St::getv(r0, m.p5, t - 1); f[6] = St::getv(r0, m.p6, t + 1);
-  f[4] = St::getv(r2, m.p4, t); f[7] = St::getv(r2, m.p7, t + 1); f[8] = St::getv(r2, m.p8, t - 1);
+  f[2] = St::getd(r0, 2, t, A); f[5] = St::getd(r0, 5, t - 1, A); f[6] = St::getd(r0, 6, t + 1, A);
+  f[4] = St::getd(r2, 4, t, A); f[7] = St::getd(r2, 7, t + 1, A); f[8] = St::getd(r2, 8, t - 1, A);
 }
 
 // Deviations <-> populations of the moving links (16-bit storage only).
@@ -455,10 +433,10 @@ struct StepIO {
 // stopped at its next barrier and drained the copies still in flight).
 // kPersist: called once per tile by the multi-step kernel, which does not
 // hand its SM slots to a dependent grid early.
-template <class St, bool kPersist, bool kRev>
-__device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
-                                          const StepIO &O, const int strip, const int seg, double *rec,
-                                          const bool records) {
+template <class St, bool kPersist = false>
+__device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
+                                           const StepIO &O, const int strip, const int seg, double *rec,
+                                           const bool records) {
   using Row = typename St::Row;
   using Smem = SweepSmem<St::kSlotBytes>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -471,23 +449,6 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
   const int yb = min(A.ny, ya + A.seg_h);
   const int nx = A.nx, ny = A.ny;
   const bool walls = A.walls != 0;
-  // Odd segments are swept downwards, so that two neighbouring segments
-  // read the rows they share (each one's warm-up rows are the other's edge
-  // rows) at about the same time and the second read hits L2.  Such a tile
-  // works in the y-mirrored frame: its row y is stored row ymir - y, its
-  // populations 2/4, 5/8, 6/7 are the stored 4/2, 8/5, 7/6 (mir), the y
-  // components of momentum and force change sign, and the walls swap
-  // places.  Every operation of the step keeps its bits under that mirror,
-  // so the direction does not change the result.
-  // (kRev = seg is odd; a template parameter, so that every plane and row
-  // offset stays a compile-time constant)
-  constexpr bool rev = kRev;
-  constexpr int rv = kRev ? 1 : 0;
-  const int ymir = ya + yb - 1;
-  constexpr Mir mir = kRev ? Mir{4, 2, 8, 7, 6, 5} : Mir{2, 4, 5, 6, 7, 8};
-  // rows of the walls below and above, and their velocities, in the frame
-  const int yw0 = rev ? ymir - (ny - 1) : 0, yw1 = rev ? ymir : ny - 1;
-  const float u_lo = rev ? A.u_top : A.u_bot, u_hi = rev ? A.u_bot : A.u_top;
   const int x = x0 - 4 + t;  // interior column of this thread (may be a halo column)
   const bool actA = t >= 1 && t <= W + 6;
   const bool actB = t >= 2 && t <= W + 5;
@@ -529,14 +490,9 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
     return false;
   }
   int issued = min(kPairs, npairs);  // pairs requested so far (thread 0's count)
-  // Padded (+4) stored row at which the box of pair P starts.  The pair is
-  // the frame's rows ya-4+2P and ya-3+2P; downwards these are stored rows
-  // yb+3-2P and yb+2-2P, so the box starts at yb+2-2P and holds the frame's
-  // two rows in reverse order (slot row j ^ rv).
-  auto pair_y = [&](int P) { return rev ? yb + 6 - 2 * P : ya + 2 * P; };
   if (t == 0) {
     for (int P = 0; P < issued; ++P)
-      tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, pair_y(P));
+      tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
   }
   __syncthreads();
   if (!mbar_wait(smem_u32(&S.full[0]), 0, A.err)) S.abort = 1;
@@ -563,7 +519,7 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
       __syncthreads();
       if (t == 0 && k - 3 + kPairs < npairs) {
         const int slot = dec(s5m2, kPairs);
-        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, pair_y(k - 3 + kPairs));
+        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k - 3 + kPairs));
         ++issued;
       }
     }
@@ -575,8 +531,8 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
     // (Steady iterations compute both rows of each stage at once wherever
     // the arithmetic needs no neighbour data: row j in lane j of a float2.)
     {
-      const Row q0 = St::row(S.pops[s5], rv), q1 = St::row(S.pops[s5], rv ^ 1);      // rows a-1, a
-      const Row q2 = St::row(S.pops[s5p1], rv), q3 = St::row(S.pops[s5p1], rv ^ 1);  // rows a+1, a+2
+      const Row q0 = St::row(S.pops[s5], 0), q1 = St::row(S.pops[s5], 1);      // rows a-1, a
+      const Row q2 = St::row(S.pops[s5p1], 0), q3 = St::row(S.pops[s5p1], 1);  // rows a+1, a+2
       float sx_new[2] = {0.f, 0.f}, sy_new[2] = {0.f, 0.f};
       const int tc = kSteady ? tcl : t;
       // Each stage computes both rows before it stores either, so that the
@@ -585,8 +541,8 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
       bool nw[2] = {false, false};
       if constexpr (kSteady) {
         float fa[9], fb[9];
-        pull<St>(q0, q1, q2, tc, fa, A, mir);
-        pull<St>(q1, q2, q3, tc, fb, A, mir);
+        pull<St>(q0, q1, q2, tc, fa, A);
+        pull<St>(q1, q2, q3, tc, fb, A);
         float2 f2[9], n2, sx2, sy2;
 #pragma unroll
         for (int q = 0; q < 9; ++q) f2[q] = make_float2(fa[q], fb[q]);
@@ -600,21 +556,19 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
         for (int j = 0; j < 2; ++j) {
           const int y = a + j;
           const Row r0 = j ? q1 : q0, r1 = j ? q2 : q1, r2 = j ? q3 : q2;
-          if (actA && (!walls || (y >= yw0 && y <= yw1))) {
+          if (actA && (!walls || (y >= 0 && y <= ny - 1))) {
             float f[9];
-            pull<St>(r0, r1, r2, tc, f, A, mir);
+            pull<St>(r0, r1, r2, tc, f, A);
             float n;
             if constexpr (St::kDev) {
-              if (walls && (y == yw0 || y == yw1)) add_refs(f, A.ref_ax, A.ref_dg);
+              if (walls && (y == 0 || y == ny - 1)) add_refs(f, A.ref_ax, A.ref_dg);
             }
-            // the site's own populations (16-bit storage: with the references)
-            const float rax = St::kDev ? A.ref_ax : 0.f, rdg = St::kDev ? A.ref_dg : 0.f;
-            if (walls && y == yw0) {
-              n = St::get(r1, 0, t, A) + (rax + St::getv(r1, mir.p4, t)) + (rdg + St::getv(r1, mir.p7, t)) +
-                  (rdg + St::getv(r1, mir.p8, t)) + f[1] + f[3] + f[4] + f[7] + f[8];
-            } else if (walls && y == yw1) {
-              n = St::get(r1, 0, t, A) + (rax + St::getv(r1, mir.p2, t)) + (rdg + St::getv(r1, mir.p6, t)) +
-                  (rdg + St::getv(r1, mir.p5, t)) + f[1] + f[3] + f[2] + f[6] + f[5];
+            if (walls && y == 0) {
+              n = St::get(r1, 0, t, A) + St::get(r1, 4, t, A) + St::get(r1, 7, t, A) + St::get(r1, 8, t, A) +
+                  f[1] + f[3] + f[4] + f[7] + f[8];
+            } else if (walls && y == ny - 1) {
+              n = St::get(r1, 0, t, A) + St::get(r1, 2, t, A) + St::get(r1, 6, t, A) + St::get(r1, 5, t, A) +
+                  f[1] + f[3] + f[2] + f[6] + f[5];
             } else {
               site_sums<float>(f, r_sum, St::kDev, n, sx_new[j], sy_new[j]);
             }
@@ -647,9 +601,9 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
           for (int j = 0; j < 2; ++j) {
             const int y = a - 1 + j;
             const float *r0 = j ? n1 : n0, *r1 = j ? n2 : n1, *r2 = j ? n3 : n2;
-            if (actB && y >= ya - 2 && (!walls || (y >= yw0 && y <= yw1))) {
-              if (walls && y == yw0) r0 = r2;
-              if (walls && y == yw1) r2 = r0;
+            if (actB && y >= ya - 2 && (!walls || (y >= 0 && y <= ny - 1))) {
+              if (walls && y == 0) r0 = r2;
+              if (walls && y == ny - 1) r2 = r0;
               plv[j] = make_float2(pressure_diff<float>(r1[tc], A.T, A.a, A.b), slap(st, r0, r1, r2, tc));
               plw[j] = true;
             }
@@ -671,10 +625,10 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int y = a - 2 + j;
-          if (!(kSteady || (actC && y >= ya - 1 && (!walls || (y >= yw0 && y <= yw1))))) continue;
+          if (!(kSteady || (actC && y >= ya - 1 && (!walls || (y >= 0 && y <= ny - 1))))) continue;
           const float2 *p0 = j ? P1 : P0, *p1 = j ? P2 : P1, *p2 = j ? P3 : P2;
-          if (!kSteady && walls && y == yw0) p0 = p2;
-          if (!kSteady && walls && y == yw1) p2 = p0;
+          if (!kSteady && walls && y == 0) p0 = p2;
+          if (!kSteady && walls && y == ny - 1) p2 = p0;
           const float n = S.n[s3m1][j][tc];
           const float kn = __fmul_rn(A.kappa, n);
           // D P + kappa n D L = D G with G = P + kappa n L at the neighbours
@@ -686,17 +640,17 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
           const float Fx = __fmaf_rn(A.A0, sinx, dstencil(st, __fsub_rn(g1p, g1m), __fsub_rn(g2p, g2m),
                                                           __fsub_rn(g0p, g0m)));
           const float Fy = dstencil(st, __fsub_rn(g2c, g0c), __fsub_rn(g2p, g0p), __fsub_rn(g2m, g0m));
-          if (!kSteady && walls && (y == yw0 || y == yw1)) {
+          if (!kSteady && walls && (y == 0 || y == ny - 1)) {
             // populations of rows y-1 .. y+1: pairs k-1 and k of the ring
-            const Row w0 = St::row(S.pops[s5m1], rv), w1 = St::row(S.pops[s5m1], rv ^ 1);
-            const Row w2 = St::row(S.pops[s5], rv), w3 = St::row(S.pops[s5], rv ^ 1);
+            const Row w0 = St::row(S.pops[s5m1], 0), w1 = St::row(S.pops[s5m1], 1);
+            const Row w2 = St::row(S.pops[s5], 0), w3 = St::row(S.pops[s5], 1);
             float f[9];
-            pull<St>(j ? w1 : w0, j ? w2 : w1, j ? w3 : w2, t, f, A, mir);
+            pull<St>(j ? w1 : w0, j ? w2 : w1, j ? w3 : w2, t, f, A);
             if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
-            const bool top = y != yw0;
-            wall_fill<float>(top, top ? u_hi : u_lo, Fx, Fy, n, f);
-            float nw;  // (unused)
-            site_sums<float>(f, 0.f, false, nw, sxv[j], syv[j]);
+            const bool top = y != 0;
+            wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, n, f);
+            sxv[j] = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
+            syv[j] = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
           }
           jw[j] = true;
           Fx_cur[j] = Fx;
@@ -728,8 +682,8 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
         const float *n0 = S.n[s3m2][0], *n1 = S.n[s3m2][1], *n2 = S.n[s3m1][0], *n3 = S.n[s3m1][1];
         const float2 *J0 = S.J[s2m1][0], *J1 = S.J[s2m1][1], *J2 = S.J[s2][0], *J3 = S.J[s2][1];
         // population rows a-4 .. a-1: pair k-2 row 1, pair k-1 rows 0, 1, pair k row 0
-        const Row q0p = St::row(S.pops[s5m2], rv ^ 1), q1p = St::row(S.pops[s5m1], rv);
-        const Row q2p = St::row(S.pops[s5m1], rv ^ 1), q3p = St::row(S.pops[s5], rv);
+        const Row q0p = St::row(S.pops[s5m2], 1), q1p = St::row(S.pops[s5m1], 0);
+        const Row q2p = St::row(S.pops[s5m1], 1), q3p = St::row(S.pops[s5], 0);
         // inputs of the collision of row a-3+j: gradients from the rings,
         // n, n u*, F; pulled populations in f
         struct In {
@@ -739,7 +693,7 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
           const float *m0 = j ? n1 : n0, *m1 = j ? n2 : n1, *m2 = j ? n3 : n2;
           const float2 *j0p = j ? J1 : J0, *j1p = j ? J2 : J1, *j2p = j ? J3 : J2;
           const float Fx = j ? Fx_cur[0] : Fx_prev, Fy = j ? Fy_cur[0] : Fy_prev;
-          const bool bot = !kSteady && walls && y == yw0, top = !kSteady && walls && y == yw1;
+          const bool bot = !kSteady && walls && y == 0, top = !kSteady && walls && y == ny - 1;
           float dJy, dJx;
           if (bot || top) {
             // mirror rows across the wall: n and J_x even, J_y odd
@@ -763,10 +717,10 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
           in.Jy = Jc.y;
           in.Fx = Fx;
           in.Fy = Fy;
-          pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, tc, f, A, mir);
+          pull<St>(j ? q1p : q0p, j ? q2p : q1p, j ? q3p : q2p, tc, f, A);
           if (bot || top) {
             if constexpr (St::kDev) add_refs(f, A.ref_ax, A.ref_dg);
-            wall_fill<float>(top, top ? u_hi : u_lo, Fx, Fy, in.n, f);
+            wall_fill<float>(top, top ? A.u_top : A.u_bot, Fx, Fy, in.n, f);
             if constexpr (St::kDev) add_refs(f, -A.ref_ax, -A.ref_dg);
           }
           return in;
@@ -776,15 +730,8 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
         // rounding for 16-bit storage
         auto emit = [&](const int y, float *fs, const In &in) {
           const float n = in.n, Jx = in.Jx, Jy = in.Jy, Fx = in.Fx, Fy = in.Fy;
-          const int yr = rev ? ymir - y : y;  // stored row
-          const int gy = (kSteady || walls) ? 0 : ((yr < 4) ? ny : ((yr >= ny - 4) ? -ny : 0));
-          float *o = col + (long long)yr * pitch;
-          if (rev) {  // back to the stored populations
-            float v;
-            v = fs[2]; fs[2] = fs[4]; fs[4] = v;
-            v = fs[5]; fs[5] = fs[8]; fs[8] = v;
-            v = fs[6]; fs[6] = fs[7]; fs[7] = v;
-          }
+          const int gy = (kSteady || walls) ? 0 : ((y < 4) ? ny : ((y >= ny - 4) ? -ny : 0));
+          float *o = col + (long long)y * pitch;
           if constexpr (!St::kDev) {
             // The new state is streamed out (evict-first stores): it is
             // read again only by the next step.
@@ -815,7 +762,7 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
               fs[q] = St::dec(code[q - 1]);
             }
             fs[0] = rest_remainder<float>(Op<float>::sub(n, r_sum), fs);
-            H *od = reinterpret_cast<H *>(O.fdev) + (A.off + x + (long long)yr * pitch);
+            H *od = reinterpret_cast<H *>(O.fdev) + (A.off + x + (long long)y * pitch);
             o[0] = fs[0];
 #pragma unroll
             for (int q = 0; q < 8; ++q) od[q * plane] = code[q];
@@ -842,9 +789,9 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
           if (records) {
             if (!(n > 0.f && n < A.nmax && fabsf(Jx) + fabsf(Jy) < 3.0e38f)) bad = 1;
             acc_m += n;
-            if constexpr (!St::kDev) {  // (the frame's y components)
+            if constexpr (!St::kDev) {
               acc_x += Jx + 0.5f * Fx;
-              acc_y += rev ? -(Jy + 0.5f * Fy) : Jy + 0.5f * Fy;
+              acc_y += Jy + 0.5f * Fy;
             } else {  // momentum of the stored (rounded) populations; refs cancel
               acc_x += ((fs[1] - fs[3]) + (fs[5] - fs[6])) + (fs[8] - fs[7]);
               acc_y += ((fs[2] - fs[4]) + (fs[5] + fs[6])) - (fs[7] + fs[8]);
@@ -897,17 +844,13 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
     return true;
   };
   // Iteration k (a = ya - 3 + 2k) is steady -- every row of its four stages
-  // interior, see the lambda's note -- when k >= 3, a - 2 < yb and the
-  // stored rows of the frame's rows a - 3 .. a + 1 lie in [lo, hi] (walls:
-  // 1 .. ny - 2; periodic: 4 .. ny - 5, no ghost images).  Upwards the
-  // stored rows are a - 3 .. a + 1, downwards ymir - a - 1 .. ymir - a + 3.
-  // These are lower and upper bounds on k, so the steady iterations are the
-  // range [klo, khi).
+  // interior, see the lambda's note -- when k >= 3, a - 2 < yb and, with
+  // walls, 1 <= a - 3 and a + 1 <= ny - 2 (periodic: 4 <= a - 3 and
+  // a + 1 < ny - 4).  These are lower and upper bounds on k, so the steady
+  // iterations are the range [klo, khi).
   auto ceil2 = [](int v) { return (v + 1) >> 1; };  // ceil(v / 2), any sign
-  const int lo = walls ? 1 : 4, hi = walls ? ny - 2 : ny - 5;
-  const int klo = max(3, rev ? ceil2(ymir + 6 - hi - ya) : ceil2(lo + 6 - ya));
-  const int khi = min(min(kmax + 1, ceil2(yb - ya + 5)),
-                      rev ? ((ymir + 2 - lo - ya) >> 1) + 1 : ((hi + 2 - ya) >> 1) + 1);
+  const int klo = max(3, ceil2((walls ? 7 : 10) - ya));
+  const int khi = min(min(kmax + 1, ceil2(yb - ya + 5)), walls ? ((ny - ya) >> 1) + 1 : ceil2(ny - ya - 2));
   int k = 0;
   bool ok = true;
   for (; ok && k < min(klo, kmax + 1); ++k) ok = iteration(k, std::false_type{});
@@ -935,7 +878,7 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
   __syncthreads();
   red[0 * kThreads + t] = (double)acc_m;
   red[1 * kThreads + t] = (double)acc_x;
-  red[2 * kThreads + t] = (double)acc_y;  // (stored frame)
+  red[2 * kThreads + t] = (double)acc_y;
   red[3 * kThreads + t] = (double)bad;
   __syncthreads();
   // Warp 0 (a full warp) sums them in a fixed order: lane l takes columns
@@ -1009,15 +952,6 @@ __device__ __forceinline__ bool sweep_dir(const CUtensorMap *tin, const CUtensor
     }
   }
   return true;
-}
-
-// One tile in its direction (odd segments downwards).
-template <class St, bool kPersist = false>
-__device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
-                                           const StepIO &O, const int strip, const int seg, double *rec,
-                                           const bool records) {
-  if (seg & 1) return sweep_dir<St, kPersist, true>(tin, tdev, A, O, strip, seg, rec, records);
-  return sweep_dir<St, kPersist, false>(tin, tdev, A, O, strip, seg, rec, records);
 }
 
 template <class St>
@@ -1525,8 +1459,7 @@ cudaError_t launch_sweep_batch_persist(int store, const BatchItem *items, const 
 
 // Tiles each tile of the sweep depends on (see sweep_batch_persist_kernel): the
 // owners of every site its TMA boxes read -- columns x0-4 .. x0+123 and
-// rows ya-4 .. yb+4 upwards, ya-5 .. yb+3 downwards (the last box may hold
-// one row beyond the ones used), periodic images mapped back to the site they copy
+// rows ya-4 .. yb+4, periodic images mapped back to the site they copy
 // (rows outside the lattice with walls are never written) -- and,
 // symmetrically, every tile whose window reads its sites.
 void sweep_deps(int store, int nx, int ny, int walls, int nstrips, int base_w, int extra, int seg_h,
@@ -1552,7 +1485,7 @@ void sweep_deps(int store, int nx, int ny, int walls, int nstrips, int base_w, i
     for (int g = 0; g < nseg; ++g) {
       const int ya = g * seg_h, yb = std::min(ny, ya + seg_h);
       gs.clear();
-      for (int y = ya - 5; y <= yb + 4; ++y) {
+      for (int y = ya - 4; y <= yb + 4; ++y) {
         if (walls && (y < 0 || y >= ny)) continue;
         gs.push_back((((y % ny) + ny) % ny) / seg_h);
       }
