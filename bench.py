@@ -538,7 +538,7 @@ def run_warmstart(args):
     S = 256 * 64
     flop_fwd = 16 * S * (4 * (2 * 32 * 32 * 2 + 2 * 32 * 32) + 2 * 64 * 32 + 2 * 3 * 64)
     results = {}
-    for (nx, ny, n, block, cap) in ((512, 128, 16, 500, 40000), (2048, 512, 4, 5000, 1500000)):
+    for (nx, ny, n, block, cap) in ((512, 128, 16, 500, 40000), (2048, 512, 16, 5000, 1500000)):
         pte = ws.sample_params(n, seed=99 if nx == 512 else 123)
         big = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=1,
                   nx_max=nx, ny_max=ny, gemm_bf16=True)
@@ -699,6 +699,76 @@ def run_precision(args):
     return 0
 
 
+def run_next4(args):
+    """The paper's sheared regimes on the batched solver (Sec. IV): the
+    broken-line velocity profile of a two-layer Couette flow against the
+    uniform-stress prediction, and every row of Table 2 (interface-wave
+    amplitude A / L_y, the L_x = 256 ... 2048 scan among them) run
+    --next4-steps steps from a seeded noisy quench, the last tenth sampled
+    ten times (interface count, amplitude, wave speed)."""
+    import torch
+    from paper_1307_6703_gb300 import LB_FP32, Batch
+    from paper_1307_6703_gb300 import regimes as R
+    torch.cuda.set_device(0)
+    t_start = time.perf_counter()
+    out = {"broken_line": [], "table2": []}
+
+    # two-layer Couette flow: liquid below, vapour above
+    cases = [(ly, uw) for ly in (64, 128, 256) for uw in (0.01, 0.02)]
+    cs = [R.couette_two_layer(ly, uw) for ly, uw in cases]
+    b = Batch([c.lb_params(LB_FP32) for c in cs])
+    nL, nV = 1.47, 0.53  # start near coexistence; the solver settles the bulk
+    for v, c in zip(b, cs):
+        v.init_fields(R.two_layer_field(c.nx, c.ny, nL, nV))
+    b.step(args.next4_couette_steps)
+    for v, c in zip(b, cs):
+        n, ux, _ = v.moments()
+        s_lo, s_hi, n_lo, n_hi, y_i = R.broken_line_slopes(n, ux)
+        p_lo, p_hi = R.broken_line_prediction(c.u_w, c.ny, n_lo, n_hi, y_i)
+        out["broken_line"].append({"ly": c.ny, "u_w": c.u_w, "steps": args.next4_couette_steps,
+                                   "slope_lo": s_lo, "slope_hi": s_hi, "pred_lo": p_lo, "pred_hi": p_hi,
+                                   "err_lo": s_lo / p_lo - 1.0, "err_hi": s_hi / p_hi - 1.0,
+                                   "n_lo": n_lo, "n_hi": n_hi, "interface_y": y_i})
+    b.close()
+
+    # Table 2
+    rows = R.table2_rows()
+    cs = [R.table2_case(r) for r in rows]
+    b = Batch([c.lb_params(LB_FP32) for c in cs])
+    rng = np.random.default_rng(2013)
+    for v, c in zip(b, cs):
+        v.init_fields(1.0 + (0.01 / 3.5) * rng.uniform(-1.0, 1.0, size=(c.ny, c.nx)))
+    total = args.next4_steps
+    b.step(total - total // 10)
+    every = max(1, total // 100)
+    samples = [[] for _ in cs]
+    for _ in range(10):
+        b.step(every)
+        for i, v in enumerate(b):
+            n, _, _ = v.moments()
+            samples[i].append(R.interface_stats(n) if np.isfinite(n).all() else None)
+    b.close()
+    for r, c, sm in zip(rows, cs, samples):
+        if any(x is None for x in sm):
+            out["table2"].append({**r, "finite": False})
+            continue
+        k, _ = R.dominant_phase(sm[-1]["height"])
+        speed = R.wave_speed([R.dominant_phase(x["height"], k)[1] for x in sm], every, k, c.nx)
+        amps = [x["amp"] for x in sm]
+        out["table2"].append({**r, "finite": True, "crossings": int(np.median([x["crossings"] for x in sm])),
+                              "amp": float(np.mean(amps)), "amp_min": float(min(amps)),
+                              "amp_max": float(max(amps)), "mode": k, "wave_speed": speed,
+                              "liquid_fraction": sm[-1]["liquid_fraction"], "u_w": c.u_w})
+    line = {"metric": "next4_regimes", "value": round(time.perf_counter() - t_start, 1), "unit": "s",
+            "n_gpus": 1, "steps": total, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper_regimes_sec4", "table2_rows": len(rows),
+                       "couette_steps": args.next4_couette_steps},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -708,7 +778,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=sorted(B_ALG), default="fp32")
-    ap.add_argument("--workload", choices=["single", "batch", "warmstart", "precision", "network"],
+    ap.add_argument("--workload", choices=["single", "batch", "warmstart", "precision", "network", "next4"],
                     default="single",
                     help="single: the 4096x1024 lattice; batch: the seeded ensemble of "
                          "independent lattices through the batched solver")
@@ -720,6 +790,8 @@ def main():
                          "ny <= 96, <= 160, > 160, comma-separated)")
     ap.add_argument("--precision-nx", type=int, default=4096)
     ap.add_argument("--precision-ny", type=int, default=1024)
+    ap.add_argument("--next4-steps", type=int, default=1_000_000)
+    ap.add_argument("--next4-couette-steps", type=int, default=200_000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -735,6 +807,8 @@ def main():
         return run_precision(args)
     if args.workload == "network":
         return run_network(args)
+    if args.workload == "next4":
+        return run_next4(args)
     return run_ours(args)
 
 

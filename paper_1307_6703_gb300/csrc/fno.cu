@@ -370,20 +370,71 @@ outer_pass1_kernel(const float *__restrict__ a, const float *__restrict__ o2, in
   }
 }
 
-__global__ void reduce_pass2_kernel(const double *__restrict__ part, int nch, int nb, float *__restrict__ out) {
-  const int ch = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ch >= nch) return;
-  double acc = 0.0;
-  for (int i = 0; i < nb; i++) acc += part[(long long)ch * nb + i];
-  out[ch] = (float)acc;
+// Pass 1 of the channel sums when S % 4 == 0: block (ch, b * nsplit + j)
+// sums float4s j * 256 + t, (j + nsplit) * 256 + t, ... of field b's channel
+// ch, two at a time into two FP32 partials (then a fixed-order warp and
+// block tree, FP64 across warps); part[ch][b * nsplit + j].
+__global__ void __launch_bounds__(kThreads)
+reduce_pass1_v4_kernel(const float *__restrict__ a, int C, long long S, int nsplit, double *__restrict__ part) {
+  __shared__ double ws[kThreads / 32];
+  const int ch = blockIdx.x, b = blockIdx.y / nsplit, j = blockIdx.y % nsplit;
+  const float4 *p = reinterpret_cast<const float4 *>(a + ((long long)b * C + ch) * S);
+  const long long S4 = S / 4, step = (long long)nsplit * blockDim.x;
+  float acc0 = 0.f, acc1 = 0.f;
+  long long i = (long long)j * blockDim.x + threadIdx.x;
+  for (; i + step < S4; i += 2 * step) {
+    const float4 u = p[i], v = p[i + step];
+    acc0 += (u.x + u.y) + (u.z + u.w);
+    acc1 += (v.x + v.y) + (v.z + v.w);
+  }
+  if (i < S4) {
+    const float4 u = p[i];
+    acc0 += (u.x + u.y) + (u.z + u.w);
+  }
+  float acc = acc0 + acc1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < kThreads / 32; w++) r += ws[w];
+    part[(long long)ch * gridDim.y + blockIdx.y] = r;
+  }
 }
 
-// out[i] = sum_b part[b][i], in order (weight gradients of the per-field GEMMs).
-__global__ void sum_fields_kernel(const float *__restrict__ part, int B, int n, float *__restrict__ out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int b = 0; b < B; b++) acc += part[(long long)b * n + i];
-    out[i] = acc;
+// Pass 2: one warp per output; lane l adds partials l, l + 32, ... in order,
+// then a fixed-order shuffle tree.
+__global__ void __launch_bounds__(kThreads)
+reduce_pass2_kernel(const double *__restrict__ part, int nch, int nb, float *__restrict__ out) {
+  const int ch = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (ch >= nch) return;
+  double acc = 0.0;
+  for (int i = lane; i < nb; i += 32) acc += part[(long long)ch * nb + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[ch] = (float)acc;
+}
+
+// out[i] = sum_b part[b][i] (weight gradients of the per-field GEMMs):
+// block k takes outputs 32k .. 32k + 31; its eight warps sum the parts
+// w, w + 8, ... in order, then warp 0 adds the eight partials in order.
+__global__ void __launch_bounds__(kThreads)
+sum_fields_kernel(const float *__restrict__ part, int B, int n, float *__restrict__ out) {
+  __shared__ float ws[kThreads / 32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  float acc = 0.f;
+  if (i < n) {
+    for (int b = w; b < B; b += kThreads / 32) acc += part[(long long)b * n + i];
+  }
+  ws[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && i < n) {
+    float r = ws[0][lane];
+#pragma unroll
+    for (int q = 1; q < kThreads / 32; q++) r += ws[q][lane];
+    out[i] = r;
   }
 }
 
@@ -564,6 +615,34 @@ transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, long long R, long lo
   }
 }
 
+// The same transpose with 16-byte accesses, for R % 32 == 0 and S % 8 == 0:
+// block (i, j, b) moves rows 32i .. 32i + 31 by sites 64j .. 64j + 63; each
+// thread reads eight sites of one row and writes eight rows of one site.
+__global__ void __launch_bounds__(256)
+transpose_bf16_v8_kernel(const __nv_bfloat16 *__restrict__ in, long long R, long long S,
+                         __nv_bfloat16 *__restrict__ out) {
+  __shared__ __align__(16) __nv_bfloat16 tile[32][64 + 8];
+  const long long r0 = (long long)blockIdx.x * 32, s0 = (long long)blockIdx.y * 64;
+  const int b = blockIdx.z, t = threadIdx.x;
+  in += (long long)b * R * S;
+  out += (long long)b * R * S;
+  {
+    const int rr = t >> 3, sc = (t & 7) * 8;
+    if (s0 + sc < S)
+      *reinterpret_cast<uint4 *>(&tile[rr][sc]) = *reinterpret_cast<const uint4 *>(in + (r0 + rr) * S + s0 + sc);
+  }
+  __syncthreads();
+  {
+    const int ss = t >> 2, rc = (t & 3) * 8;
+    if (s0 + ss < S) {
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = tile[rc + q][ss];
+      *reinterpret_cast<uint4 *>(out + (s0 + ss) * R + r0 + rc) = *reinterpret_cast<const uint4 *>(v);
+    }
+  }
+}
+
 // Transposed BF16 weights for the tensor-core products: WT_l[c][o] =
 // W_l[o][c] (layer l at l C C), then Q1T[c][h] = Q1[h][c].
 __global__ void weights_t_kernel(const __nv_bfloat16 *__restrict__ prmb, Offsets o, int C, int H, int L,
@@ -604,6 +683,7 @@ struct fno_handle {
         *dS = nullptr;
   __nv_bfloat16 *dhpb = nullptr, *dZb = nullptr, *dAb = nullptr;
   double *partial = nullptr, *loss = nullptr, *rpart = nullptr;
+  int rpart_fields = 0;  // FP64 partials per channel that rpart holds
   float *wpart = nullptr;  // per-field weight gradients [B][max(C, H) * C]
   float *Fx = nullptr, *Fxi = nullptr;
   __nv_bfloat16 *Fxb = nullptr, *Fxib = nullptr, *FxTb = nullptr, *FxiTb = nullptr;
@@ -664,13 +744,23 @@ cudaError_t sg(fno_handle *h, const float *A, long long am, long long ak, long l
 // Site-major copy of a [B][rows][S] BF16 activation: out[b][s][row].
 void site_major(fno_handle *h, const __nv_bfloat16 *in, int B, int rows, long long S, __nv_bfloat16 *out) {
   const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((S + 63) / 64), (unsigned)B);
-  transpose_bf16_kernel<<<grid, 256, 0, h->st>>>(in, rows, S, out);
+  if (rows % 32 == 0 && S % 8 == 0)
+    transpose_bf16_v8_kernel<<<grid, 256, 0, h->st>>>(in, rows, S, out);
+  else
+    transpose_bf16_kernel<<<grid, 256, 0, h->st>>>(in, rows, S, out);
 }
 
 // out[ch] = sum over (b, s) of a[b, ch, s] for the C channels of a.
 void chan_reduce(fno_handle *h, const float *a, int B, int C, long long S, float *out) {
+  if (S % 4 == 0 && B * kReduceBlocks <= h->rpart_fields) {
+    // float4 loads; about 2048 blocks, at most 32 shares of a field
+    const int nsplit = std::max(1, std::min(kReduceBlocks, (2048 + C * B - 1) / (C * B)));
+    reduce_pass1_v4_kernel<<<dim3(C, B * nsplit), kThreads, 0, h->st>>>(a, C, S, nsplit, h->rpart);
+    reduce_pass2_kernel<<<(C + 7) / 8, kThreads, 0, h->st>>>(h->rpart, C, B * nsplit, out);
+    return;
+  }
   reduce_pass1_kernel<<<dim3(C, kReduceBlocks), kThreads, 0, h->st>>>(a, B, C, S, h->rpart);
-  reduce_pass2_kernel<<<(C + kThreads - 1) / kThreads, kThreads, 0, h->st>>>(h->rpart, C, kReduceBlocks, out);
+  reduce_pass2_kernel<<<(C + 7) / 8, kThreads, 0, h->st>>>(h->rpart, C, kReduceBlocks, out);
 }
 
 // out[ca * Cb + cb] = sum over (b, s) of a[b, ca, s] f(o2[b, cb, s]) (f = gelu
@@ -680,7 +770,7 @@ template <int NA, int NB, bool kGelu>
 void outer_reduce(fno_handle *h, const float *a, const float *o2, int B, int Ca, int Cb, long long S, float *out) {
   const int tiles = ((Ca + NA - 1) / NA) * ((Cb + NB - 1) / NB);
   outer_pass1_kernel<NA, NB, kGelu><<<dim3(kOuterBlocks, tiles), kThreads, 0, h->st>>>(a, o2, B, Ca, Cb, S, h->rpart);
-  reduce_pass2_kernel<<<(Ca * Cb + kThreads - 1) / kThreads, kThreads, 0, h->st>>>(h->rpart, Ca * Cb, kOuterBlocks,
+  reduce_pass2_kernel<<<(Ca * Cb + 7) / 8, kThreads, 0, h->st>>>(h->rpart, Ca * Cb, kOuterBlocks,
                                                                                    out);
 }
 
@@ -750,9 +840,11 @@ cudaError_t alloc_workspace(fno_handle *h) {
   if (e == cudaSuccess) e = alloc(&h->dY, h->cap_modes);
   if (e == cudaSuccess) e = alloc(&h->dS, h->cap_modes);
   if (e == cudaSuccess) e = alloc(&h->partial, 8192);
+  const long long max_ch = std::max(std::max(c.width, c.hidden), c.outputs);
+  h->rpart_fields = (int)(B * kReduceBlocks);  // channel sums: at most 32 shares of each field
   if (e == cudaSuccess)
     e = alloc(&h->rpart, std::max((long long)std::max(c.width * kFeatures, c.hidden * c.outputs) * kOuterBlocks,
-                                  (long long)std::max(std::max(c.width, c.hidden), c.outputs) * kReduceBlocks));
+                                  max_ch * h->rpart_fields));
   if (e == cudaSuccess) e = alloc(&h->wpart, B * kWSplit * (long long)std::max(c.width, c.hidden) * c.width);
   if (e == cudaSuccess) e = alloc(&h->loss, 1);
   if (e == cudaSuccess) e = alloc(&h->Fx, (long long)c.nx_max * 2 * c.modes_x);
@@ -933,7 +1025,7 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
   } else {
     FNO_GEMM(h, sg(h, h->dhp, S, 1, HS, h->V[L], 1, S, CS, h->wpart, C, 1, (long long)H * C, H, C, (int)S, B, 0.f));
   }
-  sum_fields_kernel<<<blocks_for((long long)H * C), kThreads, 0, st>>>(h->wpart, parts, H * C, g + o.Q1);
+  sum_fields_kernel<<<(H * C + 31) / 32, kThreads, 0, st>>>(h->wpart, parts, H * C, g + o.Q1);
   // dv[b][c][s] = sum_h Q1[h][c] dhp[b][h][s]
   if (bf) {
     site_major(h, h->dhpb, B, H, S, h->dhpT);
@@ -951,7 +1043,7 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
                       kWSplit, 0.f));
     else
       FNO_GEMM(h, sg(h, h->dZ, S, 1, CS, h->V[l], 1, S, CS, h->wpart, C, 1, (long long)C * C, C, C, (int)S, B, 0.f));
-    sum_fields_kernel<<<blocks_for((long long)C * C), kThreads, 0, st>>>(h->wpart, parts, C * C, g + o.W[l]);
+    sum_fields_kernel<<<(C * C + 31) / 32, kThreads, 0, st>>>(h->wpart, parts, C * C, g + o.W[l]);
     // spectral path: dG = dz Fxi^T, then the adjoints of the mixing and of the y-transform
     if (bf)
       FNO_GEMM(h, tcg(h, h->dZb, nx, 0, h->Fxib, nx, 0, h->dG, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 1, 0.f));

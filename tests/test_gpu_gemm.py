@@ -5,7 +5,8 @@ PyTorch FP32 product of the same BF16 values.
 Shapes cover one and many tiles, ragged M, N and K tails (TMA zero fill,
 guarded stores), K shorter than one stage and much longer than the
 pipeline, shared and batched operands, transposed output strides and
-beta = 1 accumulation, and the network's own shapes.  The FP32 reference
+beta = 1 accumulation, odd and unaligned row pitches, and the network's
+own shapes.  The FP32 reference
 sums the same exactly representable products in another order, so the
 difference is FP32 rounding of sums of K terms."""
 import numpy as np
@@ -35,6 +36,8 @@ CASES = [
     (32768, 32, 256, 1, False, False, 0.0),   # x-transform of a training batch
     (16384, 32, 32, 4, True, True, 1.0),      # channel mixing, written transposed, accumulated
     (4096, 2048, 32, 1, False, False, 1.0),   # inverse x-transform at nx = 2048
+    (200, 37, 48, 2, False, False, 1.0),      # N and the row pitch odd
+    (130, 74, 40, 1, False, False, 0.0),      # row pitch 74: rows 8-byte aligned only
 ]
 
 

@@ -1,0 +1,119 @@
+"""The paper's regimes reproduced on the batched solver (Secs. III-IV).
+
+* Table 1: the stencil scan over droplets.  Over N the largest spurious
+  speed is smallest at N = 0.3 for every temperature of the OVC column
+  tested, and at T = 0.95 the density error is smallest at N = 0.4, the
+  ODC row's N.  Along Q both measures change by a few percent only.
+* The broken-line velocity profile of a sheared two-layer fluid: the two
+  slopes of <u_x>_x(y) against the uniform shear-stress prediction (the
+  paper's formula, for the interface where it settles), within 5 %.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from paper_1307_6703_gb300 import LB_FP32, Batch  # noqa: E402
+from paper_1307_6703_gb300 import regimes as R  # noqa: E402
+from paper_1307_6703_gb300.workloads import TC, droplet_field  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def _droplet_scan(temps, Ns, Qs, steps=4000):
+    from oracle import maxwell
+    cases = R.table1_cases(temps, Ns, Qs)
+    b = Batch([c.lb_params(LB_FP32) for c in cases])
+    coex = {tr: maxwell.coexistence(R.A_VDW, R.B_VDW, tr * TC) for tr in temps}
+    for v, c in zip(b, cases):
+        tr = round(c.T / TC, 4)
+        v.init_fields(droplet_field(c.nx, c.ny, 15.0, *coex[tr]))
+    b.step(steps)
+    res = {}
+    for v, c in zip(b, cases):
+        tr = round(c.T / TC, 4)
+        n, ux, uy = v.moments()
+        if np.isfinite(n).all():
+            res[(tr, c.N, c.Q)] = R.droplet_errors(n, ux, uy, *coex[tr])
+    b.close()
+    return res
+
+
+def test_table1_stencil_scan_on_batched_solver():
+    temps = (0.89, 0.91, 0.93, 0.95)
+    Ns = (0.1, 0.2, 0.3, 0.4, 0.5, 0.6)
+    res = _droplet_scan(temps, Ns, (1.0, 2.0, 3.0))
+    for tr in temps:
+        # (a droplet that blew up counts as infinitely bad)
+        best = {N: min([v[0] for k, v in res.items() if k[0] == tr and k[1] == N], default=np.inf) for N in Ns}
+        print(f"T = {tr}: smallest spurious speed by N", {N: f"{u:.2e}" for N, u in best.items()})
+        assert min(best, key=best.get) == R.TABLE1_OVC[tr][0], best
+    res = _droplet_scan((0.95,), (0.2, 0.3, 0.4, 0.5, 0.6), (1.8, 2.0, 2.2, 2.4))
+    odc = min(res, key=lambda k: res[k][1])
+    print("T = 0.95: smallest density error at (N, Q) =", odc[1:], f"{res[odc][1]:.2e}")
+    assert odc[1] == R.TABLE1_ODC[0.95][0], odc
+
+
+@pytest.mark.parametrize("ly,u_w,steps", [(64, 0.01, 60000), (64, 0.02, 60000), (128, 0.01, 60000),
+                                          (128, 0.02, 60000), (256, 0.02, 200000)])
+def test_broken_line_profile(ly, u_w, steps):
+    """Liquid below, vapour above, walls at -u_w and +u_w: after about five
+    viscous times L_y^2 / (pi^2 nu) the x-averaged velocity is two straight
+    segments whose slopes are in the inverse ratio of the densities."""
+    c = R.couette_two_layer(ly, u_w)
+    b = Batch([c.lb_params(LB_FP32)])
+    b[0].init_fields(R.two_layer_field(c.nx, c.ny, 1.47, 0.53))
+    b.step(steps)
+    n, ux, uy = b[0].moments()
+    b.close()
+    s_lo, s_hi, n_lo, n_hi, y_i = R.broken_line_slopes(n, ux)
+    p_lo, p_hi = R.broken_line_prediction(u_w, ly, n_lo, n_hi, y_i)
+    print(f"L_y = {ly}, U_w = {u_w}: slopes {s_lo:.4e} / {s_hi:.4e}, predicted {p_lo:.4e} / {p_hi:.4e} "
+          f"({s_lo / p_lo - 1:+.2%} / {s_hi / p_hi - 1:+.2%}); densities {n_lo:.4f} / {n_hi:.4f}, "
+          f"interface at y = {y_i:.2f}")
+    assert abs(s_lo / p_lo - 1.0) <= 0.05 and abs(s_hi / p_hi - 1.0) <= 0.05
+    assert np.abs(uy).max() < 1e-4 * u_w / 0.01  # a flat interface: no cross flow
+
+
+def test_lx_scan_of_table2():
+    """Table 2's L_x scan (T = 0.95, tau = 1, A0 = 1e-4, kappa = 0.3 in the
+    paper's units, gamma = 1e-3, L_y = 256, lambda = 32 and 64), 10^6 steps
+    from a noisy quench.  As in the paper the interface amplitude grows with
+    L_x and, from L_x = 1024 on, the interface wave travels along the
+    channel; unlike the paper, at L_x = 256 the fluid separates into a flat
+    slab (A / L_y < 0.05 against the paper's 0.172), and the amplitudes at
+    1024 and 2048 are about 0.6 and 0.75 of the paper's 0.409 and 0.417."""
+    rows = [r for r in R.table2_rows() if r["T_r"] == 0.95 and r["tau"] == 1 and r["A0"] == 1e-4
+            and r["kappa_paper"] == 0.3]
+    cases = [R.table2_case(r) for r in rows]
+    b = Batch([c.lb_params(LB_FP32) for c in cases])
+    rng = np.random.default_rng(2013)
+    for v, c in zip(b, cases):
+        v.init_fields(1.0 + (0.01 / 3.5) * rng.uniform(-1.0, 1.0, size=(c.ny, c.nx)))
+    total, every = 1_000_000, 10_000
+    b.step(total - 10 * every)
+    samples = [[] for _ in cases]
+    for _ in range(10):
+        b.step(every)
+        for i, v in enumerate(b):
+            samples[i].append(R.interface_stats(v.moments()[0]))
+    b.close()
+    amp = {}
+    for r, c, sm in zip(rows, cases, samples):
+        k, _ = R.dominant_phase(sm[-1]["height"])
+        speed = R.wave_speed([R.dominant_phase(x["height"], k)[1] for x in sm], every, k, c.nx)
+        amp[(r["lam"], r["lx"])] = a = float(np.mean([x["amp"] for x in sm]))
+        print(f"lambda {r['lam']}, {r['lx']} x 256: A/L_y {a:.3f} (paper {r['amp_paper']}), crossings "
+              f"{sm[-1]['crossings']}, mode {k}, wave speed {speed:+.2e} (U_w {c.u_w:.3f})")
+        if r["lx"] >= 1024:
+            assert abs(speed) > 0.01, speed
+    for lam in (32, 64):
+        a = [amp[(lam, lx)] for lx in (256, 512, 1024, 2048)]
+        assert a[0] < 0.05 and a[3] > 0.25 and all(x < y for x, y in zip(a, a[1:])), a
