@@ -488,10 +488,12 @@ def run_batch(args):
 
 
 def run_warmstart(args):
-    """Learned warm start: train the network on solver-generated steady
-    states, then steps (and wall time, network inference included) to the
-    steady state from the prediction against from a noisy uniform state, on
-    held-out draws at 512x128 and 2048x512."""
+    """Learned warm start: train the network on solver-generated settled
+    states (static striped states, and travelling interface waves
+    phase-aligned), then steps (and wall time, network inference included)
+    to the settled state from the prediction against from a noisy uniform
+    state, on held-out draws: static regime at 512x128 and 2048x512, wave
+    regime at 1024x256."""
     import torch
     from paper_1307_6703_gb300 import warmstart as ws
     from paper_1307_6703_gb300.fno import Fno
@@ -504,16 +506,21 @@ def run_warmstart(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     ptr = ws.sample_params(1024, seed=1)
-    n1, d1 = ws.generate(ptr[:768], 256, 64, 25000, seed=1)
-    n2, d2 = ws.generate(ptr[768:], 512, 128, 30000, seed=2)
-    k1, k2 = d1 <= ws.STEADY_TOL, d2 <= ws.STEADY_TOL
+    pwv = ws.sample_params(256, seed=3, regime="wave")
+    n1, d1, _ = ws.generate(ptr[:768], 256, 64, 25000, seed=1)
+    n2, d2, _ = ws.generate(ptr[768:], 512, 128, 30000, seed=2)
+    n3, d3, m3 = ws.generate(pwv, 512, 128, 60000, seed=3)
+    k1, k2, k3 = d1 <= ws.STEADY_TOL, d2 <= ws.STEADY_TOL, d3 <= ws.STEADY_TOL
     gen_s = time.perf_counter() - t0
     net = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=16,
               nx_max=512, ny_max=128, gemm_bf16=True)
     net.set_params(network_pack(network_weights(32, 64, 4, 16, 8, seed=0, outputs=3), 4))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = ws.train(net, [(ptr[:768][k1], n1[k1]), (ptr[768:][k2], n2[k2])], steps=6000, lr=2e-3)
+    data = [(ptr[:768][k1], n1[k1]), (ptr[768:][k2], n2[k2])]
+    if k3.sum() >= 16:
+        data.append((pwv[k3], n3[k3]))
+    hist = ws.train(net, data, steps=6000, lr=2e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # network throughput on one training batch (256x64, 16 fields), device time
@@ -538,8 +545,11 @@ def run_warmstart(args):
     S = 256 * 64
     flop_fwd = 16 * S * (4 * (2 * 32 * 32 * 2 + 2 * 32 * 32) + 2 * 64 * 32 + 2 * 3 * 64)
     results = {}
-    for (nx, ny, n, block, cap) in ((512, 128, 16, 500, 40000), (2048, 512, 16, 5000, 1500000)):
-        pte = ws.sample_params(n, seed=99 if nx == 512 else 123)
+    for (name, nx, ny, n, block, cap, regime, seed) in (
+            ("512x128", 512, 128, 16, 500, 40000, "steady", 99),
+            ("2048x512", 2048, 512, 16, 5000, 1500000, "steady", 123),
+            ("1024x256_wave", 1024, 256, 16, 5000, 600000, "wave", 77)):
+        pte = ws.sample_params(n, seed=seed, regime=regime)
         big = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=1,
                   nx_max=nx, ny_max=ny, gemm_bf16=True)
         big.set_params(net.get_params())
@@ -554,21 +564,28 @@ def run_warmstart(args):
         t0 = time.perf_counter()
         s_pred = ws.steps_to_steady(pte, nx, ny, pred, seed=7, block=block, max_steps=cap)
         pred_s = time.perf_counter() - t0
-        results[f"{nx}x{ny}"] = {
-            "lattices": n, "steps_noise": s_noise.tolist(), "steps_warm": s_pred.tolist(),
-            "mean_steps_noise": float(s_noise.mean()), "mean_steps_warm": float(s_pred.mean()),
+        settled = (s_noise <= cap) & (s_pred <= cap)
+        results[name] = {
+            "lattices": n, "regime": regime, "cap": cap, "steps_noise": s_noise.tolist(),
+            "steps_warm": s_pred.tolist(), "mean_steps_noise": float(s_noise.mean()),
+            "mean_steps_warm": float(s_pred.mean()),
             "step_ratio": round(float(s_pred.mean() / s_noise.mean()), 3),
+            "settled_both": int(settled.sum()),
+            "step_ratio_settled": (round(float(s_pred[settled].mean() / s_noise[settled].mean()), 3)
+                                   if settled.any() else None),
             "wall_s_noise": round(noise_s, 2), "wall_s_warm": round(pred_s + infer_s, 2),
             "inference_s": round(infer_s, 3)}
     net.close()
-    r = results["512x128"]
+    r = results["2048x512"]
     peak, peak_kind = measured_peaks("bf16_tflops")
     achieved = 3 * flop_fwd / (step_ms * 1e-3) / 1e12
     line = {
         "metric": "steps_to_steady_ratio", "value": r["step_ratio"], "unit": "warm/noisy",
         "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (network GEMMs bf16)", "data": "synthetic (solver-generated)",
-        "config": {"workload": "warm_start_512x128_and_2048x512", "train_fields": int(k1.sum() + k2.sum()),
+        "config": {"workload": "warm_start_2048x512", "train_fields": int(sum(len(d[0]) for d in data)),
+                   "train_wave_fields": int(k3.sum()) if k3.sum() >= 16 else 0,
+                   "wave_draws_moving": int(m3.sum()), "wave_draws_settled": int(k3.sum()),
                    "train_steps": 6000, "data_gen_s": round(gen_s, 1), "train_s": round(train_s, 1),
                    "final_loss": hist[-1][1], "steady_tol_per_1000_steps": ws.STEADY_TOL},
         "results": results,

@@ -10,7 +10,11 @@ it leads to is the solver's.
 
 Steady state (the criterion used throughout): the maximum change of the
 density and of the velocity over 1000 steps is below STEADY_TOL, measured
-every `block` steps.
+every `block` steps, in the frame that moves with the pattern: the fields
+are compared after the periodic shift along x that best overlays them, so
+a travelling interface wave that keeps its shape counts as settled.  The
+training targets of travelling states are phase-aligned: shifted along x
+so that the dominant x-mode of the column masses has zero phase.
 
 The network predicts density and velocity (three output channels, scaled
 as (n - 1)/0.5, u_x/0.05, u_y/0.05).  A predicted density is shifted to the
@@ -32,13 +36,15 @@ SCALES = (0.5, 0.05, 0.05) # network outputs (n - 1) / 0.5, u_x / 0.05, u_y / 0.
 _NQ = {0.90: (0.3, 2.6), 0.95: (0.3, 2.0)}   # Table 1 rows used in this range
 
 
-def sample_params(n: int, seed: int) -> np.ndarray:
-    """Seeded draws (U_w, A0, lambda, T_r) in the regime where the solver
-    settles into a steady striped state: U_w ~ U[0, 0.05], A0 ~ U[3e-4,
-    1e-3], lambda 32 or 64, T_r ~ U[0.925, 0.96]."""
+def sample_params(n: int, seed: int, regime: str = "steady") -> np.ndarray:
+    """Seeded draws (U_w, A0, lambda, T_r): A0 ~ U[3e-4, 1e-3], lambda 32 or
+    64, T_r ~ U[0.925, 0.96], and U_w ~ U[0, 0.035] in the "steady" regime,
+    where the solver settles into a static striped state (at 2048 x 512 draws
+    with U_w >= 0.04 had not settled after 1.5 M steps), U_w ~ U[0.04, 0.06]
+    in the "wave" regime, where the interfaces keep moving."""
     rng = np.random.default_rng(seed)
     out = np.empty((n, 4))
-    out[:, 0] = rng.uniform(0.0, 0.05, n)
+    out[:, 0] = rng.uniform(0.0, 0.035, n) if regime == "steady" else rng.uniform(0.04, 0.06, n)
     out[:, 1] = rng.uniform(3e-4, 1e-3, n)
     out[:, 2] = np.where(rng.integers(0, 2, n) == 0, 32.0, 64.0)
     out[:, 3] = rng.uniform(0.925, 0.96, n)
@@ -66,10 +72,52 @@ def _fields(b):
     return [np.stack(v.moments(np.float32)) for v in b]   # [3][ny][nx]: n, u_x, u_y
 
 
+def shift_x(f: np.ndarray, d: float) -> np.ndarray:
+    """Fields [..][nx] moved by d sites towards -x (out(x) = f(x + d)),
+    periodic, by the Fourier shift theorem."""
+    nx = f.shape[-1]
+    k = np.arange(nx // 2 + 1)
+    return np.fft.irfft(np.fft.rfft(f, axis=-1) * np.exp(2j * np.pi * k * d / nx), n=nx, axis=-1)
+
+
+def comoving_change(cur: np.ndarray, prev: np.ndarray):
+    """Largest change between two field sets [3][ny][nx] (n, u_x, u_y) in
+    the frame of the pattern: the displacement d along x that maximises the
+    overlap of the two densities (periodic cross-correlation, refined to a
+    fraction of a site by a parabola through its peak), then the change
+    after moving `cur` back by d; the smaller of that and the plain change,
+    with d."""
+    plain = float(np.abs(cur - prev).max())
+    nx = cur.shape[-1]
+    a = cur[0] - cur[0].mean()
+    b = prev[0] - prev[0].mean()
+    corr = np.fft.irfft((np.fft.rfft(a, axis=1) * np.conj(np.fft.rfft(b, axis=1))).sum(axis=0), n=nx)
+    j = int(np.argmax(corr))
+    cm, c0, cp = corr[(j - 1) % nx], corr[j], corr[(j + 1) % nx]
+    den = cm - 2.0 * c0 + cp
+    d = j + (0.5 * (cm - cp) / den if den < 0.0 else 0.0)
+    if d > nx / 2:
+        d -= nx
+    moved = float(np.abs(shift_x(cur, d) - prev).max())
+    return min(plain, moved), float(d)
+
+
+def phase_aligned(f: np.ndarray) -> np.ndarray:
+    """Fields [3][ny][nx] shifted along x so that the dominant non-zero
+    x-mode of the column masses sum_y n has zero phase."""
+    m = f[0].sum(axis=0)
+    sp = np.fft.rfft(m - m.mean())
+    k = int(np.argmax(np.abs(sp[1:])) + 1)
+    return shift_x(f, -np.angle(sp[k]) * f.shape[-1] / (2.0 * np.pi * k))
+
+
 def generate(params: np.ndarray, nx: int, ny: int, steps: int, seed: int):
     """Run the solver from noisy uniform states for `steps` steps; returns
-    the final fields [n][3][ny][nx] (density, u_x, u_y; float32) and each
-    lattice's maximum change of them over its last 1000 steps."""
+    the final fields [n][3][ny][nx] (density, u_x, u_y; float32), each
+    lattice's change of them over its last 1000 steps in the pattern's
+    frame, and whether the pattern moved (by more than a quarter site over
+    those steps while its plain change exceeded the tolerance).  The fields
+    of moving patterns are phase-aligned."""
     ws = [workload(p, nx, ny, seed * 100003 + i) for i, p in enumerate(params)]
     b = _batch(ws)
     for v, w in zip(b, ws):
@@ -78,9 +126,16 @@ def generate(params: np.ndarray, nx: int, ny: int, steps: int, seed: int):
     prev = _fields(b)
     b.step(1000)
     cur = _fields(b)
-    delta = np.array([float(np.abs(c - q).max()) for c, q in zip(cur, prev)])
     b.close()
-    return np.stack(cur), delta
+    delta, moving = [], []
+    for i, (c, q) in enumerate(zip(cur, prev)):
+        ch, d = comoving_change(c, q)
+        mv = abs(d) > 0.25 and float(np.abs(c - q).max()) > STEADY_TOL
+        delta.append(ch)
+        moving.append(mv)
+        if mv:
+            cur[i] = phase_aligned(c).astype(np.float32)
+    return np.stack(cur), np.array(delta), np.array(moving)
 
 
 def mass_projected(pred: np.ndarray, rho_mean: float = 1.0) -> np.ndarray:
@@ -113,7 +168,7 @@ def steps_to_steady(params: np.ndarray, nx: int, ny: int, init=None, seed: int =
         t += block
         cur = _fields(b)
         for i in range(len(ws)):
-            if done[i] > max_steps and np.abs(cur[i] - prev[i]).max() * (1000.0 / block) < STEADY_TOL:
+            if done[i] > max_steps and comoving_change(cur[i], prev[i])[0] * (1000.0 / block) < STEADY_TOL:
                 done[i] = t
         prev = cur
     b.close()

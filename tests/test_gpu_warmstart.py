@@ -30,8 +30,8 @@ def test_warm_start_shortens_the_run_to_steady_state():
     from paper_1307_6703_gb300 import warmstart as ws
     from paper_1307_6703_gb300.fno import Fno
     ptr = ws.sample_params(512, seed=1)
-    n1, d1 = ws.generate(ptr[:384], 256, 64, 25000, seed=1)
-    n2, d2 = ws.generate(ptr[384:], 512, 128, 30000, seed=2)
+    n1, d1, _ = ws.generate(ptr[:384], 256, 64, 25000, seed=1)
+    n2, d2, _ = ws.generate(ptr[384:], 512, 128, 30000, seed=2)
     k1, k2 = d1 <= ws.STEADY_TOL, d2 <= ws.STEADY_TOL
     assert k1.mean() > 0.9 and k2.mean() > 0.6  # the training states are steady
     net = Fno(width=32, hidden=64, layers=4, modes_x=16, modes_y=8, outputs=3, batch_max=16,
