@@ -55,7 +55,9 @@ typedef struct fno_handle fno_handle;
 /* Allocate the network (parameters zeroed), its gradients, Adam moments and
  * the activation workspace for batch_max fields of nx_max x ny_max.
  * Errors: LB_ERR_ARG (sizes: modes_x <= nx_max/2, modes_y even and
- * <= ny_max), LB_ERR_CUDA, LB_ERR_OOM.                                     */
+ * <= ny_max, modes_x * modes_y <= 512, and the per-mode mixing's shared
+ * memory 4 (4 batch_max width + 2 width^2) bytes at most 48 KB),
+ * LB_ERR_CUDA, LB_ERR_OOM.                                                  */
 int fno_create(const fno_config *cfg, fno_handle **out);
 
 /* Number of FP32 parameters (the vector described above). */

@@ -131,65 +131,126 @@ __global__ void lift_kernel(const float *__restrict__ x0, const float *__restric
   }
 }
 
-// y-transform of the x-transformed lines: A[bc][y][j] (j < mx real part,
-// j >= mx imaginary part of mode j - mx) -> Sh[bc][ky][kx][2].
-__global__ void ydft_kernel(const float *__restrict__ A, const float2 *__restrict__ Ty, int ny, int mx, int my,
-                            float *__restrict__ Sh) {
-  const int bc = blockIdx.x;
+// Spectral kernels.  Rows of the x-transformed lines hold the mx kept
+// modes as (real parts, then imaginary parts): X[bc][y][j], j < mx real and
+// j >= mx imaginary part of mode j - mx; mode sets are [bc][ky][kx][2].
+// Ty[ky][y] = (cos theta, sin theta) with theta = 2 pi ky' y / ny.  Rows are
+// processed in chunks of kYChunk staged in shared memory with the chunk's
+// twiddles; sums run over y in order.
+constexpr int kYChunk = 64;
+
+// y-transform: S[bc][ky][kx] = sum_y (X_r + i X_i)[y][kx] e^{-i theta}.
+// One block per line set bc; dynamic shared memory (kYChunk (2 mx + 2 my))
+// floats.
+__global__ void __launch_bounds__(kThreads)
+ydft_kernel(const float *__restrict__ A, const float2 *__restrict__ Ty, int ny, int mx, int my,
+            float *__restrict__ Sh) {
+  extern __shared__ float ysm[];
+  float *xs = ysm;                                              // [kYChunk][2 mx]
+  float2 *ts = reinterpret_cast<float2 *>(ysm + kYChunk * 2 * mx);  // [my][kYChunk]
+  const int bc = blockIdx.x, t = threadIdx.x, M = my * mx;
   const float *a = A + (long long)bc * ny * 2 * mx;
-  for (int t = threadIdx.x; t < my * mx; t += blockDim.x) {
-    const int k = t / mx, kx = t - k * mx;
-    float sr = 0.f, si = 0.f;
-    for (int y = 0; y < ny; y++) {
-      const float2 tw = Ty[k * ny + y];
-      const float cs = tw.x, sn = tw.y;
-      const float ar = a[y * 2 * mx + kx], ai = a[y * 2 * mx + mx + kx];
-      sr += ar * cs + ai * sn;
-      si += ai * cs - ar * sn;
+  float sr[2] = {0.f, 0.f}, si[2] = {0.f, 0.f};  // outputs t and t + kThreads
+  for (int y0 = 0; y0 < ny; y0 += kYChunk) {
+    const int yc = min(kYChunk, ny - y0);
+    __syncthreads();
+    for (int e = t; e < yc * 2 * mx; e += kThreads) xs[e] = a[(long long)y0 * 2 * mx + e];
+    for (int e = t; e < my * yc; e += kThreads) {
+      const int k = e / yc, y = e - k * yc;
+      ts[k * kYChunk + y] = Ty[k * ny + y0 + y];
     }
-    float *o = Sh + (((long long)bc * my + k) * mx + kx) * 2;
-    o[0] = sr;
-    o[1] = si;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int o = t + q * kThreads;
+      if (o < M) {
+        const int k = o / mx, kx = o - k * mx;
+        float r = sr[q], im = si[q];
+        for (int y = 0; y < yc; y++) {
+          const float2 tw = ts[k * kYChunk + y];
+          const float ar = xs[y * 2 * mx + kx], ai = xs[y * 2 * mx + mx + kx];
+          r += ar * tw.x + ai * tw.y;
+          im += ai * tw.x - ar * tw.y;
+        }
+        sr[q] = r;
+        si[q] = im;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int o = t + q * kThreads;
+    if (o < M) {
+      float *d = Sh + ((long long)bc * M + o) * 2;
+      d[0] = sr[q];
+      d[1] = si[q];
+    }
   }
 }
 
-// Per-mode complex channel mixing, then the inverse y-transform:
-// Y[o, ky] = sum_c S[c, ky] R[ky, kx, c, o];  G[o][y][kx] = sum_ky Y e^{+i theta}.
-// One block per (kx, b); shared memory: Y[C][my][2].
-__global__ void mix_iy_kernel(const float *__restrict__ Sh, const float *__restrict__ Rr, const float *__restrict__ Ri,
-                              const float2 *__restrict__ Ty, int C, int ny, int mx, int my, float *__restrict__ G,
-                              __nv_bfloat16 *__restrict__ Gb) {
+// Inverse y-transform (and the adjoint of the y-transform, which has the
+// same form): X[bc][y][kx] = sum_ky Y[bc][ky][kx] e^{+i theta}, written as
+// (real, imaginary) rows with a BF16 copy.  One block per line set;
+// dynamic shared memory (2 my mx + 2 my kYChunk) floats.
+__global__ void __launch_bounds__(kThreads)
+iy_kernel(const float *__restrict__ Y, const float2 *__restrict__ Ty, int ny, int mx, int my, float *__restrict__ X,
+          __nv_bfloat16 *__restrict__ Xb) {
   extern __shared__ float ysm[];
-  const int kx = blockIdx.x, b = blockIdx.y;
-  for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
-    const int o = t / my, k = t - o * my;
-    float yr = 0.f, yi = 0.f;
-    const long long rbase = ((long long)(k * mx + kx) * C) * C + o;
-    for (int c = 0; c < C; c++) {
-      const float *s = Sh + ((((long long)b * C + c) * my + k) * mx + kx) * 2;
-      const float rr = Rr[rbase + (long long)c * C], ri = Ri[rbase + (long long)c * C];
-      yr += s[0] * rr - s[1] * ri;
-      yi += s[0] * ri + s[1] * rr;
+  float *ys = ysm;                                              // [my][mx][2]
+  float2 *ts = reinterpret_cast<float2 *>(ysm + 2 * my * mx);   // [my][kYChunk]
+  const int bc = blockIdx.x, t = threadIdx.x;
+  for (int e = t; e < 2 * my * mx; e += kThreads) ys[e] = Y[(long long)bc * 2 * my * mx + e];
+  for (int y0 = 0; y0 < ny; y0 += kYChunk) {
+    const int yc = min(kYChunk, ny - y0);
+    __syncthreads();
+    for (int e = t; e < my * yc; e += kThreads) {
+      const int k = e / yc, y = e - k * yc;
+      ts[k * kYChunk + y] = Ty[k * ny + y0 + y];
     }
-    ysm[(o * my + k) * 2] = yr;
-    ysm[(o * my + k) * 2 + 1] = yi;
+    __syncthreads();
+    for (int e = t; e < yc * mx; e += kThreads) {
+      const int y = e / mx, kx = e - y * mx;
+      float gr = 0.f, gi = 0.f;
+      for (int k = 0; k < my; k++) {
+        const float2 tw = ts[k * kYChunk + y];
+        const float yr = ys[(k * mx + kx) * 2], yi = ys[(k * mx + kx) * 2 + 1];
+        gr += yr * tw.x - yi * tw.y;
+        gi += yr * tw.y + yi * tw.x;
+      }
+      const long long g = ((long long)bc * ny + y0 + y) * 2 * mx;
+      X[g + kx] = gr;
+      X[g + mx + kx] = gi;
+      Xb[g + kx] = __float2bfloat16_rn(gr);
+      Xb[g + mx + kx] = __float2bfloat16_rn(gi);
+    }
   }
+}
+
+// Per-mode complex channel mixing: Y[b][o][m] = sum_c S[b][c][m] R[m][c][o]
+// (m = ky mx + kx; R as real and imaginary planes [m][c][o]).  One block per
+// mode; dynamic shared memory (2 B C + 2 C C) floats.
+__global__ void __launch_bounds__(kThreads)
+mix_kernel(const float *__restrict__ Sh, const float *__restrict__ Rr, const float *__restrict__ Ri, int B, int C,
+           int M, float *__restrict__ Y) {
+  extern __shared__ float msm[];
+  float2 *ss = reinterpret_cast<float2 *>(msm);          // [B][C]
+  float2 *rs = reinterpret_cast<float2 *>(msm + 2 * B * C);  // [C][C]
+  const int m = blockIdx.x, t = threadIdx.x;
+  const float2 *S2 = reinterpret_cast<const float2 *>(Sh);
+  for (int e = t; e < B * C; e += kThreads) ss[e] = S2[(long long)e * M + m];
+  for (int e = t; e < C * C; e += kThreads)
+    rs[e] = make_float2(Rr[(long long)m * C * C + e], Ri[(long long)m * C * C + e]);
   __syncthreads();
-  for (int t = threadIdx.x; t < C * ny; t += blockDim.x) {
-    const int o = t / ny, y = t - o * ny;
-    float gr = 0.f, gi = 0.f;
-    for (int k = 0; k < my; k++) {
-      const float2 tw = Ty[k * ny + y];
-      const float cs = tw.x, sn = tw.y;
-      const float yr = ysm[(o * my + k) * 2], yi = ysm[(o * my + k) * 2 + 1];
-      gr += yr * cs - yi * sn;
-      gi += yr * sn + yi * cs;
+  float2 *Y2 = reinterpret_cast<float2 *>(Y);
+  for (int e = t; e < B * C; e += kThreads) {
+    const int b = e / C, o = e - b * C;
+    float yr = 0.f, yi = 0.f;
+    for (int c = 0; c < C; c++) {
+      const float2 sv = ss[b * C + c], rv = rs[c * C + o];
+      yr += sv.x * rv.x - sv.y * rv.y;
+      yi += sv.x * rv.y + sv.y * rv.x;
     }
-    const long long g = (((long long)b * C + o) * ny + y) * 2 * mx;
-    G[g + kx] = gr;
-    G[g + mx + kx] = gi;
-    Gb[g + kx] = __float2bfloat16_rn(gr);
-    Gb[g + mx + kx] = __float2bfloat16_rn(gi);
+    Y2[(long long)e * M + m] = make_float2(yr, yi);
   }
 }
 
@@ -448,87 +509,48 @@ __global__ void act_back_kernel(const float *__restrict__ dv, const float *__res
   }
 }
 
-// Adjoint of the inverse y-transform, then of the mode mixing (for the
-// inputs): dY[o, ky] = sum_y dG e^{-i theta} (adjoint form), dS[c, ky] =
-// sum_o (R^H-like products).  One block per (kx, b); dY kept for dR.
-__global__ void mix_iy_back_kernel(const float *__restrict__ dG, const float *__restrict__ Rr, const float *__restrict__ Ri,
-                                   const float2 *__restrict__ Ty, int C, int ny, int mx, int my, float *__restrict__ dY,
-                                   float *__restrict__ dS) {
-  extern __shared__ float ysm[];
-  const int kx = blockIdx.x, b = blockIdx.y;
-  for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
-    const int o = t / my, k = t - o * my;
-    const float *g = dG + (((long long)b * C + o) * ny) * 2 * mx;
-    float yr = 0.f, yi = 0.f;
-    for (int y = 0; y < ny; y++) {
-      const float2 tw = Ty[k * ny + y];
-      const float cs = tw.x, sn = tw.y;
-      const float gr = g[y * 2 * mx + kx], gi = g[y * 2 * mx + mx + kx];
-      yr += gr * cs + gi * sn;
-      yi += -gr * sn + gi * cs;
-    }
-    ysm[(o * my + k) * 2] = yr;
-    ysm[(o * my + k) * 2 + 1] = yi;
-    float *d = dY + ((((long long)b * C + o) * my + k) * mx + kx) * 2;
-    d[0] = yr;
-    d[1] = yi;
+// Adjoint of the mode mixing and the spectral weights' gradient, per mode m:
+// dS[b][c][m] = sum_o dY[b][o][m] conj(R[m][c][o]) and
+// dR[m][c][o] = sum_b conj(S[b][c][m]) dY[b][o][m] (real and imaginary
+// planes).  One block per mode; dynamic shared memory (4 B C + 2 C C) floats.
+__global__ void __launch_bounds__(kThreads)
+mix_back_kernel(const float *__restrict__ dY, const float *__restrict__ Sh, const float *__restrict__ Rr,
+                const float *__restrict__ Ri, int B, int C, int M, float *__restrict__ dS, float *__restrict__ dRr,
+                float *__restrict__ dRi) {
+  extern __shared__ float msm[];
+  float2 *ds = reinterpret_cast<float2 *>(msm);               // dY [B][C]
+  float2 *ss = reinterpret_cast<float2 *>(msm + 2 * B * C);   // S [B][C]
+  float2 *rs = reinterpret_cast<float2 *>(msm + 4 * B * C);   // R [C][C]
+  const int m = blockIdx.x, t = threadIdx.x;
+  const float2 *D2 = reinterpret_cast<const float2 *>(dY), *S2 = reinterpret_cast<const float2 *>(Sh);
+  for (int e = t; e < B * C; e += kThreads) {
+    ds[e] = D2[(long long)e * M + m];
+    ss[e] = S2[(long long)e * M + m];
   }
+  for (int e = t; e < C * C; e += kThreads)
+    rs[e] = make_float2(Rr[(long long)m * C * C + e], Ri[(long long)m * C * C + e]);
   __syncthreads();
-  for (int t = threadIdx.x; t < C * my; t += blockDim.x) {
-    const int c = t / my, k = t - c * my;
-    const long long rbase = ((long long)(k * mx + kx) * C + c) * C;
+  float2 *dS2 = reinterpret_cast<float2 *>(dS);
+  for (int e = t; e < B * C; e += kThreads) {
+    const int b = e / C, c = e - b * C;
     float sr = 0.f, si = 0.f;
     for (int o = 0; o < C; o++) {
-      const float yr = ysm[(o * my + k) * 2], yi = ysm[(o * my + k) * 2 + 1];
-      const float rr = Rr[rbase + o], ri = Ri[rbase + o];
-      sr += yr * rr + yi * ri;
-      si += -yr * ri + yi * rr;
+      const float2 yv = ds[b * C + o], rv = rs[c * C + o];
+      sr += yv.x * rv.x + yv.y * rv.y;
+      si += -yv.x * rv.y + yv.y * rv.x;
     }
-    float *d = dS + ((((long long)b * C + c) * my + k) * mx + kx) * 2;
-    d[0] = sr;
-    d[1] = si;
+    dS2[(long long)e * M + m] = make_float2(sr, si);
   }
-}
-
-// dR[m, c, o] = sum_b (S_r dY_r + S_i dY_i, -S_i dY_r + S_r dY_i): one block per mode.
-__global__ void dR_kernel(const float *__restrict__ Sh, const float *__restrict__ dY, int B, int C, int mx, int my,
-                          float *__restrict__ dRr, float *__restrict__ dRi) {
-  const int m = blockIdx.x;
-  const int k = m / mx, kx = m - k * mx;
-  for (int t = threadIdx.x; t < C * C; t += blockDim.x) {
-    const int c = t / C, o = t - c * C;
+  for (int e = t; e < C * C; e += kThreads) {
+    const int c = e / C, o = e - c * C;
     float ar = 0.f, ai = 0.f;
     for (int b = 0; b < B; b++) {
-      const float *s = Sh + ((((long long)b * C + c) * my + k) * mx + kx) * 2;
-      const float *d = dY + ((((long long)b * C + o) * my + k) * mx + kx) * 2;
-      ar += s[0] * d[0] + s[1] * d[1];
-      ai += -s[1] * d[0] + s[0] * d[1];
+      const float2 sv = ss[b * C + c], dv = ds[b * C + o];
+      ar += sv.x * dv.x + sv.y * dv.y;
+      ai += -sv.y * dv.x + sv.x * dv.y;
     }
-    dRr[((long long)m * C + c) * C + o] = ar;
-    dRi[((long long)m * C + c) * C + o] = ai;
-  }
-}
-
-// Adjoint of the y-transform: dA[bc][y][kx] (re / im parts) from dS.
-__global__ void ydft_back_kernel(const float *__restrict__ dS, const float2 *__restrict__ Ty, int ny, int mx, int my,
-                                 float *__restrict__ dA, __nv_bfloat16 *__restrict__ dAb) {
-  const int bc = blockIdx.x;
-  const float *d = dS + (long long)bc * my * mx * 2;
-  for (int t = threadIdx.x; t < ny * mx; t += blockDim.x) {
-    const int y = t / mx, kx = t - y * mx;
-    float ar = 0.f, ai = 0.f;
-    for (int k = 0; k < my; k++) {
-      const float2 tw = Ty[k * ny + y];
-      const float cs = tw.x, sn = tw.y;
-      const float sr = d[(k * mx + kx) * 2], si = d[(k * mx + kx) * 2 + 1];
-      ar += sr * cs - si * sn;
-      ai += sr * sn + si * cs;
-    }
-    const long long a = ((long long)bc * ny + y) * 2 * mx;
-    dA[a + kx] = ar;
-    dA[a + mx + kx] = ai;
-    dAb[a + kx] = __float2bfloat16_rn(ar);
-    dAb[a + mx + kx] = __float2bfloat16_rn(ai);
+    dRr[(long long)m * C * C + e] = ar;
+    dRi[(long long)m * C * C + e] = ai;
   }
 }
 
@@ -742,6 +764,11 @@ cudaError_t sg(fno_handle *h, const float *A, long long am, long long ak, long l
 }
 
 // Site-major copy of a [B][rows][S] BF16 activation: out[b][s][row].
+// Dynamic shared memory of the spectral kernels (bytes).
+size_t ydft_smem(int mx, int my) { return (size_t)kYChunk * (2 * mx + 2 * my) * sizeof(float); }
+size_t iy_smem(int mx, int my) { return (size_t)(2 * my * mx + 2 * my * kYChunk) * sizeof(float); }
+size_t mix_smem(int B, int C, bool back) { return (size_t)((back ? 4 : 2) * B * C + 2 * C * C) * sizeof(float); }
+
 void site_major(fno_handle *h, const __nv_bfloat16 *in, int B, int rows, long long S, __nv_bfloat16 *out) {
   const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((S + 63) / 64), (unsigned)B);
   if (rows % 32 == 0 && S % 8 == 0)
@@ -867,8 +894,10 @@ int fno_create(const fno_config *cfg, fno_handle **out) {
   const fno_config &c = *cfg;
   if (c.width < 1 || c.hidden < 1 || c.layers < 1 || c.layers > kMaxLayers || c.modes_x < 1 || c.modes_y < 2 ||
       c.modes_y % 2 != 0 || c.batch_max < 1 || c.nx_max < 2 || c.ny_max < 2 || 2 * c.modes_x > c.nx_max ||
-      c.modes_y > c.ny_max || c.width * c.modes_y * 2 * (int)sizeof(float) > 48 * 1024 || c.outputs < 1 ||
-      c.outputs > kMaxOutputs)
+      c.modes_y > c.ny_max || c.outputs < 1 || c.outputs > kMaxOutputs ||
+      c.modes_x * c.modes_y > 2 * kThreads ||  // ydft_kernel: two modes per thread
+      std::max(ydft_smem(c.modes_x, c.modes_y), std::max(iy_smem(c.modes_x, c.modes_y),
+                                                            mix_smem(c.batch_max, c.width, true))) > 48 * 1024)
     return ffail(nullptr, LB_ERR_ARG, "fno_create: bad sizes");
   if (c.gemm_bf16 && (c.width % 8 || c.hidden % 8 || (2 * c.modes_x) % 8))
     return ffail(nullptr, LB_ERR_ARG, "fno_create: BF16 tensor-core products need width, hidden and 2 modes_x "
@@ -957,9 +986,11 @@ int fno_forward(fno_handle *h, int32_t B, int32_t nx, int32_t ny, const float *p
       FNO_GEMM(h, tcg(h, h->Vb[l], nx, 0, h->FxTb, nx, 0, h->A, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 1, 0.f));
     else
       FNO_GEMM(h, sg(h, h->V[l], nx, 1, 0, h->Fx, 2 * mx, 1, 0, h->A, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 0.f));
-    ydft_kernel<<<B * C, kThreads, 0, st>>>(h->A, h->Ty, ny, mx, my, h->Sh[l]);
-    mix_iy_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->Sh[l], P + h->o.Rr[l], P + h->o.Ri[l], h->Ty,
-                                                                          C, ny, mx, my, h->G, h->Gb);
+    // y-transform, per-mode mixing (into the dY scratch), inverse y-transform
+    ydft_kernel<<<B * C, kThreads, ydft_smem(mx, my), st>>>(h->A, h->Ty, ny, mx, my, h->Sh[l]);
+    mix_kernel<<<my * mx, kThreads, mix_smem(B, C, false), st>>>(h->Sh[l], P + h->o.Rr[l], P + h->o.Ri[l], B, C,
+                                                                   my * mx, h->dY);
+    iy_kernel<<<B * C, kThreads, iy_smem(mx, my), st>>>(h->dY, h->Ty, ny, mx, my, h->G, h->Gb);
     FNO_CUDA(h, cudaGetLastError());
     // inverse x-transform into z: Z[R, nx] = G[R, 2mx] Fxi[2mx, nx]
     if (bf)
@@ -1049,10 +1080,12 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
       FNO_GEMM(h, tcg(h, h->dZb, nx, 0, h->Fxib, nx, 0, h->dG, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 1, 0.f));
     else
       FNO_GEMM(h, sg(h, h->dZ, nx, 1, 0, h->Fxi, 1, nx, 0, h->dG, 2 * mx, 1, 0, R, 2 * mx, nx, 1, 0.f));
-    mix_iy_back_kernel<<<dim3(mx, B), kThreads, C * my * 2 * sizeof(float), st>>>(h->dG, P + o.Rr[l], P + o.Ri[l], h->Ty, C, ny,
-                                                                               mx, my, h->dY, h->dS);
-    dR_kernel<<<my * mx, kThreads, 0, st>>>(h->Sh[l], h->dY, B, C, mx, my, g + o.Rr[l], g + o.Ri[l]);
-    ydft_back_kernel<<<B * C, kThreads, 0, st>>>(h->dS, h->Ty, ny, mx, my, h->dA, h->dAb);
+    // adjoints: of the inverse y-transform (a y-transform), of the mixing
+    // (with the weights' gradient), of the y-transform (an inverse one)
+    ydft_kernel<<<B * C, kThreads, ydft_smem(mx, my), st>>>(h->dG, h->Ty, ny, mx, my, h->dY);
+    mix_back_kernel<<<my * mx, kThreads, mix_smem(B, C, true), st>>>(h->dY, h->Sh[l], P + o.Rr[l], P + o.Ri[l], B, C,
+                                                                       my * mx, h->dS, g + o.Rr[l], g + o.Ri[l]);
+    iy_kernel<<<B * C, kThreads, iy_smem(mx, my), st>>>(h->dS, h->Ty, ny, mx, my, h->dA, h->dAb);
     FNO_CUDA(h, cudaGetLastError());
     // dv = W^T dz (pointwise path) + dA Fx^T (spectral path)
     if (bf) {
