@@ -200,23 +200,38 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
   return false;
 }
 
-__device__ __forceinline__ void tma_box(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad, int ypad) {
+__device__ __forceinline__ void tma_box(const CUtensorMap *map, uint32_t dst, uint32_t bar, int xpad, int ypad,
+                                        uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(xpad), "r"(ypad), "r"(0), "r"(bar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(xpad), "r"(ypad), "r"(0), "r"(bar), "l"(policy)
       : "memory");
 }
+
+// L2 policies for the population boxes.  A tile's first four pairs (its
+// 4-row warm-up and first 4 rows) are the rows the segment below reads last,
+// about one tile-duration later: they are kept (evict-last) so that read
+// comes from L2; the tile's other rows get the normal policy.
+__device__ __forceinline__ uint64_t l2_policy(bool keep) {
+  uint64_t p;
+  if (keep)
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+constexpr int kKeepPairs = 4;
 
 // Two rows (all nine planes, the window's columns) of the padded state into
 // a ring slot, completing on the slot's mbarrier.
 template <class St>
 __device__ __forceinline__ void tma_pair(const CUtensorMap *m0, const CUtensorMap *m1, uint32_t dst, uint32_t bar,
-                                         int xpad, int ypad) {
+                                         int xpad, int ypad, uint64_t policy) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(St::kTxBytes)
                : "memory");
-  tma_box(m0, dst, bar, xpad, ypad);
-  if constexpr (St::kDev) tma_box(m1, dst + St::kDevOffset, bar, xpad, ypad);
+  tma_box(m0, dst, bar, xpad, ypad, policy);
+  if constexpr (St::kDev) tma_box(m1, dst + St::kDevOffset, bar, xpad, ypad, policy);
 }
 
 __device__ __forceinline__ int dec(int s, int n) { return s == 0 ? n - 1 : s - 1; }
@@ -492,7 +507,8 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
   int issued = min(kPairs, npairs);  // pairs requested so far (thread 0's count)
   if (t == 0) {
     for (int P = 0; P < issued; ++P)
-      tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P);
+      tma_pair<St>(tin, tdev, smem_u32(S.pops[P]), smem_u32(&S.full[P]), x0, ya + 2 * P,
+                   l2_policy(P < kKeepPairs));
   }
   __syncthreads();
   if (!mbar_wait(smem_u32(&S.full[0]), 0, A.err)) S.abort = 1;
@@ -519,7 +535,8 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
       __syncthreads();
       if (t == 0 && k - 3 + kPairs < npairs) {
         const int slot = dec(s5m2, kPairs);
-        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k - 3 + kPairs));
+        tma_pair<St>(tin, tdev, smem_u32(S.pops[slot]), smem_u32(&S.full[slot]), x0, ya + 2 * (k - 3 + kPairs),
+                     l2_policy(k - 3 + kPairs < kKeepPairs));
         ++issued;
       }
     }
