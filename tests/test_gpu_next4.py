@@ -7,6 +7,9 @@
 * The broken-line velocity profile of a sheared two-layer fluid: the two
   slopes of <u_x>_x(y) against the uniform shear-stress prediction (the
   paper's formula, for the interface where it settles), within 5 %.
+* Table 2's L_x scan: the interface amplitude rises with L_x and the wave
+  travels from L_x = 1024 on (the amplitudes themselves are smaller than
+  the paper's, and L_x = 256 ends in a flat slab).
 """
 import numpy as np
 import pytest
