@@ -120,6 +120,8 @@ int lb_create(const lb_params *p, lb_handle **out);
  *          (Steele, Lea & Flood 2014); u0 = 0.  rho0/ux0/uy0 are ignored.
  *  mode 1: n0 = rho0[ny][nx] (HOST pointer, double, required); ux0 and uy0
  *          (HOST, double, [ny][nx]) may each be NULL for zero velocity.
+ *          Page-locked arrays are read by the init kernel in place;
+ *          pageable ones are first copied to a device buffer.
  * Resets the step counter to 0.  Synchronises the stream when host arrays
  * are read.  Errors: LB_ERR_ARG, LB_ERR_CUDA.                             */
 int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean,
@@ -139,7 +141,8 @@ int lb_step(lb_handle *h, int64_t nsteps);
  * next step applied to the stored state, written to rho, ux, uy ([ny][nx],
  * element type `dtype`).  Any of the three may be NULL.  on_device = 1:
  * the pointers are device pointers and the call only enqueues work;
- * on_device = 0: host pointers, the call synchronises the stream.
+ * on_device = 0: host pointers, the call synchronises the stream (the
+ * kernel writes page-locked arrays in place; pageable ones receive a copy).
  * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA.                          */
 int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype,
                int on_device);

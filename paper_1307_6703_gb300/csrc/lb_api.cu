@@ -89,6 +89,31 @@ int cuda_fail(lb_handle *h, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
+// Device address of page-locked host memory (mapped into the device's
+// address space under unified addressing), or nullptr for pageable memory,
+// device memory and anything else.  Asked through the driver, so that the
+// runtime's last-error state is left as the caller had it.
+void *host_mapped(const void *p) {
+  typedef CUresult (*get_attr_fn)(void *, CUpointer_attribute, CUdeviceptr);
+  static get_attr_fn get = nullptr;
+  if (!p) return nullptr;
+  if (!get) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return nullptr;
+    get = (get_attr_fn)fn;
+  }
+  unsigned type = 0;
+  if (get(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, (CUdeviceptr)p) != CUDA_SUCCESS || type != CU_MEMORYTYPE_HOST)
+    return nullptr;
+  CUdeviceptr d = 0;
+  if (get(&d, CU_POINTER_ATTRIBUTE_DEVICE_POINTER, (CUdeviceptr)p) != CUDA_SUCCESS || !d) return nullptr;
+  return (void *)d;
+}
+
 template <typename real_t>
 StepArgs<real_t> make_args(const lb_handle *h) {
   const lb_params &p = h->p;
@@ -554,17 +579,20 @@ int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean, double noise
   const double *dr = nullptr, *du = nullptr, *dv = nullptr;
   if (mode == 1) {
     if (!rho0) return fail(h, LB_ERR_ARG, "lb_init: mode 1 needs rho0");
-    if (!h->d_fields) LB_CUDA(h, cudaMalloc((void **)&h->d_fields, 3 * h->S * sizeof(double)));
-    const size_t nb = h->S * sizeof(double);
-    LB_CUDA(h, cudaMemcpyAsync(h->d_fields, rho0, nb, cudaMemcpyHostToDevice, h->st));
-    dr = h->d_fields;
-    if (ux0) {
-      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + h->S, ux0, nb, cudaMemcpyHostToDevice, h->st));
-      du = h->d_fields + h->S;
-    }
-    if (uy0) {
-      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + 2 * h->S, uy0, nb, cudaMemcpyHostToDevice, h->st));
-      dv = h->d_fields + 2 * h->S;
+    // Page-locked fields are read by the init kernel where they are;
+    // pageable ones are staged in device memory first.
+    const double *src[3] = {rho0, ux0, uy0};
+    const double **dst[3] = {&dr, &du, &dv};
+    for (int k = 0; k < 3; ++k) {
+      if (!src[k]) continue;
+      if (void *m = host_mapped(src[k])) {
+        *dst[k] = (const double *)m;
+        continue;
+      }
+      if (!h->d_fields) LB_CUDA(h, cudaMalloc((void **)&h->d_fields, 3 * h->S * sizeof(double)));
+      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + k * h->S, src[k], h->S * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->st));
+      *dst[k] = h->d_fields + k * h->S;
     }
   }
   h->cur = 0;
@@ -652,12 +680,22 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_de
   if (!h->initialised) return fail(h, LB_ERR_STATE, "lb_moments: state not initialised");
   const size_t es = dtype == LB_DTYPE_F64 ? sizeof(double) : sizeof(float);
   void *dn = rho, *du = ux, *dv = uy;
+  bool staged[3] = {false, false, false};
   if (!on_device) {
-    if (!h->d_mom) LB_CUDA(h, cudaMalloc(&h->d_mom, 3 * h->S * sizeof(double)));
-    char *base = (char *)h->d_mom;
-    dn = rho ? base : nullptr;
-    du = ux ? base + h->S * es : nullptr;
-    dv = uy ? base + 2 * h->S * es : nullptr;
+    // The kernel writes page-locked host arrays directly; pageable ones
+    // get a device buffer and a copy.
+    void *const host[3] = {rho, ux, uy};
+    void **dst[3] = {&dn, &du, &dv};
+    for (int k = 0; k < 3; ++k) {
+      if (!host[k]) continue;
+      if (void *m = host_mapped(host[k])) {
+        *dst[k] = m;
+        continue;
+      }
+      if (!h->d_mom) LB_CUDA(h, cudaMalloc(&h->d_mom, 3 * h->S * sizeof(double)));
+      *dst[k] = (char *)h->d_mom + k * h->S * es;
+      staged[k] = true;
+    }
   }
   cudaError_t e;
   if (fp64(h)) {
@@ -670,9 +708,9 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_de
   if (e != cudaSuccess) return cuda_fail(h, e, "lb_moments: kernel");
   if (!on_device) {
     const size_t nb = h->S * es;
-    if (rho) LB_CUDA(h, cudaMemcpyAsync(rho, dn, nb, cudaMemcpyDeviceToHost, h->st));
-    if (ux) LB_CUDA(h, cudaMemcpyAsync(ux, du, nb, cudaMemcpyDeviceToHost, h->st));
-    if (uy) LB_CUDA(h, cudaMemcpyAsync(uy, dv, nb, cudaMemcpyDeviceToHost, h->st));
+    if (staged[0]) LB_CUDA(h, cudaMemcpyAsync(rho, dn, nb, cudaMemcpyDeviceToHost, h->st));
+    if (staged[1]) LB_CUDA(h, cudaMemcpyAsync(ux, du, nb, cudaMemcpyDeviceToHost, h->st));
+    if (staged[2]) LB_CUDA(h, cudaMemcpyAsync(uy, dv, nb, cudaMemcpyDeviceToHost, h->st));
     LB_CUDA(h, cudaStreamSynchronize(h->st));
   }
   return LB_OK;

@@ -346,31 +346,58 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-// f*_i = f_i^eq(n0, u0) evaluated in FP64, stored as real_t.
+// f*_i = f_i^eq(n0, u0) evaluated in FP64, stored as real_t.  Threads run
+// along x, blocks stride over rows (blockIdx.y); site s = y * nx + x is the
+// noise counter and the index into the host fields.  With zero velocity
+// (noise, or a density field alone) t1 = +-0 and t2 = +0 in feq9, so
+// f^eq_i = (w_i n) (1 + t3_i) with the same roundings: the three isotropic
+// factors 1 + t3 (rest, axes, diagonals) are evaluated once per thread by
+// the same expression and each site costs two FP64 products per link
+// class instead of feq9's divisions.
 template <typename real_t>
 __global__ void init_kernel(real_t *__restrict__ f, int nx, int ny, int pitch, long long plane,
                             long long off, int mode, uint64_t seed, double rho_mean, double amp,
                             const double *__restrict__ rho0, const double *__restrict__ ux0,
                             const double *__restrict__ uy0, double T) {
-  const size_t S = (size_t)nx * ny;
-  for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < S;
-       s += (size_t)gridDim.x * blockDim.x) {
-    double n0, u = 0.0, v = 0.0;
-    if (mode == 0) {
-      const double U = (double)(splitmix64_at(seed, (uint64_t)s) >> 11) * 0x1.0p-53;
-      n0 = rho_mean + amp * (2.0 * U - 1.0);
-    } else {
-      n0 = rho0[s];
-      if (ux0) u = ux0[s];
-      if (uy0) v = uy0[s];
-    }
-    double fe[9];
-    feq9<double>(n0, u, v, T, fe);
-    const long long y = (long long)(s / (size_t)nx), x = (long long)(s % (size_t)nx);
-    const long long e = off + y * pitch + x;
+  constexpr double T0 = Consts<double>::T0;
+  const bool at_rest = mode == 0 || (ux0 == nullptr && uy0 == nullptr);
+  double iso[3];
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i * plane + e] = (real_t)fe[i];
+  for (int c = 0; c < 3; c++) {
+    const double t3 = (T - T0) * (double(c) - 2.0 * T0) / (2.0 * T0 * T0);
+    iso[c] = 1.0 + t3;
   }
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+      const size_t s = (size_t)y * nx + x;
+      double n0, u = 0.0, v = 0.0;
+      if (mode == 0) {
+        const double U = (double)(splitmix64_at(seed, (uint64_t)s) >> 11) * 0x1.0p-53;
+        n0 = rho_mean + amp * (2.0 * U - 1.0);
+      } else {
+        n0 = rho0[s];
+        if (ux0) u = ux0[s];
+        if (uy0) v = uy0[s];
+      }
+      double fe[9];
+      if (at_rest) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) fe[i] = Consts<double>::w(i) * n0 * iso[cx(i) * cx(i) + cy(i) * cy(i)];
+      } else {
+        feq9<double>(n0, u, v, T, fe);
+      }
+      const long long e = off + (long long)y * pitch + x;
+#pragma unroll
+      for (int i = 0; i < 9; i++) f[i * plane + e] = (real_t)fe[i];
+    }
+  }
+}
+
+// Grid of init_kernel: 256-thread blocks along x; up to 256 row blocks, so
+// that a thread sets several rows.
+inline dim3 init_grid(int nx, int ny) {
+  const unsigned bx = (unsigned)((nx + 255) / 256);
+  return dim3(bx < 64u ? bx : 64u, (unsigned)(ny < 256 ? ny : 256));
 }
 
 }  // namespace lbk

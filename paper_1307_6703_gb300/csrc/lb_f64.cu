@@ -30,9 +30,7 @@ cudaError_t launch_moments(const double *fin, const StepArgs<double> &A, void *n
 cudaError_t launch_init(double *f, int nx, int ny, int pitch, long long plane, long long off, int mode, uint64_t seed, double rho_mean,
                         double amp, const double *rho0, const double *ux0, const double *uy0,
                         double T, cudaStream_t st) {
-  const size_t S = (size_t)nx * ny;
-  const unsigned blocks = (unsigned)((S + 255) / 256 < 4096 ? (S + 255) / 256 : 4096);
-  init_kernel<double><<<blocks, 256, 0, st>>>(f, nx, ny, pitch, plane, off, mode, seed, rho_mean, amp, rho0, ux0, uy0, T);
+  init_kernel<double><<<init_grid(nx, ny), 256, 0, st>>>(f, nx, ny, pitch, plane, off, mode, seed, rho_mean, amp, rho0, ux0, uy0, T);
   return cudaGetLastError();
 }
 

@@ -448,10 +448,14 @@ struct StepIO {
 // stopped at its next barrier and drained the copies still in flight).
 // kPersist: called once per tile by the multi-step kernel, which does not
 // hand its SM slots to a dependent grid early.
-template <class St, bool kPersist = false>
+struct NoDone {
+  __device__ void operator()() const {}
+};
+
+template <class St, bool kPersist = false, class Done = NoDone>
 __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtensorMap *tdev, const SweepArgs &A,
                                            const StepIO &O, const int strip, const int seg, double *rec,
-                                           const bool records) {
+                                           const bool records, const Done &done = Done{}) {
   using Row = typename St::Row;
   using Smem = SweepSmem<St::kSlotBytes>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -886,6 +890,10 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
   }
   // The next step may be scheduled now (it waits for this grid to finish).
   if constexpr (!kPersist) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // Every thread is here: the tile's stores are done.  A persistent caller
+  // publishes its completion now -- the records below touch only this CTA's
+  // shared memory and the record slots, so dependent tiles need not wait.
+  done();
 
   // CTA partial sums of the stored state (FP64, fixed order), when asked
   // for.  Every TMA copy has been waited for, so the population ring is
@@ -1115,9 +1123,8 @@ sweep_batch_persist_kernel(const BatchItem *__restrict__ items, const SweepArgs 
     first = false;
     const StepIO O{A.fout, A.fdev, A.partials, 0u, nullptr, nullptr, nullptr, 0.0};
     if (!sweep_body<St, true>(m, m + 1, A, O, it.strip, it.seg, A.partials + 4 * (size_t)it.rec,
-                              k == P.nsteps - 1))
+                              k == P.nsteps - 1, [&] { release_item(P, i, target + 1u); }))
       return;
-    release_item(P, i, target + 1u);
   }
 }
 
@@ -1167,33 +1174,11 @@ sweep_multi_kernel(const __grid_constant__ CUtensorMap tin0, const __grid_consta
     O.monitor = mon ? Q.mon_ring + 6 * ((Q.mon_step0 + k) % Q.mon_cap) : nullptr;
     O.mon_step = (double)(Q.mon_step0 + k);
     if (!sweep_body<St, true>(par ? &tin1 : &tin0, par ? &tdev1 : &tdev0, A, O, i % A.nstrips, i / A.nstrips,
-                              const_cast<double *>(O.recs) + 4 * (size_t)i, last || mon)) {
+                              const_cast<double *>(O.recs) + 4 * (size_t)i, last || mon,
+                              [&] { release_item(P, i, target + 1u); })) {
       if (t == 0) Q.total[4] = 1.0;
       return;
     }
-    release_item(P, i, target + 1u);
-  }
-}
-
-// Copy the periodic images into the ghost band of nplanes padded planes.
-template <typename E>
-__global__ void ghost_fill_kernel(E *f, int nplanes, int nx, int ny, int pitch, long long plane, long long off,
-                                  int walls) {
-  const int rows = ny + 8;
-  const long long total = (long long)nplanes * rows * pitch;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(k / ((long long)rows * pitch));
-    const long long rem = k - (long long)q * rows * pitch;
-    const int py = (int)(rem / pitch), px = (int)(rem % pitch);
-    const int y = py - 4, x = px - 4;
-    if (x >= nx + 4) continue;
-    const bool gxb = (x < 0 || x >= nx), gyb = (y < 0 || y >= ny);
-    if (!gxb && !gyb) continue;
-    if (gyb && walls) continue;
-    const int sx = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-    const int sy = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    f[q * plane + off + (long long)y * pitch + x] = f[q * plane + off + (long long)sy * pitch + sx];
   }
 }
 
@@ -1525,18 +1510,6 @@ void sweep_deps(int store, int nx, int ny, int walls, int nstrips, int base_w, i
     idx.insert(idx.end(), deps[a].begin(), deps[a].end());
     ofs[a + 1] = (int)idx.size();
   }
-}
-
-cudaError_t launch_ghost_fill(void *f, int elem_bytes, int nplanes, int nx, int ny, int pitch, long long plane,
-                              long long off, int walls, cudaStream_t st) {
-  const unsigned blocks = elementwise_blocks((long long)nplanes * (ny + 8) * pitch);
-  if (elem_bytes == 4)
-    ghost_fill_kernel<uint32_t><<<blocks, 256, 0, st>>>((uint32_t *)f, nplanes, nx, ny, pitch, plane, off, walls);
-  else if (elem_bytes == 2)
-    ghost_fill_kernel<uint16_t><<<blocks, 256, 0, st>>>((uint16_t *)f, nplanes, nx, ny, pitch, plane, off, walls);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
 }
 
 cudaError_t launch_widen(int store, const void *buf, float *wide, long long plane, float ref_ax, float ref_dg,

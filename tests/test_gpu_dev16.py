@@ -129,6 +129,33 @@ def test_dev16_full_size_one_step(prec, fmt):
     assert frac <= 1e-2
 
 
+@pytest.mark.parametrize("prec,fmt", FORMATS)
+def test_dev16_full_size_bench_launches(prec, fmt):
+    """The benchmark's launch sequence with 16-bit storage on 4096x1024
+    (autotuned tiling, a 5-step launch, then one persistent 20-step launch)
+    against the full-precision oracle and the oracle that rounds its state
+    to the format every step: the GPU's density error is within twice the
+    format's own, and its distance from the exact-format run is a small
+    fraction of that."""
+    w = C4
+    n0 = noise_field(w)
+    s = dev16_solver(w, prec, RHO_REF).init_fields(n0)
+    seg_h = s.autotune(20)
+    s.step(5)
+    s.step(20)
+    n = s.moments()[0]
+    rc, _ = s.reduce()
+    s.close()
+    exact = oracle_for(w).init_fields(n0).quantize(fmt, RHO_REF).step(25, storage=(fmt, RHO_REF))
+    full = oracle_for(w).init_fields(n0).step(25)
+    ne, nf = exact.moments()[0], full.moments()[0]
+    gpu_err, fmt_err, gpu_exact = rel_err(n, nf), rel_err(ne, nf), rel_err(n, ne)
+    print(f"4096x1024 {fmt}, seg_h {seg_h}, 5 + 20 steps: GPU vs full {gpu_err:.3e}, format vs full "
+          f"{fmt_err:.3e}, GPU vs exact format {gpu_exact:.3e}")
+    assert rc == 0
+    assert gpu_err <= 2.0 * fmt_err + 1e-6
+
+
 DAMPED = {
     # supercritical sheared fluid relaxing to Couette flow
     "couette": (dict(nx=128, ny=48, T=1.1 * TC, A0=0.0, lam=0.0, u_bot=-0.05, u_top=0.05),

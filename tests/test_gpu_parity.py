@@ -248,6 +248,65 @@ def test_full_size_fp32_one_step():
     s.close()
 
 
+def test_full_size_bench_launches_against_oracle():
+    """The benchmark's own launch sequence on 4096x1024: device noise init,
+    the autotuner's tiling, a 5-step warm-up launch, then one persistent
+    20-step launch; every site's populations and density against 25 oracle
+    steps, at the FP32 tolerance of 1e-5."""
+    w = C4
+    s = solver_for(w, LB_FP32).init_noise(w.seed, w.rho_mean, w.noise)
+    seg_h = s.autotune(20)
+    s.step(5)
+    s.step(20)
+    ref = oracle_for(w).init_noise(w.seed, w.rho_mean, w.noise).step(25)
+    e_f = rel_err(s.get_state(), ref.f)
+    n, ux, uy = s.moments()
+    rn, rux, ruy = ref.moments()
+    e_n = rel_err(n, rn)
+    e_u = max(float(np.abs(ux - rux).max()), float(np.abs(uy - ruy).max()))
+    rc, _ = s.reduce()
+    s.close()
+    print(f"4096x1024, seg_h {seg_h}, 5 + 20 steps: populations {e_f:.2e}, density {e_n:.2e}, "
+          f"velocity {e_u:.2e} (absolute)")
+    assert rc == 0
+    assert e_f <= 1e-5 and e_n <= 1e-5
+    # u = (sum_i f_i c_i + F / 2) / n: six populations enter each component,
+    # so at the population tolerance (1e-5 of max f ~ 0.5) and n ~ 0.5 the
+    # velocity error is at most ~6e-5 in lattice units
+    assert e_u <= 6e-5
+
+
+def test_page_locked_and_pageable_host_arrays_agree():
+    """lb_init reads page-locked host fields in place and stages pageable
+    ones; lb_moments writes page-locked host arrays from the kernel and
+    copies into pageable ones: both routes give the same bits."""
+    import torch
+    from paper_1307_6703_gb300 import LB_DTYPE_F32, lb_init, lb_moments
+    w = C2(0.05)
+    n0 = noise_field(w, seed=5)
+    u0 = 0.01 * np.sin(2 * np.pi * np.arange(w.nx) / w.nx)[None, :] * np.ones((w.ny, 1))
+    v0 = np.zeros_like(n0)
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in (n0, u0, v0)]
+    out = []
+    for fields in ((n0, u0, v0), tuple(p.numpy() for p in pinned), (n0, None, None),
+                   (pinned[0].numpy(), None, None)):
+        s = solver_for(w, LB_FP32)
+        if fields[1] is None:
+            lb_init(s.h, 1, 0, 0.0, 0.0, fields[0], None, None)
+        else:
+            lb_init(s.h, 1, 0, 0.0, 0.0, *fields)
+        s.step(7)
+        host = np.empty((3, w.ny, w.nx), np.float32)
+        lb_moments(s.h, host[0], host[1], host[2], LB_DTYPE_F32, 0)
+        locked = torch.empty((3, w.ny, w.nx), dtype=torch.float32).pin_memory()
+        lb_moments(s.h, locked[0].data_ptr(), locked[1].data_ptr(), locked[2].data_ptr(), LB_DTYPE_F32, 0)
+        assert np.array_equal(host, locked.numpy())
+        out.append((s.get_state(), host))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[2][0], out[3][0]) and np.array_equal(out[2][1], out[3][1])
+
+
 def test_full_size_fp64_one_step_bitwise():
     w = C4
     ref = oracle_for(w).init_noise(3, w.rho_mean, w.noise).step(1)
