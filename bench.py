@@ -36,7 +36,8 @@ B_ALG = {"fp32": 72.0, "bf16dev": 40.0, "fp16dev": 40.0}
 KERNEL_SRC = os.path.join(ROOT, "paper_1307_6703_gb300", "csrc", "lb_sweep.cu")
 PROFILE = {"fp32": os.path.join(ROOT, "profiles", "lb_step_sweep_fp32_4096x1024.md"),
            "bf16dev": os.path.join(ROOT, "profiles", "lb_step_sweep_bf16dev_4096x1024.md"),
-           "fp16dev": os.path.join(ROOT, "profiles", "lb_step_sweep_fp16dev_4096x1024.md")}
+           "fp16dev": os.path.join(ROOT, "profiles", "lb_step_sweep_fp16dev_4096x1024.md"),
+           "batch:fp32": os.path.join(ROOT, "profiles", "lb_batch_sweep_fp32_ensemble64.md")}
 
 
 # The workload's physics: the mixed-precision 4096x1024 configuration of the
@@ -78,7 +79,7 @@ def profiled_traffic(precision: str, steps_per_launch: int):
     try:
         with open(PROFILE[precision]) as fh:
             text = fh.read()
-    except OSError:
+    except (KeyError, OSError):
         return None, "no committed ncu summary"
     digest, per_step, basis = None, None, None
     for line in text.splitlines():
@@ -461,6 +462,8 @@ def run_batch(args):
     launches = 1
     kernel = "lbk::sweep_batch_kernel" if args.steps == 1 else "lbk::sweep_batch_persist_kernel"
     achieved = b_alg * sites * (args.steps // launches) / (t_ms * 1e-3 / launches) / 1e9
+    traffic, traffic_basis = (profiled_traffic("batch:" + args.precision, args.steps // launches)
+                              if args.steps > 1 else (None, "single-step launches are not profiled"))
     if rank == 0:
         line = {
             "metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
@@ -472,8 +475,8 @@ def run_batch(args):
                        "sites": sites, "seg_h": segs, "unstable_instances": unstable,
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "traffic_basis": "not captured for the ensemble",
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "traffic_basis": traffic_basis,
                          "peak_kind": peak_kind, "kernel": kernel, "steps_per_launch": args.steps // launches,
                          "bytes_per_site": b_alg},
             "one_by_one": {"value": round(seq, 1), "unit": "MLUPS", "steps": k_seq,
