@@ -558,7 +558,7 @@ def run_warmstart(args):
         big.set_params(net.get_params())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pred = np.concatenate([ws.mass_projected(ws.predict(big, pte[i:i + 1], nx, ny)) for i in range(n)])
+        pred = torch.cat([ws.predict(big, pte[i:i + 1], nx, ny) for i in range(n)])
         infer_s = time.perf_counter() - t0
         big.close()
         t0 = time.perf_counter()

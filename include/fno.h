@@ -83,6 +83,21 @@ int fno_backward(fno_handle *h, const float *target, double *loss);
  * (t = 1, 2, ... is the step number for the bias corrections).            */
 int fno_adam(fno_handle *h, float lr, float beta1, float beta2, float eps, int32_t t);
 
+/* Initial fields of the solver (lb_init, mode 1) from the network output,
+ * on the device.  For each of `batch` fields out[b] ([outputs][ny][nx]
+ * FP32, DEVICE, outputs >= 3, the layout of fno_forward): density
+ * n = 1 + s0 out[b][0] + c_b with the constant c_b that makes its mean over
+ * the nx ny sites rho_mean (the solver conserves mass, so a prediction must
+ * carry the mass of the state it replaces), u_x = s1 out[b][1],
+ * u_y = s2 out[b][2], written to fields[b][3][ny][nx] (FP64, DEVICE: rho0,
+ * ux0, uy0 of lb_init at fields + 3 b nx ny, + nx ny, + 2 nx ny).
+ * scales = (s0, s1, s2), a HOST array.  FP64 arithmetic, each operation
+ * rounded once; the mean is a fixed-order sum.  Enqueued on the handle's
+ * stream.  Errors: LB_ERR_ARG (null pointers, batch outside 1..65535,
+ * fewer than 3 outputs), LB_ERR_CUDA.                                      */
+int fno_fields(fno_handle *h, const float *out, int32_t batch, int32_t nx, int32_t ny, const double *scales,
+               double rho_mean, double *fields);
+
 int fno_destroy(fno_handle *h);
 const char *fno_last_error(const fno_handle *h);
 

@@ -118,10 +118,12 @@ int lb_create(const lb_params *p, lb_handle **out);
  *          U in [0,1) is the top 53 bits of output y*nx + x of the
  *          counter-based SplitMix64 generator seeded with `seed`
  *          (Steele, Lea & Flood 2014); u0 = 0.  rho0/ux0/uy0 are ignored.
- *  mode 1: n0 = rho0[ny][nx] (HOST pointer, double, required); ux0 and uy0
- *          (HOST, double, [ny][nx]) may each be NULL for zero velocity.
- *          Page-locked arrays are read by the init kernel in place;
- *          pageable ones are first copied to a device buffer.
+ *  mode 1: n0 = rho0[ny][nx] (double, required); ux0 and uy0 (double,
+ *          [ny][nx]) may each be NULL for zero velocity.  Host arrays
+ *          (pageable or page-locked) or arrays in the handle's device
+ *          memory: page-locked and device arrays are read by the init
+ *          kernel in place, pageable ones are first copied to a device
+ *          buffer.
  * Resets the step counter to 0.  Synchronises the stream when host arrays
  * are read.  Errors: LB_ERR_ARG, LB_ERR_CUDA.                             */
 int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean,

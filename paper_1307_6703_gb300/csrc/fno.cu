@@ -16,6 +16,7 @@
 // Activation layout: [batch][channel][ny][nx] (x fastest).  A "row" of the
 // x-transform is one (batch, channel, y) line, so the x-transform of all
 // channels of all fields is a single GEMM [B*C*ny, nx] x [nx, 2*mx].
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -318,6 +319,42 @@ __global__ void finish_loss_kernel(const double *__restrict__ partial, int n, lo
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
   const double r = block_sum(acc, sm);
   if (threadIdx.x == 0) *loss = r / (double)total;
+}
+
+// Initial fields of the solver from the network output (fno_fields):
+// per field b, block j: FP64 sum of the density d = 1 + s0 o0 over the
+// block's sites (grid-strided, then the fixed-order block tree).
+__global__ void field_mass_kernel(const float *__restrict__ out, int outputs, long long S, double s0,
+                                  double *__restrict__ part) {
+  __shared__ double sm[kThreads];
+  const float *o = out + (size_t)blockIdx.y * outputs * S;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < S; e += (long long)gridDim.x * blockDim.x)
+    acc += __dadd_rn(__dmul_rn(s0, (double)o[e]), 1.0);
+  const double r = block_sum(acc, sm);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
+}
+
+// fields[b] = (d + (rho_mean - mean d), s1 o1, s2 o2); the mean from the
+// nblk block sums of field b in a fixed order.
+__global__ void fields_kernel(const float *__restrict__ out, int outputs, long long S, double s0, double s1,
+                              double s2, double rho_mean, const double *__restrict__ part, int nblk,
+                              double *__restrict__ fields) {
+  __shared__ double shift;
+  const int b = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int j = 0; j < nblk; ++j) m += part[(size_t)b * nblk + j];
+    shift = rho_mean - m / (double)S;
+  }
+  __syncthreads();
+  const float *o = out + (size_t)b * outputs * S;
+  double *f = fields + (size_t)b * 3 * S;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < S; e += (long long)gridDim.x * blockDim.x) {
+    f[e] = __dadd_rn(__dadd_rn(__dmul_rn(s0, (double)o[e]), 1.0), shift);
+    f[S + e] = __dmul_rn(s1, (double)o[S + e]);
+    f[2 * S + e] = __dmul_rn(s2, (double)o[2 * S + e]);
+  }
 }
 
 // dhp[b, h, s] = sum_j Q2[j, h] dout[b, j, s] gelu'(hp[b, h, s])
@@ -1108,6 +1145,22 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
     FNO_CUDA(h, cudaStreamSynchronize(st));
     if (gerr) return ffail(h, LB_ERR_TIMEOUT, "fno_backward: a tensor-core product's bounded wait gave up");
   }
+  return LB_OK;
+}
+
+int fno_fields(fno_handle *h, const float *out, int32_t batch, int32_t nx, int32_t ny, const double *scales,
+               double rho_mean, double *fields) {
+  if (!h || !out || !scales || !fields) return ffail(h, LB_ERR_ARG, "fno_fields: null argument");
+  if (batch < 1 || batch > 65535 || nx < 1 || ny < 1 || h->c.outputs < 3)
+    return ffail(h, LB_ERR_ARG, "fno_fields: batch, lattice or output channels out of range");
+  const long long S = (long long)nx * ny;
+  // block sums in the loss partials (8192 doubles; the same stream orders
+  // their uses)
+  const int nblk = (int)std::max<long long>(1, std::min<long long>({256, 8192 / batch, (S + kThreads - 1) / kThreads}));
+  field_mass_kernel<<<dim3(nblk, batch), kThreads, 0, h->st>>>(out, h->c.outputs, S, scales[0], h->partial);
+  fields_kernel<<<dim3(nblk, batch), kThreads, 0, h->st>>>(out, h->c.outputs, S, scales[0], scales[1], scales[2],
+                                                           rho_mean, h->partial, nblk, fields);
+  FNO_CUDA(h, cudaGetLastError());
   return LB_OK;
 }
 

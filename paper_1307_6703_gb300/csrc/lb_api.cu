@@ -89,11 +89,13 @@ int cuda_fail(lb_handle *h, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
-// Device address of page-locked host memory (mapped into the device's
-// address space under unified addressing), or nullptr for pageable memory,
-// device memory and anything else.  Asked through the driver, so that the
-// runtime's last-error state is left as the caller had it.
-void *host_mapped(const void *p) {
+// Address under which the current device's kernels can read and write p:
+// page-locked host memory (mapped into the device's address space under
+// unified addressing) or memory of the current device itself; nullptr for
+// pageable memory, another device's memory and anything else.  Asked
+// through the driver, so that the runtime's last-error state is left as
+// the caller had it.
+void *device_view(const void *p) {
   typedef CUresult (*get_attr_fn)(void *, CUpointer_attribute, CUdeviceptr);
   static get_attr_fn get = nullptr;
   if (!p) return nullptr;
@@ -107,8 +109,15 @@ void *host_mapped(const void *p) {
     get = (get_attr_fn)fn;
   }
   unsigned type = 0;
-  if (get(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, (CUdeviceptr)p) != CUDA_SUCCESS || type != CU_MEMORYTYPE_HOST)
-    return nullptr;
+  if (get(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, (CUdeviceptr)p) != CUDA_SUCCESS) return nullptr;
+  if (type == CU_MEMORYTYPE_DEVICE) {
+    int ord = -1, cur = -2;
+    if (get(&ord, CU_POINTER_ATTRIBUTE_DEVICE_ORDINAL, (CUdeviceptr)p) != CUDA_SUCCESS ||
+        cudaGetDevice(&cur) != cudaSuccess || ord != cur)
+      return nullptr;
+    return const_cast<void *>(p);
+  }
+  if (type != CU_MEMORYTYPE_HOST) return nullptr;
   CUdeviceptr d = 0;
   if (get(&d, CU_POINTER_ATTRIBUTE_DEVICE_POINTER, (CUdeviceptr)p) != CUDA_SUCCESS || !d) return nullptr;
   return (void *)d;
@@ -579,19 +588,18 @@ int lb_init(lb_handle *h, int mode, uint64_t seed, double rho_mean, double noise
   const double *dr = nullptr, *du = nullptr, *dv = nullptr;
   if (mode == 1) {
     if (!rho0) return fail(h, LB_ERR_ARG, "lb_init: mode 1 needs rho0");
-    // Page-locked fields are read by the init kernel where they are;
-    // pageable ones are staged in device memory first.
+    // Page-locked host fields and fields in this device's memory are read
+    // by the init kernel where they are; others are staged first.
     const double *src[3] = {rho0, ux0, uy0};
     const double **dst[3] = {&dr, &du, &dv};
     for (int k = 0; k < 3; ++k) {
       if (!src[k]) continue;
-      if (void *m = host_mapped(src[k])) {
+      if (void *m = device_view(src[k])) {
         *dst[k] = (const double *)m;
         continue;
       }
       if (!h->d_fields) LB_CUDA(h, cudaMalloc((void **)&h->d_fields, 3 * h->S * sizeof(double)));
-      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + k * h->S, src[k], h->S * sizeof(double), cudaMemcpyHostToDevice,
-                                 h->st));
+      LB_CUDA(h, cudaMemcpyAsync(h->d_fields + k * h->S, src[k], h->S * sizeof(double), cudaMemcpyDefault, h->st));
       *dst[k] = h->d_fields + k * h->S;
     }
   }
@@ -682,13 +690,13 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_de
   void *dn = rho, *du = ux, *dv = uy;
   bool staged[3] = {false, false, false};
   if (!on_device) {
-    // The kernel writes page-locked host arrays directly; pageable ones
-    // get a device buffer and a copy.
+    // The kernel writes page-locked host arrays (and this device's memory)
+    // directly; pageable ones get a device buffer and a copy.
     void *const host[3] = {rho, ux, uy};
     void **dst[3] = {&dn, &du, &dv};
     for (int k = 0; k < 3; ++k) {
       if (!host[k]) continue;
-      if (void *m = host_mapped(host[k])) {
+      if (void *m = device_view(host[k])) {
         *dst[k] = m;
         continue;
       }
@@ -708,9 +716,9 @@ int lb_moments(lb_handle *h, void *rho, void *ux, void *uy, int dtype, int on_de
   if (e != cudaSuccess) return cuda_fail(h, e, "lb_moments: kernel");
   if (!on_device) {
     const size_t nb = h->S * es;
-    if (staged[0]) LB_CUDA(h, cudaMemcpyAsync(rho, dn, nb, cudaMemcpyDeviceToHost, h->st));
-    if (staged[1]) LB_CUDA(h, cudaMemcpyAsync(ux, du, nb, cudaMemcpyDeviceToHost, h->st));
-    if (staged[2]) LB_CUDA(h, cudaMemcpyAsync(uy, dv, nb, cudaMemcpyDeviceToHost, h->st));
+    if (staged[0]) LB_CUDA(h, cudaMemcpyAsync(rho, dn, nb, cudaMemcpyDefault, h->st));
+    if (staged[1]) LB_CUDA(h, cudaMemcpyAsync(ux, du, nb, cudaMemcpyDefault, h->st));
+    if (staged[2]) LB_CUDA(h, cudaMemcpyAsync(uy, dv, nb, cudaMemcpyDefault, h->st));
     LB_CUDA(h, cudaStreamSynchronize(h->st));
   }
   return LB_OK;

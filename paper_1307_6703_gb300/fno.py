@@ -37,6 +37,7 @@ def _lib():
         lib.fno_forward.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P]
         lib.fno_backward.argtypes = [P, P, C.POINTER(C.c_double)]
         lib.fno_adam.argtypes = [P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32]
+        lib.fno_fields.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_double, P]
         lib.fno_destroy.argtypes = [P]
         lib.fno_last_error.argtypes = [P]
         lib.fno_last_error.restype = C.c_char_p
@@ -45,7 +46,7 @@ def _lib():
                                       C.c_float, P, P]
         lib.fno_gemm_bf16.restype = C.c_int
         for n in ("fno_create", "fno_set_params", "fno_get_params", "fno_get_grads", "fno_forward",
-                  "fno_backward", "fno_adam", "fno_destroy"):
+                  "fno_backward", "fno_adam", "fno_fields", "fno_destroy"):
             getattr(lib, n).restype = C.c_int
         _ready = True
     return lib
@@ -115,6 +116,11 @@ class Fno:
         self.t += 1
         _check(_lib().fno_adam(self.h, lr, beta1, beta2, eps, self.t), self.h)
 
+    def fields(self, out, nx: int, ny: int, scales, rho_mean: float, fields) -> None:
+        """Solver fields [B][3][ny][nx] (device float64) from the network
+        output `out` (device [B][outputs][ny][nx]); see fno_fields."""
+        fno_fields(self.h, out, out.shape[0], nx, ny, scales, rho_mean, fields)
+
     def close(self):
         if self.h:
             _lib().fno_destroy(self.h)
@@ -157,6 +163,11 @@ def fno_backward(h, target) -> float:
 
 def fno_adam(h, lr: float, beta1: float, beta2: float, eps: float, t: int):
     _check(_lib().fno_adam(h, lr, beta1, beta2, eps, t), h)
+
+
+def fno_fields(h, out, batch: int, nx: int, ny: int, scales, rho_mean: float, fields):
+    sc = (C.c_double * 3)(*[float(v) for v in scales])
+    _check(_lib().fno_fields(h, _ptr(out), batch, nx, ny, sc, rho_mean, _ptr(fields)), h)
 
 
 def fno_destroy(h):

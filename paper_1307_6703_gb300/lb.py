@@ -132,6 +132,8 @@ def lb_init(h, mode: int, seed: int = 0, rho_mean: float = 0.0, noise_amp: float
     for a in (rho0, ux0, uy0):
         if isinstance(a, np.ndarray):
             assert a.dtype == np.float64 and a.flags.c_contiguous
+        elif hasattr(a, "data_ptr"):
+            assert str(a.dtype) == "torch.float64" and a.is_contiguous()
     return _check(load_library().lb_init(h, mode, seed, rho_mean, noise_amp, _addr(rho0),
                                          _addr(ux0), _addr(uy0)), h)
 
@@ -295,7 +297,12 @@ class Solver:
         return self
 
     def init_fields(self, rho0, ux0=None, uy0=None):
-        c = (lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64))
+        """Host arrays (converted to contiguous float64) or contiguous
+        float64 device tensors, which lb_init reads in place."""
+        def c(a):
+            if a is None or hasattr(a, "data_ptr"):
+                return a
+            return np.ascontiguousarray(a, dtype=np.float64)
         lb_init(self.h, 1, 0, 0.0, 0.0, c(rho0), c(ux0), c(uy0))
         return self
 

@@ -138,14 +138,6 @@ def generate(params: np.ndarray, nx: int, ny: int, steps: int, seed: int):
     return np.stack(cur), np.array(delta), np.array(moving)
 
 
-def mass_projected(pred: np.ndarray, rho_mean: float = 1.0) -> np.ndarray:
-    """Predicted fields [n][3][ny][nx] with each density shifted to the mean
-    rho_mean (the mass of the noisy uniform state)."""
-    out = np.array(pred, dtype=np.float64, copy=True)
-    out[:, 0] += rho_mean - out[:, 0].mean(axis=(1, 2), keepdims=True)
-    return out
-
-
 def steps_to_steady(params: np.ndarray, nx: int, ny: int, init=None, seed: int = 0,
                     block: int = 500, max_steps: int = 40000) -> np.ndarray:
     """Steps until each lattice is steady (STEADY_TOL), from the given
@@ -158,7 +150,7 @@ def steps_to_steady(params: np.ndarray, nx: int, ny: int, init=None, seed: int =
         if init is None:
             v.init_fields(_noise(w))
         else:
-            f = np.asarray(init[i], dtype=np.float64)
+            f = init[i] if hasattr(init, "data_ptr") else np.asarray(init[i], dtype=np.float64)
             v.init_fields(f[0], f[1], f[2])
     prev = _fields(b)
     done = np.full(len(ws), max_steps + block)
@@ -211,14 +203,16 @@ def train(net, datasets, steps: int, lr: float = 2e-3, batch: int = 16, seed: in
     return hist
 
 
-def predict(net, params: np.ndarray, nx: int, ny: int) -> np.ndarray:
-    """Predicted steady fields [n][3][ny][nx] (density, u_x, u_y; float64)."""
+def predict(net, params: np.ndarray, nx: int, ny: int, rho_mean: float = 1.0):
+    """Initial fields [n][3][ny][nx] (density, u_x, u_y; float64, on the
+    device) for the solver: the network's prediction rescaled and with each
+    density shifted to the mean rho_mean, the mass of the noisy uniform
+    state it replaces (fno_fields).  Ready for lb_init when it returns."""
     import torch
     prm = torch.tensor(np.asarray(params, dtype=np.float32), device="cuda")
-    out = torch.empty((prm.shape[0], 3, ny, nx), dtype=torch.float32, device="cuda")
+    out = torch.empty((prm.shape[0], net.outputs, ny, nx), dtype=torch.float32, device="cuda")
     net.forward(prm, nx, ny, out)
-    f = out.cpu().numpy().astype(np.float64)
-    for j, sc in enumerate(SCALES):
-        f[:, j] *= sc
-    f[:, 0] += 1.0
-    return f
+    fields = torch.empty((prm.shape[0], 3, ny, nx), dtype=torch.float64, device="cuda")
+    net.fields(out, nx, ny, SCALES, rho_mean, fields)
+    torch.cuda.synchronize()
+    return fields

@@ -40,8 +40,20 @@ def test_warm_start_shortens_the_run_to_steady_state():
     hist = ws.train(net, [(ptr[:384][k1], n1[k1]), (ptr[384:][k2], n2[k2])], steps=3000, lr=2e-3)
     assert hist[-1][1] < 0.2 * hist[0][1] and hist[-1][1] < 1e-2
     pte = ws.sample_params(16, seed=99)
-    pred = ws.mass_projected(ws.predict(net, pte, 512, 128))
-    assert np.allclose(pred[:, 0].mean(axis=(1, 2)), 1.0, atol=1e-12)
+    pred = ws.predict(net, pte, 512, 128)
+    # the device-side rescale and mass projection against the same steps in
+    # numpy on the network's raw output
+    import torch
+    raw = torch.empty((16, 3, 128, 512), dtype=torch.float32, device="cuda")
+    net.forward(torch.tensor(pte, dtype=torch.float32, device="cuda"), 512, 128, raw)
+    ref = raw.cpu().numpy().astype(np.float64)
+    for j, sc in enumerate(ws.SCALES):
+        ref[:, j] *= sc
+    ref[:, 0] += 1.0
+    ref[:, 0] += 1.0 - ref[:, 0].mean(axis=(1, 2), keepdims=True)
+    got = pred.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13
+    assert np.allclose(got[:, 0].mean(axis=(1, 2)), 1.0, atol=1e-12)
     s_noise = ws.steps_to_steady(pte, 512, 128, None, seed=7)
     s_pred = ws.steps_to_steady(pte, 512, 128, pred, seed=7)
     net.close()
