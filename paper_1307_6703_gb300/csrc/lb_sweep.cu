@@ -76,16 +76,18 @@ namespace lbk {
 
 namespace {
 
-constexpr int kCols = 124;                  // window width (columns x0-4 .. x0+119)
 constexpr int kPairs = 5;                   // population ring, in pairs of rows
-constexpr int kThreads = kCols;             // one thread per window column
 constexpr int kSeg = 64;                    // rows per segment
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 constexpr int round128(int b) { return ((b + 127) / 128) * 128; }
 
 // FP32 storage: one 3D box {kCols, 2, 9} (columns, rows, planes) per pair.
+// A CTA has one thread per window column (kCols threads): the window is
+// the strip plus 4 halo columns on each side.  124 columns keep four CTAs'
+// shared memory within an SM.
 struct StoreF32 {
+  static constexpr int kCols = 124;           // columns x0-4 .. x0+119
   static constexpr bool kDev = false;
   static constexpr int kQuantum = 4;          // 16-byte x coordinates of float boxes
   static constexpr int kMaxW = kCols - 8;     // 116
@@ -102,11 +104,13 @@ struct StoreF32 {
 
 // 16-bit deviation storage: a float box {kCols, 2, 1} of the rest plane and a
 // 16-bit box {128, 2, 8} of the deviation planes (256-byte rows) per pair.
+// The window is 128 columns (four full warps): five CTAs per SM still fit.
 template <class H>
 struct StoreDev {
+  static constexpr int kCols = 128;           // columns x0-4 .. x0+123
   static constexpr bool kDev = true;
   static constexpr int kQuantum = 8;          // 16-byte x coordinates of 16-bit boxes
-  static constexpr int kMaxW = 112;
+  static constexpr int kMaxW = kCols - 8;     // 120
   static constexpr int kDevCols = 128;
   static constexpr int kRestBytes = 2 * kCols * sizeof(float);
   static constexpr int kDevOffset = round128(kRestBytes);
@@ -152,7 +156,7 @@ using StoreFP16 = StoreDev<__half>;
 // ya - 5, chosen so that iteration k writes pair k of every ring.  Each
 // ring is long enough that no stage overwrites a slot another thread may
 // still read without a barrier in between.
-template <int SlotBytes>
+template <int SlotBytes, int kCols>
 struct __align__(128) SweepSmem {
   unsigned char pops[kPairs][SlotBytes];  // one row pair of every plane per slot
   // four pairs: stage A of iteration k+1 writes pair k+1 into a slot that
@@ -163,10 +167,13 @@ struct __align__(128) SweepSmem {
   unsigned long long full[kPairs];
   int abort;  // set by a thread whose copy wait gave up; read after a barrier
   static_assert(SlotBytes % 128 == 0, "TMA destinations must be 128-byte aligned");
-  static_assert(kPairs * SlotBytes >= (int)(sizeof(double) * 4 * kThreads + sizeof(unsigned)),
+  static_assert(kPairs * SlotBytes >= (int)(sizeof(double) * 4 * kCols + sizeof(unsigned)),
                 "the end-of-kernel reduction reuses the population ring");
 };
-static_assert(offsetof(SweepSmem<StoreF32::kSlotBytes>, pops) == 0, "the ring starts the (128-byte aligned) block");
+template <class St>
+using SmemOf = SweepSmem<St::kSlotBytes, St::kCols>;
+static_assert(offsetof(SmemOf<StoreF32>, pops) == 0 && offsetof(SmemOf<StoreBF16>, pops) == 0,
+              "the ring starts the (128-byte aligned) block");
 static_assert(StoreBF16::kDevOffset % 128 == 0, "16-bit boxes must land on 128-byte boundaries");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -457,7 +464,7 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
                                            const StepIO &O, const int strip, const int seg, double *rec,
                                            const bool records, const Done &done = Done{}) {
   using Row = typename St::Row;
-  using Smem = SweepSmem<St::kSlotBytes>;
+  using Smem = SmemOf<St>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem &S = *reinterpret_cast<Smem *>(smem_raw);
 
@@ -478,6 +485,7 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
   // neighbours stay inside the window) and store ring values at column t:
   // the columns an inactive thread writes are never read by the next
   // stage's active threads, so only the global stores need a guard.
+  constexpr int kCols = St::kCols, kThreads = St::kCols;
   const int tcl = min(max(t, 1), kCols - 2);
   const int kmax = (yb - ya + 5) >> 1;  // last iteration
   const int npairs = kmax + 2;          // rows ya-4 .. ya+2*kmax+3
@@ -980,7 +988,7 @@ __device__ __forceinline__ bool sweep_body(const CUtensorMap *tin, const CUtenso
 }
 
 template <class St>
-__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+__global__ void __launch_bounds__(St::kCols, St::kMinBlocks)
 sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tdev,
                   const SweepArgs A) {
   const StepIO O{A.fout, A.fdev, A.partials, gridDim.x * gridDim.y, A.total ? A.arrivals : nullptr,
@@ -994,7 +1002,7 @@ sweep_step_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant
 // each instance sit in device memory for both buffer parities; an instance
 // reads buffer (item.par0 ^ kpar).
 template <class St>
-__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+__global__ void __launch_bounds__(St::kCols, St::kMinBlocks)
 sweep_batch_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restrict__ args,
                    const CUtensorMap *__restrict__ maps, int kpar, int records) {
   __shared__ SweepArgs A;
@@ -1050,7 +1058,7 @@ __device__ __forceinline__ unsigned next_ticket(const PersistArgs &P, unsigned *
 // item i depends on has finished `target` steps; false on give-up.  The
 // caller's next barrier publishes *ok.
 __device__ __forceinline__ void wait_deps(const PersistArgs &P, int i, unsigned target, int *err, int *ok) {
-  for (int d = P.dep_ofs[i] + (int)threadIdx.x; d < P.dep_ofs[i + 1]; d += kThreads) {
+  for (int d = P.dep_ofs[i] + (int)threadIdx.x; d < P.dep_ofs[i + 1]; d += (int)blockDim.x) {
     const unsigned *f = P.done + P.dep_idx[d];
     uint32_t n = 0;
     while ((int)(ld_acquire_gpu(f) - target) < 0) {
@@ -1080,7 +1088,7 @@ __device__ __forceinline__ void release_item(const PersistArgs &P, int i, unsign
 template <class St>
 __device__ __forceinline__ void inval_ring() {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  auto &S = *reinterpret_cast<SweepSmem<St::kSlotBytes> *>(smem_raw);
+  auto &S = *reinterpret_cast<SmemOf<St> *>(smem_raw);
   for (int q = 0; q < kPairs; ++q)
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[q])) : "memory");
 }
@@ -1088,7 +1096,7 @@ __device__ __forceinline__ void inval_ring() {
 // Batched form: items[i] names the lattice, tile and record; arguments and
 // tensor maps of every lattice (both buffer parities) in device memory.
 template <class St>
-__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+__global__ void __launch_bounds__(St::kCols, St::kMinBlocks)
 sweep_batch_persist_kernel(const BatchItem *__restrict__ items, const SweepArgs *__restrict__ args,
                            const CUtensorMap *__restrict__ maps, const PersistArgs P) {
   __shared__ SweepArgs A;
@@ -1134,7 +1142,7 @@ sweep_batch_persist_kernel(const BatchItem *__restrict__ items, const SweepArgs 
 // `total` (mass, momentum, flags); while monitoring, every step does so into
 // its own record slot and writes its record into the host ring.
 template <class St>
-__global__ void __launch_bounds__(kThreads, St::kMinBlocks)
+__global__ void __launch_bounds__(St::kCols, St::kMinBlocks)
 sweep_multi_kernel(const __grid_constant__ CUtensorMap tin0, const __grid_constant__ CUtensorMap tdev0,
                    const __grid_constant__ CUtensorMap tin1, const __grid_constant__ CUtensorMap tdev1,
                    const SweepArgs A, const PersistArgs P, const MultiOut Q) {
@@ -1256,7 +1264,7 @@ int maxw_of(int store) {
 
 template <class St>
 cudaError_t prepare_one(size_t *smem_bytes) {
-  *smem_bytes = sizeof(SweepSmem<St::kSlotBytes>);
+  *smem_bytes = sizeof(SmemOf<St>);
   cudaError_t e = cudaFuncSetAttribute(sweep_step_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)*smem_bytes);
   if (e == cudaSuccess)
@@ -1267,7 +1275,7 @@ cudaError_t prepare_one(size_t *smem_bytes) {
 template <class St>
 cudaError_t launch_batch_one(const BatchItem *items, int nitems, const SweepArgs *args, const CUtensorMap *maps,
                              int kpar, int records, size_t smem, cudaStream_t st) {
-  sweep_batch_kernel<St><<<nitems, kThreads, smem, st>>>(items, args, maps, kpar, records);
+  sweep_batch_kernel<St><<<nitems, St::kCols, smem, st>>>(items, args, maps, kpar, records);
   return cudaGetLastError();
 }
 
@@ -1279,7 +1287,7 @@ cudaError_t launch_one(const CUtensorMap &m0, const CUtensorMap &m1, const Sweep
   // touching global memory.
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)A.nstrips, (unsigned)A.nseg);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(St::kCols);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1297,7 +1305,7 @@ cudaError_t launch_batch_persist_one(const BatchItem *items, const SweepArgs *ar
   // all at once, which the dependency waits rely on.
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(St::kCols);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1320,7 +1328,7 @@ cudaError_t launch_multi_one(const CUtensorMap (&m)[2][2], const SweepArgs &A, c
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(St::kCols);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1340,9 +1348,9 @@ cudaError_t persist_capacity_one(size_t smem, int *blocks) {
     e = cudaFuncSetAttribute(sweep_multi_kernel<St>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, per_sm2 = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_persist_kernel<St>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_persist_kernel<St>, St::kCols, smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, sweep_multi_kernel<St>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, sweep_multi_kernel<St>, St::kCols, smem);
   per_sm = std::min(per_sm, per_sm2);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1367,15 +1375,15 @@ size_t sweep_buffer_bytes(int store, long long plane) {
 cudaError_t sweep_make_maps(int store, void *base, int pitch, int ny, long long plane, CUtensorMap *m0,
                             CUtensorMap *m1) {
   if (store == kStoreF32) {
-    static_assert(StoreF32::kTxBytes == 9 * 2 * kCols * sizeof(float), "TMA box must match the slot");
-    cudaError_t e = encode_map(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, pitch, ny, plane, 9, kCols, m0);
+    static_assert(StoreF32::kTxBytes == 9 * 2 * StoreF32::kCols * sizeof(float), "TMA box must match the slot");
+    cudaError_t e = encode_map(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, pitch, ny, plane, 9, StoreF32::kCols, m0);
     *m1 = *m0;
     return e;
   }
-  static_assert(StoreBF16::kRestBytes == 2 * kCols * sizeof(float) &&
-                    StoreBF16::kDevBytes == 2 * StoreBF16::kDevCols * 8 * 2,
+  static_assert(StoreBF16::kRestBytes == 2 * StoreBF16::kCols * sizeof(float) &&
+                    StoreBF16::kDevBytes == 2 * StoreBF16::kDevCols * 8 * 2 && StoreBF16::kCols == StoreFP16::kCols,
                 "TMA boxes must match the slot");
-  cudaError_t e = encode_map(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, pitch, ny, plane, 1, kCols, m0);
+  cudaError_t e = encode_map(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, pitch, ny, plane, 1, StoreBF16::kCols, m0);
   if (e != cudaSuccess) return e;
   void *dev = static_cast<char *>(base) + (size_t)plane * sizeof(float);
   return encode_map(store == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, dev,
