@@ -156,6 +156,41 @@ def test_dev16_full_size_bench_launches(prec, fmt):
     assert gpu_err <= 2.0 * fmt_err + 1e-6
 
 
+def test_dev16_largest_lattice_against_fp64():
+    """The largest lattice whose padded planes the sweep indexes in 32 bits
+    (16384 x 13000, 213 M sites), 16-bit storage with its 128-column
+    window: three steps from the same noise against the FP64 path on every
+    site (compared on the device), and the mass.  Bound: each step rounds
+    every stored deviation to the format (half an ulp of deviations that
+    stay below ~0.02 here: 8 links x 3 steps x 2^-9 x 0.02 ~ 1e-3 for bf16,
+    8x less for fp16's 3 more bits); the measured errors are printed."""
+    import torch
+    from paper_1307_6703_gb300 import LB_DTYPE_F32, LB_DTYPE_F64, LB_FP64, lb_moments
+    from gpu_util import solver_for
+    w = C4.with_(nx=16384, ny=13000)
+    pitch = ((w.nx + 8 + 31) // 32) * 32
+    assert 9 * pitch * (w.ny + 8) < 2 ** 31
+    s = solver_for(w, LB_FP64).init_noise(9, w.rho_mean, w.noise).step(3)
+    n64 = torch.empty((w.ny, w.nx), dtype=torch.float64, device="cuda")
+    lb_moments(s.h, n64, None, None, LB_DTYPE_F64, 1)
+    rc, (m64, _, _) = s.reduce()
+    s.close()
+    assert rc == 0
+    for prec, fmt, bound in ((LB_BF16DEV, "bf16", 1e-3), (LB_FP16DEV, "fp16", 1.25e-4)):
+        s = dev16_solver(w, prec, RHO_REF).init_noise(9, w.rho_mean, w.noise).step(3)
+        n = torch.empty((w.ny, w.nx), dtype=torch.float32, device="cuda")
+        lb_moments(s.h, n, None, None, LB_DTYPE_F32, 1)
+        torch.cuda.synchronize()
+        rc, (m, _, _) = s.reduce()
+        s.close()
+        err = float(((n.double() - n64).abs().max() / n64.abs().max()).item())
+        print(f"16384 x 13000 {fmt}: max rel density error after 3 steps {err:.2e}, mass {abs(m - m64) / m64:.1e}")
+        assert rc == 0
+        assert err <= bound
+        assert abs(m - m64) / m64 <= 1e-6
+    del n64
+
+
 DAMPED = {
     # supercritical sheared fluid relaxing to Couette flow
     "couette": (dict(nx=128, ny=48, T=1.1 * TC, A0=0.0, lam=0.0, u_bot=-0.05, u_top=0.05),
