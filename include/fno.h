@@ -93,7 +93,7 @@ int fno_adam(fno_handle *h, float lr, float beta1, float beta2, float eps, int32
  * ux0, uy0 of lb_init at fields + 3 b nx ny, + nx ny, + 2 nx ny).
  * scales = (s0, s1, s2), a HOST array.  FP64 arithmetic, each operation
  * rounded once; the mean is a fixed-order sum.  Enqueued on the handle's
- * stream.  Errors: LB_ERR_ARG (null pointers, batch outside 1..65535,
+ * stream.  Errors: LB_ERR_ARG (null pointers, batch outside 1..8192,
  * fewer than 3 outputs), LB_ERR_CUDA.                                      */
 int fno_fields(fno_handle *h, const float *out, int32_t batch, int32_t nx, int32_t ny, const double *scales,
                double rho_mean, double *fields);

@@ -1151,11 +1151,12 @@ int fno_backward(fno_handle *h, const float *target, double *loss) {
 int fno_fields(fno_handle *h, const float *out, int32_t batch, int32_t nx, int32_t ny, const double *scales,
                double rho_mean, double *fields) {
   if (!h || !out || !scales || !fields) return ffail(h, LB_ERR_ARG, "fno_fields: null argument");
-  if (batch < 1 || batch > 65535 || nx < 1 || ny < 1 || h->c.outputs < 3)
+  // (the block sums of every field share the 8192-double loss partials)
+  if (batch < 1 || batch > 8192 || nx < 1 || ny < 1 || h->c.outputs < 3)
     return ffail(h, LB_ERR_ARG, "fno_fields: batch, lattice or output channels out of range");
   const long long S = (long long)nx * ny;
-  // block sums in the loss partials (8192 doubles; the same stream orders
-  // their uses)
+  // block sums in the loss partials (8192 doubles, batch * nblk of them; the
+  // same stream orders their uses)
   const int nblk = (int)std::max<long long>(1, std::min<long long>({256, 8192 / batch, (S + kThreads - 1) / kThreads}));
   field_mass_kernel<<<dim3(nblk, batch), kThreads, 0, h->st>>>(out, h->c.outputs, S, scales[0], h->partial);
   fields_kernel<<<dim3(nblk, batch), kThreads, 0, h->st>>>(out, h->c.outputs, S, scales[0], scales[1], scales[2],

@@ -133,3 +133,32 @@ def test_adam_step_matches_the_update_rule():
     expect = flat - 1e-3 * g / (np.abs(g) + 1e-8)
     assert np.abs(new - expect).max() <= 1e-6
     net.close()
+
+
+def test_fields_from_the_network_output():
+    """fno_fields against the same steps in numpy: rescale the three output
+    channels, then shift each density to the mean rho_mean (FP64, each
+    operation rounded once); batches outside 1..8192 are refused."""
+    import torch
+    from paper_1307_6703_gb300.fno import Fno, fno_fields
+    from paper_1307_6703_gb300.lb import LBError
+    net = Fno(**CFG, batch_max=2, nx_max=NX, ny_max=NY, gemm_bf16=False)
+    rng = np.random.default_rng(11)
+    B, scales, rho_mean = 3, (0.5, 0.05, 0.05), 0.93
+    raw = rng.standard_normal((B, CFG["outputs"], NY, NX)).astype(np.float32)
+    out = torch.tensor(raw, device="cuda")
+    fields = torch.empty((B, 3, NY, NX), dtype=torch.float64, device="cuda")
+    net.fields(out, NX, NY, scales, rho_mean, fields)
+    torch.cuda.synchronize()
+    ref = raw[:, :3].astype(np.float64)
+    for j, sc in enumerate(scales):
+        ref[:, j] *= sc
+    ref[:, 0] += 1.0
+    ref[:, 0] += rho_mean - ref[:, 0].mean(axis=(1, 2), keepdims=True)
+    got = fields.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13
+    assert np.allclose(got[:, 0].mean(axis=(1, 2)), rho_mean, atol=1e-13)
+    for bad in (0, 8193):
+        with pytest.raises(LBError):
+            fno_fields(net.h, out, bad, NX, NY, scales, rho_mean, fields)
+    net.close()
