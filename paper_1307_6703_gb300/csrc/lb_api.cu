@@ -453,8 +453,15 @@ int multi_steps(lb_handle *h, int64_t nsteps) {
     Q.mon_ring = h->mon_ring;
     Q.mon_cap = h->mon_cap;
   }
+  // A monitored launch holds at most as many steps as the ring has records,
+  // so it writes each ring slot once; launches are stream-ordered, so an
+  // earlier step's record never lands after a later one's in the same slot
+  // (a tile publishes its completion before its record reduction, so the
+  // final sums of different steps of one launch are not ordered).
+  const int64_t per_launch = mon ? std::min<int64_t>(kMonSlots, h->mon_cap)
+                                 : std::max<int64_t>(2, (1LL << 30) / ntiles);
   for (int64_t done = 0; done < nsteps;) {
-    const int chunk = (int)std::min<int64_t>(nsteps - done, mon ? kMonSlots : std::max<int64_t>(2, (1LL << 30) / ntiles));
+    const int chunk = (int)std::min<int64_t>(nsteps - done, per_launch);
     Q.mon_step0 = h->step + 1;  // step number of the first step's result
     lbk::PersistArgs P{};
     P.nitems = ntiles;

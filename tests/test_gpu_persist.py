@@ -224,3 +224,24 @@ def test_monitor_across_multistep_launches(steps):
     assert np.all(np.abs(r[r[:, 5] >= 0, 0] - vals[0]) <= 1e-6 * vals[0])
     assert np.all(r[r[:, 5] >= 0, 3:5] == 0.0)
     s.close()
+
+
+@pytest.mark.parametrize("cap,steps", [(5, 23), (1, 7)])
+def test_monitor_ring_smaller_than_the_run(cap, steps):
+    """A ring of fewer records than steps: each record holds the latest
+    step of its residue (s mod cap), the last equal to lb_reduce bit for
+    bit."""
+    import torch
+    w = C2(0.05).with_(nx=256, ny=128)
+    s = solver_for(w, LB_FP32).init_noise(3, w.rho_mean, w.noise)
+    ring = torch.full((cap, 6), -1.0, dtype=torch.float64).pin_memory()
+    s.monitor(ring)
+    s.step(steps)
+    torch.cuda.synchronize()
+    r = ring.numpy().copy()
+    latest = {s_ % cap: s_ for s_ in range(1, steps + 1)}
+    assert [int(r[k, 5]) for k in range(cap)] == [latest[k] for k in range(cap)]
+    rc, vals = s.reduce()
+    assert rc == 0 and list(r[steps % cap, :3]) == vals
+    assert np.all(r[:, 3:5] == 0.0)
+    s.close()
