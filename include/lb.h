@@ -204,7 +204,8 @@ int lb_set_state(lb_handle *h, const void *buf, size_t bytes, int64_t step);
  * candidate tiling -- segment height (rows per CTA, which trades CTAs per SM
  * against re-read warm-up rows) and strip count (the fewest strips and up
  * to three more of at least 64 columns, which changes how the tiles fill
- * the GPU) -- keeps the fastest for later lb_step calls and writes its
+ * the GPU) -- times the three fastest twice more and keeps the one with
+ * the smallest of its three timings for later lb_step calls, and writes its
  * segment height to *seg_h (may be NULL; 0 when the handle uses the tile
  * kernel, which has no tiling choice; lb_get_tiling gives both).  The state and the step counter are restored
  * afterwards: the trajectory is the same as without the call.  Needs one

@@ -923,33 +923,56 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(save, h->f[cur0], buf_bytes, cudaMemcpyDeviceToDevice, h->st);
-  for (int sc : strips) {
-  h->sweep_nstrips = sc;
-  lbk::sweep_strips(h->store, h->p.nx, sc, &h->sweep_base, &h->sweep_extra);
-  int last = -1;
-  for (int c : cand) {
-    if (e != cudaSuccess || rc != LB_OK) break;
-    const int sh = std::min(c, ny);
-    if (sh == last) continue;
-    last = sh;
+  // One timing of `steps` steps (after a 2-step warm-up) of a tiling, from
+  // the saved state, which is restored afterwards; < 0 on failure.
+  auto time_tiling = [&](int sc, int sh) -> float {
+    h->sweep_nstrips = sc;
+    lbk::sweep_strips(h->store, h->p.nx, sc, &h->sweep_base, &h->sweep_extra);
     set_segments(h, sh);
-    float ms = 0.f;
+    float ms = -1.f;
     rc = lb_step(h, 2);  // warm-up
     if (rc == LB_OK) e = cudaEventRecord(e0, h->st);
     if (rc == LB_OK && e == cudaSuccess) rc = lb_step(h, steps);
     if (rc == LB_OK && e == cudaSuccess) e = cudaEventRecord(e1, h->st);
     if (rc == LB_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (rc == LB_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (rc == LB_OK && e == cudaSuccess && ms < best_ms) {
-      best_ms = ms;
-      best = sh;
-      best_strips = sc;
-    }
-    // back to the saved state for the next candidate
     h->cur = cur0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->f[cur0], save, buf_bytes, cudaMemcpyDeviceToDevice, h->st);
+    return (rc == LB_OK && e == cudaSuccess) ? ms : -1.f;
+  };
+  // Every candidate once, then the three fastest twice more: the minimum of
+  // three timings decides among them (single timings of close candidates
+  // differ by less than their run-to-run spread).
+  struct Timed {
+    float ms;
+    int sc, sh;
+  };
+  std::vector<Timed> timed;
+  for (int sc : strips) {
+    int last = -1;
+    for (int c : cand) {
+      if (e != cudaSuccess || rc != LB_OK) break;
+      const int sh = std::min(c, ny);
+      if (sh == last) continue;
+      last = sh;
+      const float ms = time_tiling(sc, sh);
+      if (ms >= 0.f) timed.push_back({ms, sc, sh});
+    }
   }
-  }
+  std::sort(timed.begin(), timed.end(), [](const Timed &a, const Timed &b) { return a.ms < b.ms; });
+  if (timed.size() > 3) timed.resize(3);
+  for (int rep = 0; rep < 2; ++rep)
+    for (Timed &t : timed) {
+      if (e != cudaSuccess || rc != LB_OK) break;
+      const float ms = time_tiling(t.sc, t.sh);
+      if (ms >= 0.f) t.ms = std::min(t.ms, ms);
+    }
+  for (const Timed &t : timed)
+    if (t.ms < best_ms) {
+      best_ms = t.ms;
+      best = t.sh;
+      best_strips = t.sc;
+    }
   h->cur = cur0;
   h->step = step0;
   const bool tuned = rc == LB_OK && e == cudaSuccess;
