@@ -55,3 +55,39 @@ def test_kernel_digest_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_source_digest() == base
     p.write_text(src.replace("kWaitLimit = 1u << 22", "kWaitLimit = 1u << 21"))
     assert bench.kernel_source_digest() != base
+
+
+def test_profiled_traffic_follows_the_summary_and_its_digest(tmp_path, monkeypatch):
+    """roofline.traffic: the committed summary's back-to-back bytes per step
+    times the steps of one launch, with its basis; None (and the reason)
+    when the summary is missing, gives no bytes, or was taken on another
+    kernel source."""
+    sys.path.insert(0, ROOT)
+    import bench
+    digest = bench.kernel_source_digest()
+    p = tmp_path / "summary.md"
+    p.write_text(f"# x\n\nkernel source digest: `{digest}` (sha256 ...)\n"
+                 "dram bytes per step: 1000 (back to back, 20-step launch)\n")
+    monkeypatch.setitem(bench.PROFILE, "fp32", str(p))
+    traffic, basis = bench.profiled_traffic("fp32", 20)
+    assert traffic == 20000 and basis.startswith("20 steps x 1000")
+    p.write_text("kernel source digest: `0123456789abcdef`\ndram bytes per step: 1000 (x)\n")
+    traffic, basis = bench.profiled_traffic("fp32", 20)
+    assert traffic is None and "changed" in basis
+    p.write_text(f"kernel source digest: `{digest}`\n")
+    assert bench.profiled_traffic("fp32", 20)[0] is None
+    monkeypatch.setitem(bench.PROFILE, "fp32", str(tmp_path / "missing.md"))
+    assert bench.profiled_traffic("fp32", 20) == (None, "no committed ncu summary")
+    assert bench.profiled_traffic("no such precision", 20) == (None, "no committed ncu summary")
+
+
+def test_step_launches_of_one_call():
+    """One lb_step(h, K) call: a single-step launch for K = 1, else
+    multi-step launches of at most max(2, 2^30 / tiles) steps each."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.step_launches(1, 720) == (1, "lbk::sweep_step_kernel")
+    assert bench.step_launches(20, 720) == (1, "lbk::sweep_multi_kernel")
+    chunk = (1 << 30) // 720
+    assert bench.step_launches(chunk + 1, 720) == (2, "lbk::sweep_multi_kernel")
+    assert bench.step_launches(5, 1 << 31) == (3, "lbk::sweep_multi_kernel")
