@@ -95,7 +95,7 @@ int cuda_fail(lb_handle *h, cudaError_t e, const char *where) {
 // pageable memory, another device's memory and anything else.  Asked
 // through the driver, so that the runtime's last-error state is left as
 // the caller had it.
-void *device_view(const void *p) {
+void *device_view(const void *p, bool host_only = false) {
   typedef CUresult (*get_attr_fn)(void *, CUpointer_attribute, CUdeviceptr);
   static get_attr_fn get = nullptr;
   if (!p) return nullptr;
@@ -110,7 +110,7 @@ void *device_view(const void *p) {
   }
   unsigned type = 0;
   if (get(&type, CU_POINTER_ATTRIBUTE_MEMORY_TYPE, (CUdeviceptr)p) != CUDA_SUCCESS) return nullptr;
-  if (type == CU_MEMORYTYPE_DEVICE) {
+  if (type == CU_MEMORYTYPE_DEVICE && !host_only) {
     int ord = -1, cur = -2;
     if (get(&ord, CU_POINTER_ATTRIBUTE_DEVICE_ORDINAL, (CUdeviceptr)p) != CUDA_SUCCESS ||
         cudaGetDevice(&cur) != cudaSuccess || ord != cur)
@@ -418,7 +418,7 @@ cudaError_t ensure_mon_slots(lb_handle *h, int ntiles) {
   h->mon_tiles = 0;
   e = cudaMalloc((void **)&h->d_mon_recs, 4 * sizeof(double) * (size_t)ntiles * kMonSlots);
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_mon_arr, kMonSlots * sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMemset(h->d_mon_arr, 0, kMonSlots * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_mon_arr, 0, kMonSlots * sizeof(unsigned), h->st);
   if (e == cudaSuccess) h->mon_tiles = ntiles;
   return e;
 }
@@ -798,12 +798,11 @@ int lb_monitor(lb_handle *h, double *host_ring, int32_t capacity) {
   }
   if (!h->sweep || h->in_batch)
     return fail(h, LB_ERR_ARG, "lb_monitor: only for strip-sweep handles outside a batch");
-  void *dev = nullptr;
-  const cudaError_t e = cudaHostGetDevicePointer(&dev, host_ring, 0);
-  if (e != cudaSuccess || !dev) {
-    cudaGetLastError();  // clear the error state of the call
-    return fail(h, LB_ERR_ARG, "lb_monitor: the ring is not page-locked memory the device can address");
-  }
+  void *dev = device_view(host_ring, true);
+  if (!dev) return fail(h, LB_ERR_ARG, "lb_monitor: the ring is not page-locked memory the device can address");
+  // the per-step record slots of the current tiling now, not at the first
+  // monitored step (a later, finer tiling grows them at its launch)
+  LB_CUDA(h, ensure_mon_slots(h, h->sweep_nstrips * h->sweep_nseg));
   h->mon_ring = static_cast<double *>(dev);
   h->mon_cap = capacity;
   return LB_OK;
