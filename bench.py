@@ -8,7 +8,17 @@ arithmetic).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|bf16dev|fp16dev]
-                  [--workload single|batch|warmstart|precision|network]
+                  [--workload single|batch|warmstart|precision|network|next4]
+
+`value`: K steps in one lb_step call (one persistent launch), CUDA events
+on the solver's stream, inputs resident in HBM.  `e2e`: the same K steps
+through the C ABI with host buffers -- lb_init from a page-locked FP64
+density field, every step's record written into a page-locked ring by the
+step kernel (registered with lb_monitor before the timed region, like the
+allocation of the ring itself), lb_moments of the final state into
+page-locked host arrays -- timed on the host clock.  `roofline.traffic`:
+the committed ncu summary's back-to-back DRAM bytes per step, while the
+summary's kernel source digest matches the source.
 
 --impl reference times the FP64 CPU oracle (the reference arm) on the host
 cores, each step a bounded row band of the same workload.
