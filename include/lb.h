@@ -179,9 +179,13 @@ int lb_reduce_async(lb_handle *h, double *out);
  * straight into host memory, s being the step number after that step.  The
  * records of the steps enqueued so far are complete once the stream has
  * been synchronised; the ring must stay allocated while monitoring is on.
+ * The call allocates the device-side per-step record slots for the current
+ * tiling (synchronising the stream when it replaces smaller ones); while
+ * monitoring, lb_step launches at most min(capacity, 64) steps at a time,
+ * so each ring record is written once per launch and in step order.
  * Strip-sweep handles only (FP32 and 16-bit storage, not inside a batch).
  * Errors: LB_ERR_ARG (other handles, capacity < 0, memory the device cannot
- * address).                                                               */
+ * address), LB_ERR_CUDA, LB_ERR_OOM.                                       */
 int lb_monitor(lb_handle *h, double *host_ring, int32_t capacity);
 
 /* Checkpoint: copy the stored populations to the HOST buffer buf:
