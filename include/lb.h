@@ -234,12 +234,31 @@ int lb_get_tiling(const lb_handle *h, int32_t *nstrips, int32_t *seg_h);
 
 /* Set the tiling without tuning (e.g. one lb_get_tiling reported after
  * lb_autotune): nstrips column strips, at least the fewest the kernel's
- * window allows (ceil(nx / 116) for FP32, ceil(nx / 112) for 16-bit
+ * window allows (ceil(nx / 116) for FP32, ceil(nx / 120) for 16-bit
  * storage) and at most nx / (2 * quantum) (quantum 4 columns for FP32, 8
- * for 16-bit storage); seg_h as lb_set_seg_h.  The trajectory does not
- * depend on it beyond FP32 rounding order.  No-op for the tile kernel.
- * Errors: LB_ERR_ARG (out of range), LB_ERR_CUDA, LB_ERR_OOM.             */
+ * for 16-bit storage); seg_h as lb_set_seg_h.  Strip s starts at column
+ * s base + quantum min(s, extra) and is base or base + quantum wide (the
+ * first `extra` strips wider), base = quantum floor(nx / (quantum nstrips)).
+ * The trajectory is the same bit for bit for every tiling.  No-op for the
+ * tile kernel.  Errors: LB_ERR_ARG (out of range), LB_ERR_CUDA, LB_ERR_OOM. */
 int lb_set_tiling(lb_handle *h, int32_t nstrips, int32_t seg_h);
+
+/* Dependency lists of the multi-step sweep, for inspection and tests (host
+ * computation only, no GPU work; the paper has no counterpart).  For an
+ * nx x ny lattice (walls 0 or 1) in `precision` (LB_FP32, LB_BF16DEV or
+ * LB_FP16DEV) tiled as lb_set_tiling(nstrips, seg_h) describes, tile
+ * t = strip + nstrips * segment (segment g covers rows g seg_h ..
+ * min(ny, (g + 1) seg_h) - 1) waits, before each step of a multi-step
+ * launch, for every tile in idx[ofs[t] .. ofs[t + 1]) to have finished the
+ * previous step: the tiles that write a site (or a periodic image of one)
+ * that its TMA window reads -- rows ya - 4 .. yb + 4, columns from x0 - 4
+ * over the window's width -- and the tiles whose windows read its sites.
+ * ofs: ntiles + 1 entries (HOST); idx: up to cap entries (HOST, may be
+ * NULL when cap = 0); *count receives the number of entries.  Errors:
+ * LB_ERR_ARG (a lattice or tiling the sweep does not take, or cap below
+ * *count, which then holds the size needed).                               */
+int lb_sweep_dependencies(int32_t precision, int32_t nx, int32_t ny, int32_t walls, int32_t nstrips,
+                          int32_t seg_h, int32_t *ofs, int32_t *idx, int64_t cap, int64_t *count);
 
 /* ------------------------------------------------------------------------
  * Batched solver: many independent lattices (different sizes and physical

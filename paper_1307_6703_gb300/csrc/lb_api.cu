@@ -993,6 +993,26 @@ int lb_autotune(lb_handle *h, int steps, int32_t *seg_h) {
   return LB_OK;
 }
 
+int lb_sweep_dependencies(int32_t precision, int32_t nx, int32_t ny, int32_t walls, int32_t nstrips,
+                          int32_t seg_h, int32_t *ofs, int32_t *idx, int64_t cap, int64_t *count) {
+  if (!ofs || !count || cap < 0 || (cap > 0 && !idx)) return LB_ERR_ARG;
+  if ((precision != LB_FP32 && precision != LB_BF16DEV && precision != LB_FP16DEV) || (walls != 0 && walls != 1))
+    return LB_ERR_ARG;
+  const int store = precision;  // the storage codes of the sweep are the precision codes
+  if (!lbk::sweep_supported(store, nx, ny) || seg_h < 1) return LB_ERR_ARG;
+  const int qn = store == lbk::kStoreF32 ? 4 : 8;
+  if (nstrips < lbk::sweep_min_strips(store, nx) || nstrips > nx / (2 * qn)) return LB_ERR_ARG;
+  int base = 0, extra = 0;
+  lbk::sweep_strips(store, nx, nstrips, &base, &extra);
+  std::vector<int> o, d;
+  lbk::sweep_deps(store, nx, ny, walls, nstrips, base, extra, std::min((int)seg_h, (int)ny), o, d);
+  *count = (int64_t)d.size();
+  if (cap < *count) return LB_ERR_ARG;
+  for (size_t i = 0; i < o.size(); ++i) ofs[i] = o[i];
+  for (size_t i = 0; i < d.size(); ++i) idx[i] = d[i];
+  return LB_OK;
+}
+
 int lb_get_tiling(const lb_handle *h, int32_t *nstrips, int32_t *seg_h) {
   if (!h || !nstrips || !seg_h) return LB_ERR_ARG;
   *nstrips = h->sweep ? h->sweep_nstrips : 0;

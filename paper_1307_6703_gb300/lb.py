@@ -83,6 +83,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_set_seg_h.argtypes = [P, C.c_int32]
         lib.lb_get_tiling.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         lib.lb_set_tiling.argtypes = [P, C.c_int32, C.c_int32]
+        lib.lb_sweep_dependencies.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                              P, P, C.c_int64, C.POINTER(C.c_int64)]
         lib.lb_batch_create.argtypes = [C.POINTER(lb_params), C.c_int32, C.POINTER(P)]
         lib.lb_batch_handle.argtypes = [P, C.c_int32]
         lib.lb_batch_handle.restype = P
@@ -93,7 +95,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         lib.lb_batch_last_error.restype = C.c_char_p
         for name in ("lb_create", "lb_init", "lb_step", "lb_moments", "lb_reduce",
                      "lb_get_state", "lb_set_state", "lb_get_step", "lb_destroy",
-                     "lb_reduce_noalloc", "lb_autotune", "lb_get_tiling", "lb_set_tiling", "lb_batch_create", "lb_batch_step",
+                     "lb_reduce_noalloc", "lb_autotune", "lb_get_tiling", "lb_set_tiling", "lb_sweep_dependencies",
+                     "lb_batch_create", "lb_batch_step",
                      "lb_batch_autotune", "lb_batch_destroy"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
@@ -229,6 +232,26 @@ def lb_get_tiling(h) -> tuple[int, int]:
 def lb_set_tiling(h, nstrips: int, seg_h: int) -> None:
     """Fix the sweep kernel's strip count and segment height without tuning."""
     _check(load_library().lb_set_tiling(h, nstrips, seg_h), h)
+
+
+def lb_sweep_dependencies(precision: int, nx: int, ny: int, walls: int, nstrips: int, seg_h: int):
+    """(ofs, idx): the multi-step sweep's dependency lists in CSR form, tile
+    t = strip + nstrips * segment waiting for idx[ofs[t]:ofs[t + 1]] (host
+    computation; no GPU needed)."""
+    lib = load_library()
+    nseg = -(-ny // min(seg_h, ny)) if seg_h >= 1 else 1
+    ofs = np.zeros(max(nstrips, 0) * nseg + 1, dtype=np.int32)
+    count = C.c_int64(0)
+    rc = lib.lb_sweep_dependencies(precision, nx, ny, walls, nstrips, seg_h, ofs.ctypes.data, None, 0,
+                                   C.byref(count))
+    if rc != LB_OK and count.value == 0:
+        raise LBError(rc, "lb_sweep_dependencies: lattice or tiling not taken by the sweep")
+    idx = np.zeros(count.value, dtype=np.int32)
+    rc = lib.lb_sweep_dependencies(precision, nx, ny, walls, nstrips, seg_h, ofs.ctypes.data, idx.ctypes.data,
+                                   count.value, C.byref(count))
+    if rc != LB_OK:
+        raise LBError(rc, "lb_sweep_dependencies failed")
+    return ofs, idx
 
 
 def _bcheck(rc: int, b) -> int:
