@@ -106,3 +106,19 @@ def test_batch_create_rejects_bad_parameters_without_gpu(lib):
         with pytest.raises(LBError) as ei:
             lb_batch_create(ps)
         assert ei.value.code == LB_ERR_ARG
+
+
+@pytest.mark.parametrize("header", ["lb.h", "fno.h"])
+def test_headers_are_plain_c(header, tmp_path):
+    """The boundary is a C ABI: each public header compiles on its own as
+    C99 and as C++17 with warnings as errors (no C++ or library types)."""
+    import shutil
+    import subprocess
+    for cc, std, lang in (("gcc", "c99", "c"), ("g++", "c++17", "c++")):
+        if not shutil.which(cc):
+            pytest.skip(f"{cc} not available")
+        src = tmp_path / f"use_{header}.{ 'c' if lang == 'c' else 'cpp'}"
+        src.write_text(f'#include "{header}"\nint lb_header_check_dummy;\n')
+        r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                            "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
